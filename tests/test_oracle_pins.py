@@ -1,0 +1,668 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test states the passage of arXiv:1608.04601 it checks, and the fact
+(closed form, invariant, brute force, published vector) that pins it. All run
+on the CPU with the FP64 build unless stated.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import inputs as I
+from oracle import oracle as O
+from paper_1608_04601_gb300 import xsections as X
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _gas_custom(mass, n_pts, de, sig_e_cols, sig_i_cols, eps_exc=(1e9,), eps_iz=2e9):
+    return X.GasTables("custom", mass, tuple(eps_exc), eps_iz, de, np.ascontiguousarray(np.stack(sig_e_cols, 1)),
+                       np.ascontiguousarray(np.stack(sig_i_cols, 1)))
+
+
+# --------------------------------------------------------------------------- RNG and own functions
+
+def test_philox_known_answers():
+    """Philox4x32-10 (Salmon et al. SC'11) against the published known-answer vectors."""
+    rows = [ln.split() for ln in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+def test_uniform_exact_and_open():
+    assert O.uniform(0) == 2.0 ** -24
+    assert O.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    rng = np.random.default_rng(0)
+    for x in rng.integers(0, 2 ** 32, 2000):
+        assert O.uniform(int(x)) == ((int(x) >> 9) + 0.5) * 2.0 ** -23
+
+
+def _ulp32(x):
+    x = np.abs(np.float32(x))
+    return float(np.spacing(x)) if x > 0 else 2.0 ** -149
+
+
+def test_own_log_against_libm():
+    """Own log agrees with the correctly rounded log to 3 ulp over the whole Box-Muller range."""
+    rng = np.random.default_rng(11)
+    xs = np.concatenate([(np.arange(1 << 12) + 0.5) * 2.0 ** -12, rng.uniform(2 ** -25, 1, 4000),
+                         2.0 ** rng.uniform(-25, 30, 2000), [2 ** -25, 1 - 2 ** -24, 0.70710677, 1.4142135]])
+    worst = 0.0
+    for x in xs.astype(np.float32):
+        got = O.logf(float(x))
+        ref = math.log(float(x))
+        worst = max(worst, abs(got - ref) / _ulp32(ref))
+    assert worst <= 3.0, worst
+
+
+def test_own_sincospi_against_libm():
+    """Own sin(pi y), cos(pi y) agree with libm to 2^-22 absolute on [0, 2]."""
+    ys = np.concatenate([np.linspace(0, 2, 4001), np.random.default_rng(3).uniform(0, 2, 3000)]).astype(np.float32)
+    for y in ys:
+        s, c = O.sincospif(float(y))
+        assert abs(s - math.sin(math.pi * float(y))) <= 2 ** -22
+        assert abs(c - math.cos(math.pi * float(y))) <= 2 ** -22
+        assert s * s + c * c == pytest.approx(1.0, abs=4e-7)
+
+
+def test_box_muller_and_isotropy_statistics():
+    n = 40000
+    words = np.array([O.philox([k, 7, 0, 0], [1, 2]) for k in range(n)], dtype=np.uint64)
+    u = ((words >> 9).astype(np.float64) + 0.5) * 2.0 ** -23
+    n0 = np.empty(n)
+    n1 = np.empty(n)
+    d = np.empty((n, 3))
+    for k in range(n):
+        n0[k], n1[k] = O.box_muller(u[k, 0], u[k, 1])
+        d[k] = O.isotropic(u[k, 2], u[k, 3])
+    assert stats.kstest(n0, "norm").pvalue > 1e-4
+    assert stats.kstest(n1, "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(n0, n1)[0, 1]) < 5 / math.sqrt(n)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-6)
+    assert stats.kstest(d[:, 2], "uniform", args=(-1, 2)).pvalue > 1e-4
+    az = np.arctan2(d[:, 1], d[:, 0])
+    assert stats.kstest(az, "uniform", args=(-math.pi, 2 * math.pi)).pvalue > 1e-4
+    assert np.all(np.abs(d.mean(0)) < 5 / math.sqrt(3 * n))
+
+
+# --------------------------------------------------------------------------- field solve
+
+def test_poisson_uniform_charge_closed_form():
+    """Eq. (poisson) with uniform rho0 and phi(0)=V, phi(d)=0: phi = V(1-z/d) + rho0 z(d-z)/(2 eps0).
+    The 3-point stencil is exact for quadratics, so the nodes agree to round-off; E = -phi' is linear
+    and the central / half-cell wall formulas reproduce it exactly."""
+    for N, d, V, rho0 in [(128, 0.025, 200.0, 3e-5), (2048, 0.05, -500.0, -1e-4), (7, 0.01, 13.0, 2e-6)]:
+        dx = d / N
+        z = np.arange(N + 1) * dx
+        phi, E = O.poisson(np.full(N + 1, rho0), dx, V, 0.0)
+        phi_ref = V * (1 - z / d) + rho0 * z * (d - z) / (2 * I.EPS0)
+        E_ref = V / d - rho0 * (d - 2 * z) / (2 * I.EPS0)
+        scale = abs(V) + abs(rho0) * d * d / I.EPS0
+        assert np.max(np.abs(phi - phi_ref)) <= 1e-12 * scale * N
+        assert np.max(np.abs(E - E_ref)) <= 1e-11 * (abs(V) / d + abs(rho0) * d / I.EPS0) * N
+
+
+def test_poisson_random_charge_dense_solve():
+    rng = np.random.default_rng(5)
+    N, dx, V = 300, 1e-4, 77.0
+    rho = rng.normal(0, 1e-5, N + 1)
+    phi, E = O.poisson(rho, dx, V, 0.0)
+    A = np.zeros((N - 1, N - 1))
+    b = -rho[1:N] * dx * dx / I.EPS0
+    for k in range(N - 1):
+        A[k, k] = -2
+        if k > 0:
+            A[k, k - 1] = 1
+        if k < N - 2:
+            A[k, k + 1] = 1
+    b[0] -= V
+    ref = np.linalg.solve(A, b)
+    assert np.max(np.abs(phi[1:N] - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # Gauss's law over the half cells and the interior central difference
+    assert E[0] == pytest.approx((phi[0] - phi[1]) / dx - rho[0] * dx / (2 * I.EPS0), rel=1e-14)
+    assert E[N] == pytest.approx((phi[N - 1] - phi[N]) / dx + rho[N] * dx / (2 * I.EPS0), rel=1e-14)
+    assert np.allclose(E[1:N], (phi[:N - 1] - phi[2:]) / (2 * dx), rtol=1e-14, atol=0)
+
+
+# --------------------------------------------------------------------------- CIC, gather, push
+
+def _no_collision_gas(mass=4.002602 * I.AMU):
+    n_pts, de = 101, 1.0
+    z = np.zeros(n_pts)
+    return _gas_custom(mass, n_pts, de, [z, z, z], [z, z])
+
+
+def test_deposit_conserves_charge_and_node_cases():
+    """Cloud-in-cell (section 'PIC/MCC simulation procedure'): weight 1-f to node c, f to node c+1;
+    the fixed-point total is exactly 2^32 per particle, and a particle on a node puts all of it there."""
+    N = 32
+    o = O.Oracle(_no_collision_gas(), I.discharge(n_cells=N, dt_s=None) if False else I.discharge(n_cells=N),
+                 "f64", load=False)
+    rng = np.random.default_rng(1)
+    st = I.maxwell_state(rng, 5000, N, 0.0)
+    st["f"][:10] = 0.0
+    st["c"][:10] = 5
+    st["f"][10] = 0.25
+    st["c"][10] = 9
+    o.set_state(0, st)
+    o.set_state(1, I.maxwell_state(rng, 10, N, 0.0))
+    o.set_field(np.zeros(N + 1))
+    o.sweep()
+    De = o.get_deposit(0)
+    assert De.sum() == 5000 * 2 ** 32
+    ref = np.zeros(N + 1, np.int64)
+    for c, f in zip(st["c"], st["f"]):
+        F = int(np.rint(f * 2.0 ** 32))
+        ref[c] += 2 ** 32 - F
+        ref[c + 1] += F
+    assert np.array_equal(De, ref)
+    one = O.Oracle(_no_collision_gas(), I.discharge(n_cells=N), "f64", load=False)
+    one.set_state(0, {"c": [9], "f": [0.25], "vx": [0.0], "vy": [0.0], "vz": [0.0]})
+    one.set_state(1, {"c": [5], "f": [0.0], "vx": [0.0], "vy": [0.0], "vz": [0.0]})
+    one.set_field(np.zeros(N + 1))
+    one.sweep()
+    d0, d1 = one.get_deposit(0), one.get_deposit(1)
+    assert d0[9] == 3 * 2 ** 30 and d0[10] == 2 ** 30 and d0.sum() == 2 ** 32
+    assert d1[5] == 2 ** 32 and d1.sum() == 2 ** 32
+
+
+def test_gather_linear_field_and_kick_sign():
+    """Linear interpolation of a linear node field is exact; one sweep from rest kicks v_z by
+    (q/m) E(x) dt for each species (electrons against the field, ions along it)."""
+    N, gap, dt = 16, 0.016, 1e-11
+    d = I.discharge(n_cells=N, gap_m=gap, steps_per_period=int(round(1 / (13.56e6 * dt))))
+    dt = d.dt_s
+    o = O.Oracle(_no_collision_gas(), d, "f64", load=False)
+    z = np.arange(N + 1) * (gap / N)
+    E = 1000.0 + 2.5e5 * z
+    o.set_field(E)
+    rng = np.random.default_rng(2)
+    n = 200
+    st = {"c": rng.integers(2, N - 2, n).astype(np.int32), "f": rng.uniform(0, 1, n),
+          "vx": np.zeros(n), "vy": np.zeros(n), "vz": np.zeros(n)}
+    o.set_state(0, st)
+    o.set_state(1, st)
+    o.sweep()
+    zp = (st["c"] + st["f"]) * (gap / N)
+    Ep = 1000.0 + 2.5e5 * zp
+    for sp, qm in ((0, -I.E_CH / I.M_E), (1, I.E_CH / (4.002602 * I.AMU))):
+        out = o.get_state(sp)
+        assert out["c"].size == n
+        assert np.allclose(out["vz"], qm * Ep * dt, rtol=1e-12, atol=0)
+
+
+def test_field_free_push_is_exact_and_conserves_energy():
+    """No field, no collisions: x_n = x_0 + v t exactly to round-off, speeds unchanged (velocity Verlet)."""
+    N, gap = 64, 0.05
+    d = I.discharge(n_cells=N, gap_m=gap)
+    o = O.Oracle(_no_collision_gas(), d, "f64", load=False)
+    o.set_field(np.zeros(N + 1))
+    rng = np.random.default_rng(3)
+    n = 300
+    st = {"c": np.full(n, N // 2, np.int32), "f": rng.uniform(0, 1, n), "vx": rng.normal(0, 1e5, n),
+          "vy": rng.normal(0, 1e5, n), "vz": rng.uniform(-1, 1, n) * 0.3 * (gap / 2) / (20 * d.dt_s)}
+    o.set_state(0, st)
+    o.set_state(1, {k: v[:1] for k, v in st.items()})
+    for k in range(20):
+        o.step_index = k
+        o.sweep()
+    out = o.get_state(0)
+    dx = gap / N
+    z = (out["c"] + out["f"]) * dx
+    z_ref = (st["c"] + st["f"]) * dx + st["vz"] * 20 * d.dt_s
+    assert np.max(np.abs(z - z_ref)) <= 1e-12 * gap
+    assert np.array_equal(out["vx"], st["vx"]) and np.array_equal(out["vz"], st["vz"])
+
+
+def test_constant_field_parabola():
+    """Velocity Verlet integrates constant acceleration exactly: z = z0 + v0 t + a t^2 / 2.
+    The stored velocity is v0 - a dt / 2 (the half back-kick of the load)."""
+    N, gap = 64, 0.05
+    d = I.discharge(n_cells=N, gap_m=gap)
+    dt = d.dt_s
+    o = O.Oracle(_no_collision_gas(), d, "f64", load=False)
+    E0 = -350.0
+    o.set_field(np.full(N + 1, E0))
+    a = (-I.E_CH / I.M_E) * E0
+    rng = np.random.default_rng(4)
+    n, steps = 100, 30
+    v0 = rng.uniform(-1, 1, n) * 2e5
+    st = {"c": np.full(n, 20, np.int32), "f": rng.uniform(0, 1, n), "vx": np.zeros(n), "vy": np.zeros(n),
+          "vz": v0 - 0.5 * a * dt}
+    o.set_state(0, st)
+    o.set_state(1, {k: v[:1] for k, v in st.items()})
+    for k in range(steps):
+        o.step_index = k
+        o.sweep()
+    out = o.get_state(0)
+    assert out["c"].size == n
+    t = steps * dt
+    dx = gap / N
+    z = (out["c"] + out["f"]) * dx
+    z_ref = (st["c"] + st["f"]) * dx + v0 * t + 0.5 * a * t * t
+    assert np.max(np.abs(z - z_ref)) <= 1e-11 * gap
+
+
+# --------------------------------------------------------------------------- MCC
+
+def test_brute_force_collision_probability_electrons():
+    """Null-collision method (section 'PIC/MCC simulation procedure'): a particle is a candidate with
+    P_null = 1 - exp(-nu_max dt) and collides for real with nu(eps)/nu_max, so
+    P = P_null nu/nu_max, within nu dt * nu_max dt / 2 of the exact 1 - exp(-n sigma v dt)."""
+    sig = 1e-19
+    g = X.constant_sigma(sigma_el=sig, eps_max_eV=100.0, de_eV=1e-2)
+    d = I.discharge(n_cells=64, p_Pa=30.0, steps_per_period=int(1 / (13.56e6 * 7.4e-11)))
+    o = O.Oracle(g, d, "f64", load=False)
+    o.set_field(np.zeros(65))
+    n = 1_000_000
+    eps = 10.0
+    v = math.sqrt(2 * I.E_CH * eps / I.M_E)
+    rng = np.random.default_rng(6)
+    o.set_state(0, I.speed_state(rng, n, 64, v))
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    k = o.counters()["collisions_e"][0]
+    n_gas = d.p_Pa / (I.K_B * d.T_gas_K)
+    nu = n_gas * sig * v
+    vmax = math.sqrt(2 * I.E_CH * 100.0 / I.M_E)
+    numax = n_gas * sig * vmax
+    dt = d.dt_s
+    p_alg = -math.expm1(-numax * dt) * nu / numax
+    p_exact = -math.expm1(-nu * dt)
+    assert abs(p_alg - p_exact) <= nu * dt * numax * dt / 2
+    se = math.sqrt(p_alg * (1 - p_alg) / n)
+    assert abs(k / n - p_alg) <= 5 * se
+    assert abs(k / n - p_exact) <= 5 * se + nu * dt * numax * dt / 2
+
+
+def test_brute_force_collision_probability_ions_centre_of_mass():
+    """Ion tables are indexed by the centre-of-mass energy eps_cm = M g^2 / 4 (equal masses; helium
+    caption of Fig. 'Cross_He'): with constant sigma the collision probability is 1 - exp(-n sigma g dt)."""
+    M = 4.002602 * I.AMU
+    sig = 3e-19
+    n_pts, de = 20001, 1e-2
+    z = np.zeros(n_pts)
+    g = _gas_custom(M, n_pts, de, [z, z, z], [np.full(n_pts, sig), z])
+    d = I.discharge(n_cells=64, p_Pa=30.0, steps_per_period=int(1 / (13.56e6 * 1e-9)))
+    o = O.Oracle(g, d, "f64", load=False)
+    o.set_field(np.zeros(65))
+    n = 400_000
+    v = 1.0e5
+    rng = np.random.default_rng(7)
+    o.set_state(1, I.speed_state(rng, n, 64, v))
+    o.set_state(0, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    k = o.counters()["collisions_i"][0]
+    n_gas = d.p_Pa / (I.K_B * d.T_gas_K)
+    dt = d.dt_s
+    gmax = math.sqrt(4 * I.E_CH * (n_pts - 1) * de / M)
+    numax = n_gas * sig * gmax
+    p_alg = -math.expm1(-numax * dt) * (v / gmax)   # thermal target motion: (790/1e5)^2 correction
+    se = math.sqrt(p_alg * (1 - p_alg) / n)
+    assert abs(k / n - p_alg) <= 5 * se + 1e-4 * p_alg
+    # a lab-frame lookup would be off by sqrt(2)
+    assert abs(k / n - p_alg * math.sqrt(2)) > 50 * se
+
+
+def test_exponential_free_flight():
+    """Constant nu (sigma proportional to 1/v): the first real collision after t is exp(-nu t)
+    distributed at the step times (the null-collision candidates are Bernoulli(P_null) per step)."""
+    M = 1e6 * I.AMU
+    k_el = 2e-14
+    g = X.constant_nu(k_el, M, eps_max_eV=10.0, de_eV=1e-3)
+    d = I.discharge(n_cells=64, p_Pa=30.0, gap_m=1.0, steps_per_period=int(1 / (13.56e6 * 2e-10)))
+    dt = d.dt_s
+    o = O.Oracle(g, d, "f64", load=False)
+    o.set_field(np.zeros(65))
+    n, steps = 50_000, 60
+    rng = np.random.default_rng(8)
+    st = I.speed_state(rng, n, 64, 1e5)   # 28 meV: well inside the tabulated range
+    o.set_state(0, st)
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    first = np.full(n, -1)
+    prev = st["vx"].copy()
+    for k in range(steps):
+        o.step_index = k
+        o.sweep()
+        cur = o.get_state(0)["vx"]
+        hit = (cur != prev) & (first < 0)
+        first[hit] = k + 1
+        prev = cur.copy()
+    assert o.count(0) == n
+    n_gas = d.p_Pa / (I.K_B * d.T_gas_K)
+    nu = n_gas * k_el
+    t_grid = np.arange(1, steps + 1) * dt
+    cdf_ref = 1 - np.exp(-nu * t_grid)
+    emp = np.array([(first[first > 0] <= j).sum() for j in range(1, steps + 1)]) / n
+    eps = math.sqrt(math.log(2 / 1e-6) / (2 * n))  # DKW bound
+    assert np.max(np.abs(emp - cdf_ref)) <= eps
+
+
+def _forced_gas(mass, col, k, eps_th=0.0, n_exc=1):
+    """Every candidate takes process `col` (sigma*v = k for eps > eps_th); nu_max dt >> 1 makes every
+    particle a candidate."""
+    n_pts, de = 40001, 5e-3
+    eps = np.arange(n_pts) * de
+    v = np.sqrt(2 * I.E_CH * np.maximum(eps, 1e-9) / I.M_E)
+    cols = [np.zeros(n_pts) for _ in range(2 + n_exc)]
+    cols[col] = np.where(eps > eps_th, k / v, 0.0)
+    z = np.zeros(n_pts)
+    exc = (eps_th,) if col == 1 else (1e9,)
+    iz = eps_th if col == 2 + n_exc - 1 else 2e9
+    return _gas_custom(mass, n_pts, de, cols, [z, z], eps_exc=exc, eps_iz=iz)
+
+
+def test_elastic_collision_conserves_energy_and_momentum():
+    """Elastic electron-atom collision as two-body kinematics, target at rest: with the recoil
+    V' = (m/M)(v - v'), kinetic energy and momentum are conserved to round-off, and the speed in the
+    centre-of-mass frame is unchanged."""
+    M = 4.002602 * I.AMU
+    g = _forced_gas(M, 0, 1e-10)
+    d = I.discharge(n_cells=64, p_Pa=30.0, steps_per_period=400)
+    o = O.Oracle(g, d, "f64", load=False)
+    o.set_field(np.zeros(65))
+    rng = np.random.default_rng(9)
+    n = 20000
+    st = I.energy_state(rng, n, 64, 1.0, 150.0, I.M_E)
+    st["c"][:] = 32
+    o.set_state(0, st)
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    assert o.counters()["collisions_e"][0] == n
+    out = o.get_state(0)
+    v = np.stack([st["vx"], st["vy"], st["vz"]], 1)
+    vp = np.stack([out["vx"], out["vy"], out["vz"]], 1)
+    Vp = (I.M_E / M) * (v - vp)
+    ke0 = 0.5 * I.M_E * (v ** 2).sum(1)
+    ke1 = 0.5 * I.M_E * (vp ** 2).sum(1) + 0.5 * M * (Vp ** 2).sum(1)
+    assert np.max(np.abs(ke1 - ke0) / ke0) < 1e-12
+    beta = I.M_E / (I.M_E + M)
+    vcm = beta * v
+    assert np.allclose(np.linalg.norm(vp - vcm, axis=1), (1 - beta) * np.linalg.norm(v, axis=1), rtol=1e-13)
+    # isotropic scattering (section 'PIC/MCC simulation procedure'): directions uniform on the sphere
+    u = (vp - vcm) / np.linalg.norm(vp - vcm, axis=1)[:, None]
+    assert stats.kstest(u[:, 2], "uniform", args=(-1, 2)).pvalue > 1e-4
+    assert np.all(np.abs(u.mean(0)) < 5 / math.sqrt(3 * n))
+
+
+def test_excitation_loses_exactly_the_threshold():
+    M = 4.002602 * I.AMU
+    eth = 19.8
+    g = _forced_gas(M, 1, 1e-10, eps_th=eth)
+    o = O.Oracle(g, I.discharge(n_cells=64), "f64", load=False)
+    o.set_field(np.zeros(65))
+    rng = np.random.default_rng(10)
+    n = 10000
+    st = I.energy_state(rng, n, 64, eth + 0.5, 150.0, I.M_E)
+    st["c"][:] = 32
+    o.set_state(0, st)
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    assert o.counters()["collisions_e"][1] == n
+    out = o.get_state(0)
+    e0 = 0.5 * I.M_E * (st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2) / I.E_CH
+    e1 = 0.5 * I.M_E * (out["vx"] ** 2 + out["vy"] ** 2 + out["vz"] ** 2) / I.E_CH
+    assert np.max(np.abs((e0 - e1) - eth)) < 1e-11 * np.max(e0)
+
+
+def test_ionization_shares_remaining_energy_equally():
+    """Ionization (section 'PIC/MCC simulation procedure'): the energy left after the threshold is
+    split equally between the two electrons; one ion is born per event, at the parent's position."""
+    M = 4.002602 * I.AMU
+    eiz = 24.6
+    g = _forced_gas(M, 2, 1e-10, eps_th=eiz)
+    o = O.Oracle(g, I.discharge(n_cells=64), "f64", load=False)
+    o.set_field(np.zeros(65))
+    rng = np.random.default_rng(12)
+    n = 8000
+    st = I.energy_state(rng, n, 64, eiz + 1.0, 200.0, I.M_E)
+    st["c"][:] = 32
+    o.set_state(0, st)
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    assert o.counters()["collisions_e"][3] == n
+    out = o.get_state(0)
+    assert out["c"].size == 2 * n
+    e0 = 0.5 * I.M_E * (st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2) / I.E_CH
+    e = 0.5 * I.M_E * (out["vx"] ** 2 + out["vy"] ** 2 + out["vz"] ** 2) / I.E_CH
+    e1, e2 = e[0::2], e[1::2]     # parent, then its secondary
+    assert np.max(np.abs(e1 + e2 - (e0 - eiz))) < 1e-11 * np.max(e0)
+    assert np.max(np.abs(e1 - e2)) < 1e-11 * np.max(e0)
+    ions = o.get_state(1)
+    assert ions["c"].size == 1 + n
+    born = {k: v[1:] for k, v in ions.items()}
+    # the newborn ion starts at the parent's position and drifts with its thermal velocity
+    d = I.discharge(n_cells=64)
+    shift = (born["c"] + born["f"]) - (st["c"] + st["f"])
+    assert np.allclose(shift, born["vz"] * d.dt_s / (d.gap_m / 64), rtol=1e-6, atol=1e-12)
+    sig_n = math.sqrt(I.K_B * 300.0 / M)
+    assert abs(np.std(born["vx"]) / sig_n - 1) < 5 / math.sqrt(2 * n)
+
+
+def test_ion_isotropic_and_backward_elastic_conserve():
+    """Ion-atom elastic processes (Table 'reactions'), equal masses, target from the Maxwellian of the
+    gas: isotropic scattering conserves momentum and energy of the pair; backward scattering swaps
+    the two velocities. The target velocity is recomputed here from its random stream."""
+    M = 39.948 * I.AMU
+    n_pts, de = 4001, 1e-2
+    z = np.zeros(n_pts)
+    gr = np.sqrt(4 * I.E_CH * np.maximum(np.arange(n_pts) * de, 1e-9) / M)
+    for col in (0, 1):
+        si = [z, z]
+        si[col] = 1e-8 / gr
+        g = _gas_custom(M, n_pts, de, [z, z, z], si)
+        d = I.discharge(n_cells=64, p_Pa=1000.0, seed=99)
+        o = O.Oracle(g, d, "f64", load=False)
+        o.set_field(np.zeros(65))
+        rng = np.random.default_rng(13 + col)
+        n = 5000
+        st = I.energy_state(rng, n, 64, 0.5, 20.0, M)
+        st["c"][:] = 32
+        o.set_state(1, st)
+        o.set_state(0, I.speed_state(rng, 1, 64, 0.0))
+        o.sweep()
+        assert o.counters()["collisions_i"][col] == n
+        out = o.get_state(1)
+        sig_n = math.sqrt(I.K_B * 300.0 / M)
+        vn = np.zeros((n, 3))
+        for k in range(n):
+            q = O.philox([k, 0, (1 << 8) | 1, 0], [99, 0])
+            a0, a1 = O.box_muller(O.uniform(q[0]), O.uniform(q[1]))
+            a2, _ = O.box_muller(O.uniform(q[2]), O.uniform(q[3]))
+            vn[k] = sig_n * np.array([a0, a1, a2], dtype=np.float64)
+        v = np.stack([st["vx"], st["vy"], st["vz"]], 1)
+        vp = np.stack([out["vx"], out["vy"], out["vz"]], 1)
+        if col == 1:
+            assert np.allclose(vp, vn, rtol=0, atol=1e-9)
+        else:
+            Vp = v + vn - vp
+            e0 = (v ** 2).sum(1) + (vn ** 2).sum(1)
+            e1 = (vp ** 2).sum(1) + (Vp ** 2).sum(1)
+            assert np.max(np.abs(e1 - e0) / e0) < 1e-12
+
+
+def test_drift_velocity_maxwell_molecules():
+    """Constant nu, isotropic elastic scattering off infinitely heavy atoms, uniform field: the
+    scheme's mean stored velocity obeys E[v*] = a dt (2 - p) / (2 p), p = 1 - exp(-nu dt) (one step
+    of the recursion), which tends to the Maxwell-molecule drift a / nu = qE/(m nu) as nu dt -> 0."""
+    M = 1e7 * I.AMU
+    k_el = 1.4e-13
+    g = X.constant_nu(k_el, M, eps_max_eV=400.0, de_eV=1e-2)
+    d = I.discharge(n_cells=64, gap_m=1.0, p_Pa=30.0, steps_per_period=int(1 / (13.56e6 * 2e-10)))
+    dt = d.dt_s
+    o = O.Oracle(g, d, "f64", load=False)
+    E0 = -1000.0
+    o.set_field(np.full(65, E0))
+    a = (-I.E_CH / I.M_E) * E0
+    rng = np.random.default_rng(14)
+    n = 100_000
+    o.set_state(0, I.speed_state(rng, n, 64, 3e5))
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    means = []
+    for k in range(150):
+        o.step_index = k
+        o.sweep()
+        if k >= 50:
+            means.append(o.get_state(0)["vz"].mean())
+    assert o.count(0) == n
+    n_gas = d.p_Pa / (I.K_B * d.T_gas_K)
+    nu = n_gas * k_el
+    p = -math.expm1(-nu * dt)
+    vd_scheme = a * dt * (2 - p) / (2 * p)
+    got = float(np.mean(means))
+    assert abs(got / vd_scheme - 1) < 0.01
+    assert abs(vd_scheme / (a / nu) - 1) < nu * dt
+
+
+def test_growth_with_zero_threshold_ionization():
+    """Zero-threshold ionization at constant nu, no field: E[N_n] = N_0 (1 + P)^n, P = 1 - exp(-nu dt);
+    every ionization adds one ion."""
+    M = 4.002602 * I.AMU
+    k_iz = 1e-13
+    g = X.constant_nu(0.0, M, eps_max_eV=50.0, de_eV=1e-2, k_iz=k_iz)
+    d = I.discharge(n_cells=64, gap_m=1.0, p_Pa=30.0, steps_per_period=int(1 / (13.56e6 * 2e-10)))
+    o = O.Oracle(g, d, "f64", load=False)
+    o.set_field(np.zeros(65))
+    rng = np.random.default_rng(15)
+    n0, steps = 20000, 8
+    o.set_state(0, I.speed_state(rng, n0, 64, 1e6))
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    for k in range(steps):
+        o.step_index = k
+        o.sweep()
+    n_gas = d.p_Pa / (I.K_B * d.T_gas_K)
+    P = -math.expm1(-n_gas * k_iz * d.dt_s)
+    m = 1 + P
+    mean = n0 * m ** steps
+    var = n0 * P * (1 - P) * m ** (steps - 1) * (m ** steps - 1) / (m - 1)
+    ne = o.count(0)
+    assert abs(ne - mean) <= 5 * math.sqrt(var)
+    assert o.count(1) - 1 == ne - n0
+    assert o.counters()["collisions_e"][3] == ne - n0
+
+
+# --------------------------------------------------------------------------- walls, load, moments, sort
+
+def test_wall_flux_one_sided_maxwellian():
+    """Full absorption at the electrodes: the particle flux onto a wall from a uniform field-free
+    Maxwellian is n v_th / 4, v_th = sqrt(8 kT / (pi m)) (the 1/4 v_th term of Eq. 'BCparticles')."""
+    N, gap = 64, 0.025
+    d = I.discharge(n_cells=N, gap_m=gap)
+    o = O.Oracle(_no_collision_gas(), d, "f64", load=False)
+    o.set_field(np.zeros(N + 1))
+    T = 2.0
+    sig = math.sqrt(I.E_CH * T / I.M_E)
+    dt = 1e-3 * gap / sig
+    d2 = I.discharge(n_cells=N, gap_m=gap, steps_per_period=int(round(1 / (13.56e6 * dt))))
+    dt = d2.dt_s
+    o = O.Oracle(_no_collision_gas(), d2, "f64", load=False)
+    o.set_field(np.zeros(N + 1))
+    rng = np.random.default_rng(16)
+    n = 2_000_000
+    o.set_state(0, I.maxwell_state(rng, n, N, sig))
+    o.set_state(1, I.maxwell_state(rng, 1, N, 0.0))
+    o.sweep()
+    ab = o.counters()["absorbed"][0]
+    vth = math.sqrt(8 * I.E_CH * T / (math.pi * I.M_E))
+    expect = (n / gap) * vth / 4 * dt
+    for side in (0, 1):
+        assert abs(ab[side] - expect) <= 5 * math.sqrt(expect) + 1e-3 * expect
+
+
+def test_load_positions_and_velocities():
+    """Homogeneous quasi-neutral start (section 'Boundary conditions and initial values'): uniform
+    positions, Maxwellian velocities at T_e0 and T_i0."""
+    d = I.discharge(n_cells=128, n_e0=30000, n_i0=30000, V_rf_V=0.0, T_e0_eV=2.0, T_i0_K=300.0)
+    o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=True)
+    for sp, sig in ((0, math.sqrt(I.E_CH * 2.0 / I.M_E)), (1, math.sqrt(I.K_B * 300 / (4.002602 * I.AMU)))):
+        st = o.get_state(sp)
+        z = (st["c"] + st["f"]) / 128
+        assert stats.kstest(z, "uniform").pvalue > 1e-4
+        assert stats.kstest(st["vx"] / sig, "norm").pvalue > 1e-4
+        assert stats.kstest(st["vy"] / sig, "norm").pvalue > 1e-4
+
+
+def test_moments_of_uniform_load():
+    """Density moments integrate to w N exactly (charge conservation with half-cell wall volumes) and
+    the mean energy of a 2 eV Maxwellian is 3 eV."""
+    n = 200_000
+    d = I.discharge(n_cells=128, n_e0=n, n_i0=n, V_rf_V=0.0, T_e0_eV=2.0, n_init_m3=1e14,
+                    steps_per_period=100000)
+    o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=True)
+    o.step(1)
+    m = o.moments()
+    dx = d.gap_m / d.n_cells
+    V = np.full(d.n_cells + 1, dx)
+    V[0] = V[-1] = dx / 2
+    w = d.w_e
+    absorbed = sum(m["absorbed"][0])
+    assert np.sum(m["n_e"] * V) == pytest.approx(w * (n - absorbed + (o.count(0) - n + absorbed)), rel=1e-12)
+    Q = m["mean_eps"]
+    # energy moment at (x_n, v_n) of the first step = the loaded velocities
+    st_ne = m["n_e"]
+    mean_eps = np.sum(Q * st_ne * V) / np.sum(st_ne * V)
+    assert abs(mean_eps - 3.0) < 5 * math.sqrt(1.5) * 2.0 / math.sqrt(n) + 0.01
+
+
+def test_stable_sort_by_cell():
+    d = I.discharge(n_cells=64, n_e0=5000, n_i0=5000, V_rf_V=100.0)
+    o = O.Oracle(X.he_like(eps_max_eV=100, de_eV=1e-2), d, "f64", load=True)
+    o.sweep()
+    before = [o.get_state(s) for s in (0, 1)]
+    o.sort()
+    for s in (0, 1):
+        after = o.get_state(s)
+        perm = np.argsort(before[s]["c"], kind="stable")
+        for k in ("c", "f", "vx", "vy", "vz"):
+            assert np.array_equal(after[k], before[s][k][perm])
+
+
+def test_secondary_emission_count_is_binomial():
+    """Added option (not in the paper): each absorbed ion emits an electron with probability gamma."""
+    M = 4.002602 * I.AMU
+    d = I.discharge(n_cells=32, gamma_see=0.3, steps_per_period=400)
+    o = O.Oracle(_no_collision_gas(M), d, "f64", load=False)
+    o.set_field(np.zeros(33))
+    rng = np.random.default_rng(17)
+    n = 20000
+    dx = d.gap_m / 32
+    st = {"c": np.where(np.arange(n) % 2 == 0, 0, 31).astype(np.int32), "f": rng.uniform(0, 1, n),
+          "vx": np.zeros(n), "vy": np.zeros(n), "vz": np.zeros(n)}
+    st["vz"] = np.where(st["c"] == 0, -1.0, 1.0) * 3 * dx / d.dt_s
+    o.set_state(1, st)
+    o.set_state(0, I.speed_state(rng, 1, 32, 0.0))
+    o.sweep()
+    c = o.counters()
+    ab = c["absorbed"][1][0] + c["absorbed"][1][1]
+    assert ab == n
+    k = c["see_emitted"]
+    assert abs(k - 0.3 * n) <= 5 * math.sqrt(0.3 * 0.7 * n)
+    e = o.get_state(0)
+    born = {kk: v[1:] for kk, v in e.items()}
+    assert born["c"].size == k
+    left = born["c"] == 0
+    assert np.all(born["vz"][left] > 0) and np.all(born["vz"][~left] < 0)
+    assert np.all(born["f"][left] == 0.0)
+
+
+def test_f32_build_runs_and_matches_physics_build_statistically():
+    """The decision-precision build takes the same steps; after a short run its moments agree with the
+    FP64 build within the seed spread."""
+    d = I.discharge(n_cells=64, n_e0=20000, n_i0=20000, V_rf_V=150.0, n_init_m3=4e14, steps_per_period=400)
+    g = X.he_like(eps_max_eV=200, de_eV=1e-2)
+    o64 = O.Oracle(g, d, "f64", sort_every=1)
+    o32 = O.Oracle(g, d, "f32", sort_every=1)
+    o64.step(100)
+    o32.step(100)
+    n64, n32 = o64.count(0), o32.count(0)
+    assert abs(n64 - n32) < 0.05 * n64
+    m64, m32 = o64.moments(), o32.moments()
+    rel = np.linalg.norm(m64["n_i"] - m32["n_i"]) / np.linalg.norm(m64["n_i"])
+    assert rel < 0.05
