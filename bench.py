@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark of the PIC/MCC step on one GB300 (or N independent GPUs under torchrun).
+
+Workload: Ar-like gas, 10 Pa, 2.5 cm gap, 300 V at 13.56 MHz, 512 cells, 2000 steps per rf
+period, 1e6 electrons + 1e6 ions loaded uniform/Maxwellian (synthetic cross sections). One
+benchmark step = one full PIC/MCC time step (sweep: gather, Verlet, MCC, walls, compaction,
+deposit; births appended; Poisson; moments; the periodic cell sort when due).
+
+The particle store (40 MB) would fit in L2, so L2 is flushed (a 256 MB write) before every
+timed step, outside the timed region; each step is timed with CUDA events on the library's
+stream (the torch stream handed to it). Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s/GPU FP32 vs FP64 path; rf periods to steady state warm vs cold"
+UNIT = "particle-steps/s"
+BYTES_PER_PS = {"fp32": 40, "fp64": 72}   # algorithmic HBM bytes per particle-step (read + write)
+
+
+def workload():
+    from paper_1608_04601_gb300.workloads import c2
+    return c2()
+
+
+def gas_for(d):
+    from paper_1608_04601_gb300 import xsections as X
+    return X.by_name(d.gas, eps_max_eV=d.eps_max_eV, de_eV=d.de_eV)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pic_kernels.cu", "pic_device.cuh", "pic_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1608_04601_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(prec: str):
+    """DRAM bytes per particle-step of the sweep from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    e = j.get(prec)
+    if not e or e.get("source_hash") != sweep_source_hash():
+        return None
+    return e
+
+
+class Clocks:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_1608_04601_gb300 import pic
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    d0 = workload()
+    d = d0.scaled(seed=d0.seed + rank, discharge_id=rank)
+    gas = gas_for(d)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def measure(prec: str, steps: int, warmup: int, sort_every: int):
+        sim = pic.Simulation(gas, d, seed=d.seed, precision=prec, sort_every=sort_every, stream="torch",
+                             block=args.block, ppt=args.ppt)
+        sim.step(warmup)
+        sim.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        counts = []
+        sim.sweep_timing(True)
+        torch.cuda.synchronize()
+        with Clocks(dev) as clk:
+            for k in range(steps):
+                counts.append(sim.count(0, 0) + sim.count(0, 1))
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                sim.step(1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        sim.sync()
+        sweep_ms, launches = sim.sweep_timing(False)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = sum(step_ms)
+        ps = float(sum(counts))
+        out = {"ps": ps, "total_ms": total_ms, "sweep_ms": sweep_ms, "sweep_launches": launches,
+               "clocks": clk.summary(), "counts": (counts[0], counts[-1])}
+        # kernels launched per step: sweep + finalize, and the 4 sort kernels when a sort is due
+        step0 = sim.step_index - steps
+        sorts = sum(1 for n in range(step0 + 1, step0 + steps + 1) if sort_every > 0 and n % sort_every == 0)
+        out["gpu_launches"] = 2 * steps + 4 * sorts
+        sim.close()
+        return out
+
+    def measure_e2e(prec: str, steps: int, sort_every: int):
+        """Through the public API with host buffers: upload the state, one step, read the state and
+        the moments back; host wall clock."""
+        import numpy as np
+        sim = pic.Simulation(gas, d, seed=d.seed, precision=prec, sort_every=sort_every, stream="torch",
+                             block=args.block, ppt=args.ppt)
+        sim.step(2)
+        host = [sim.get_state(0, sp) for sp in (0, 1)]
+        rb = 4 if prec == "fp32" else 8
+        h2d = sum(h["c"].size * (4 + 4 * rb) for h in host)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ps = 0
+        d2h = 0
+        for _ in range(steps):
+            for sp in (0, 1):
+                sim.set_state(0, sp, host[sp])
+            sim.step(1)
+            host = [sim.get_state(0, sp) for sp in (0, 1)]
+            m = sim.moments(0)
+            ps += sum(h["c"].size for h in host)
+            d2h += sum(h["c"].size * (4 + 4 * rb) for h in host) + 3 * 8 * m["n_e"].size
+        dt = time.perf_counter() - t0
+        sim.close()
+        return {"value": ps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h / steps)}
+
+    sort_every = args.sort_every
+    main = measure("fp32", args.steps, args.warmup, sort_every)
+    fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
+    e2e = measure_e2e("fp32", max(3, min(10, args.steps)), sort_every)
+
+    # aggregate over ranks
+    total_ms = main["total_ms"]
+    ps = main["ps"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([ps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        total_ms, ps = float(t.item()), float(p.item())
+    value = ps / (total_ms * 1e-3)
+
+    peak, peak_note = peaks()
+    launch_ps = main["ps"] / max(1, main["sweep_launches"])
+    bytes_per_launch = BYTES_PER_PS["fp32"] * launch_ps
+    avg_sweep_s = main["sweep_ms"] * 1e-3 / max(1, main["sweep_launches"])
+    achieved = bytes_per_launch / avg_sweep_s / 1e9
+    tr = recorded_traffic("fp32")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tr["dram_bytes_per_particle"] * launch_ps) if tr else None,
+                "kernel": "k_sweep<float,%d,%d>" % (args.block, args.ppt),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_note,
+                "avg_launch_ms": avg_sweep_s * 1e3,
+                "sweep_share_of_step": main["sweep_ms"] / main["total_ms"]}
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": d0.name, "cells": d0.n_cells, "particles_per_species": d0.n_e0,
+                      "steps_per_period": d0.steps_per_period, "sort_every": sort_every,
+                      "block": args.block, "ppt": args.ppt, "parallelism": f"replicas{world}" if world > 1 else "1gpu",
+                      "l2": "flushed (256 MB write) before every timed step"},
+           "roofline": roofline,
+           "fp64_path": {"value": fp64["ps"] / (fp64["total_ms"] * 1e-3), "unit": UNIT,
+                         "ms_per_step": fp64["total_ms"] / max(1, max(4, args.steps // 2)),
+                         "sweep_gbs": BYTES_PER_PS["fp64"] * fp64["ps"] / (fp64["sweep_ms"] * 1e-3) / 1e9,
+                         "bytes_per_particle_step": BYTES_PER_PS["fp64"]},
+           "e2e": e2e, "clocks": main["clocks"], "gpu_launches": main["gpu_launches"]}
+    return res
+
+
+def run_cpu_baseline(args):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of the same workload."""
+    from oracle import oracle as O
+    d = workload()
+    gas = gas_for(d)
+    t0 = time.perf_counter()
+    o = O.Oracle(gas, d, "f64", sort_every=args.sort_every)
+    t_load = time.perf_counter() - t0
+    n_steps = args.cpu_steps
+    n0 = o.count(0) + o.count(1)
+    t0 = time.perf_counter()
+    ps = 0
+    for _ in range(n_steps):
+        ps += o.count(0) + o.count(1)
+        o.step(1)
+    dt = time.perf_counter() - t0
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d.name}: full load ({n0} particles, {t_load:.1f} s), {n_steps} FP64 steps, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sort-every", type=int, default=4)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--ppt", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from oracle import oracle as O
+        O.build()
+        d = workload()
+        gas = gas_for(d)
+        o = O.Oracle(gas, d, "f64", sort_every=args.sort_every)
+        o.step(args.warmup)
+        ps = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ps += o.count(0) + o.count(1)
+            o.step(1)
+        dt = time.perf_counter() - t0
+        v = ps / dt
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": d.name, "sort_every": args.sort_every},
+                          "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                           "sample": f"{d.name}, full population, {args.steps} FP64 steps"},
+                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+        dist.barrier()
+    import __graft_entry__ as g
+    g.build()
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = run_cpu_baseline(args)
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

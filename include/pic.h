@@ -1,0 +1,229 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) 1d3v electrostatic PIC/MCC library.
+ *
+ * The library advances electrons and one positive ion species between two
+ * parallel plates, the kinetic method of Becker, Kaehlert, Sun, Bonitz,
+ * Loffhagen, arXiv:1608.04601, section "PIC/MCC simulation procedure":
+ *   - superparticles of constant weight, one space coordinate and three
+ *     velocity components (1d3v);
+ *   - cloud-in-cell charge assignment and field interpolation;
+ *   - Eq. (poisson) on N cells with phi(0,t) = V0 sin(2 pi f t), phi(d,t) = 0
+ *     (section "Boundary conditions and initial values"), second-order
+ *     central differences;
+ *   - velocity Verlet push; collisions act on the synchronised velocity;
+ *   - full absorption at both electrodes (optional secondary electrons);
+ *   - null-collision Monte Carlo collisions with the processes of Table
+ *     "reactions": electron elastic, excitation (1 or 2 levels), ionization
+ *     (remaining energy shared equally); ion isotropic and backward elastic.
+ *
+ * Conventions for every entry point:
+ *   - Return a pic_status; PIC_OK is 0. No C++ exception crosses the ABI.
+ *     pic_last_error() gives a text for the last failure of a context.
+ *   - Pointers named host_* or documented "host" are host memory owned by
+ *     the caller, read or written before the call returns. The library owns
+ *     all device memory it allocates; nothing is kept of caller pointers
+ *     after a call returns.
+ *   - Work is enqueued on the context's CUDA stream (the caller's, if given
+ *     in pic_options.cuda_stream). Calls that return host data synchronise
+ *     that stream first; pic_sync() synchronises and reports errors that the
+ *     device raised (capacity overflow, look-back timeout, non-finite state).
+ *   - Species index 0 = electrons, 1 = ions. Discharge index counts from 0 in
+ *     the order given to pic_batch_create.
+ *   - Particle state is structure-of-arrays: int32 cell c in [0, N), in-cell
+ *     offset f in [0, 1), velocities vx, vy, vz in m/s, with z = (c + f) d/N.
+ *     The stored v_z is the Verlet half-step velocity v_n + (q/m) E_n dt/2.
+ *     Real arrays are float (PIC_FP32) or double (PIC_FP64), per context.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = -1,        /* invalid argument (sizes, NULL, ranges)          */
+    PIC_ERR_CUDA = -2,       /* a CUDA call failed                              */
+    PIC_ERR_CAPACITY = -3,   /* a particle or birth buffer would overflow       */
+    PIC_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up              */
+    PIC_ERR_TABLE = -5,      /* cross-section table rejected (negative, NaN)    */
+    PIC_ERR_NONFINITE = -6,  /* a non-finite particle coordinate was met        */
+    PIC_ERR_STATE = -7       /* call not valid in the context's current state   */
+} pic_status;
+
+enum { PIC_ELECTRONS = 0, PIC_IONS = 1 };
+enum { PIC_FP32 = 0, PIC_FP64 = 1 };
+enum { PIC_MAX_DISCHARGES = 64, PIC_MAX_CELLS = 4096 };
+
+/* Background gas with its cross sections (Table "reactions"), tabulated on
+ * eps_k = k de_eV, k = 0..n_pts-1 (host arrays, copied at create time):
+ *   sigma_e[k*(2+n_exc) + j] m^2, lab energy: j = 0 elastic, 1..n_exc
+ *                                  excitation levels, 1+n_exc ionization;
+ *   sigma_i[k*2 + j] m^2, centre-of-mass energy: j = 0 isotropic elastic,
+ *                                  1 backward elastic (charge exchange).   */
+typedef struct {
+    double mass_kg;
+    int32_t n_exc;           /* 1 or 2                                      */
+    int32_t n_pts;           /* >= 2, <= 2^24                               */
+    double de_eV;
+    double eps_exc_eV[2];
+    double eps_iz_eV;
+    const double* sigma_e;
+    const double* sigma_i;
+} pic_gas;
+
+/* Superparticle weights, initial population and store capacity. */
+typedef struct {
+    double w_e, w_i;         /* physical particles per superparticle per m^2 */
+    int64_t n_e0, n_i0;      /* loaded at create (uniform, Maxwellian)       */
+    int64_t capacity_e;      /* maximum superparticles held per species      */
+    int64_t capacity_i;
+    double T_e0_eV, T_i0_K;  /* temperatures of the initial Maxwellians      */
+    double gamma_see;        /* secondary electrons per absorbed ion (0: off) */
+    int32_t steps_per_period;/* rf period in steps (diagnostic bookkeeping)  */
+    int32_t reserved;
+} pic_weights;
+
+/* One discharge of a batch. */
+typedef struct {
+    int32_t gas;             /* index into the gas array                    */
+    int32_t n_cells;         /* N, 1..PIC_MAX_CELLS                         */
+    double gap_m, p_Pa, T_gas_K, f_rf_Hz, V_rf_V, dt_s;
+    pic_weights weights;
+    uint32_t discharge_id;   /* fourth word of every random-stream counter  */
+    int32_t reserved;
+} pic_discharge;
+
+typedef struct {
+    int32_t precision;       /* PIC_FP32 (default) or PIC_FP64                */
+    int32_t sort_every;      /* 0: never sort; K > 0: stable sort by cell    */
+                             /* after every step n with (n+1) % K == 0       */
+    int32_t block;           /* sweep threads per CTA: 128, 256 (default)    */
+    int32_t ppt;             /* sweep particles per thread: 2, 4 (default), 8 */
+    int32_t ctas_per_sm;     /* persistent sweep CTAs per SM (0: occupancy)  */
+    int32_t use_graph;       /* 1: replay pic_step in CUDA graphs of one rf  */
+                             /* period (requires sort_every | steps/period)  */
+    void* cuda_stream;       /* cudaStream_t to enqueue on; NULL = own stream */
+    int32_t load;            /* 1 (default): load n_e0 / n_i0 at create      */
+    int32_t reserved;
+} pic_options;
+
+/* Fills *opt with the defaults documented above. */
+void pic_default_options(pic_options* opt);
+
+/* Creates a batch of independent discharges that advance together (one
+ * sweep launch and one field launch per step for all of them). seed keys
+ * every random stream (Philox4x32-10). opt may be NULL (defaults).
+ * On PIC_OK, *out owns all device memory; release it with pic_destroy.   */
+pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int32_t n_gases,
+                            const pic_discharge* discharges, int32_t n_discharges,
+                            uint64_t seed, const pic_options* opt);
+
+/* One discharge: gas and its tables, gap, pressure, gas temperature, rf
+ * frequency and amplitude, cells, time step, weights, seed.              */
+pic_status pic_create(pic_ctx** out, const pic_gas* gas, double gap_m, double p_Pa,
+                      double T_gas_K, double f_rf_Hz, double V_rf_V, int32_t n_cells,
+                      double dt_s, const pic_weights* weights, uint64_t seed,
+                      const pic_options* opt);
+
+/* Enqueues n_steps full time steps: sweep (gather, half kick, MCC, half
+ * kick, drift, walls, compaction, deposit), births appended, periodic sort,
+ * Poisson at t_{n+1}, moments accumulated. Asynchronous.                  */
+pic_status pic_step(pic_ctx* ctx, int64_t n_steps);
+
+/* The parts of one step, for tests and custom drivers:
+ *   pic_sweep  -- sweep of all discharges at the current step with the
+ *                 current node field, births appended, counts updated;
+ *   pic_sort   -- stable counting sort of every store by cell;
+ *   pic_solve  -- charge density, Poisson at t_{n+1}, node field, moments
+ *                 accumulated, step counter advanced.                     */
+pic_status pic_sweep(pic_ctx* ctx);
+pic_status pic_sort(pic_ctx* ctx);
+pic_status pic_solve(pic_ctx* ctx);
+
+/* Waits for the stream; returns the first device-raised error, if any.   */
+pic_status pic_sync(pic_ctx* ctx);
+
+/* Cycle-averaged moments of one discharge since the last reset (host
+ * arrays of N+1 nodes, caller-owned, each may be NULL).                   */
+typedef struct {
+    double* n_e;             /* electron density, m^-3                       */
+    double* n_i;             /* ion density, m^-3                            */
+    double* mean_eps;        /* mean electron energy, eV                     */
+    int64_t steps;           /* steps accumulated                            */
+    int64_t count[2];        /* superparticles now, per species              */
+    double absorbed[2][2];   /* superparticles absorbed [species][electrode] */
+    double flux[2][2];       /* particle flux to [species][electrode], m^-2 s^-1 */
+    double surface_charge;   /* eps0 E(0) at the last solve, C m^-2          */
+} pic_moments_t;
+pic_status pic_moments(pic_ctx* ctx, int32_t discharge, pic_moments_t* out);
+pic_status pic_reset_moments(pic_ctx* ctx);
+
+void        pic_destroy(pic_ctx* ctx);         /* NULL-safe                 */
+const char* pic_last_error(const pic_ctx* ctx);
+const char* pic_status_string(pic_status s);
+
+/* ---- state access (host buffers; synchronous) --------------------------- */
+pic_status pic_get_count(pic_ctx* ctx, int32_t d, int32_t species, int64_t* n);
+/* Copies the store of (d, species) into host arrays of at least `cap`
+ * entries; *n receives the count. Real arrays per the context precision. */
+pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t species, int64_t cap, int32_t* c,
+                         void* f, void* vx, void* vy, void* vz, int64_t* n);
+pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t species, int64_t n, const int32_t* c,
+                         const void* f, const void* vx, const void* vy, const void* vz);
+/* Node field used by the gather (N+1 reals); FP64 potential and field.   */
+pic_status pic_get_field(pic_ctx* ctx, int32_t d, void* E, double* E64, double* phi);
+pic_status pic_set_field(pic_ctx* ctx, int32_t d, const void* E);
+/* 64-bit fixed-point CIC deposits of the last sweep (2^32 per particle). */
+pic_status pic_get_deposit(pic_ctx* ctx, int32_t d, int32_t species, int64_t* D);
+pic_status pic_set_deposit(pic_ctx* ctx, int32_t d, int32_t species, const int64_t* D);
+/* Electron energy moment of the last sweep at (x_n, v_n), 2^-16 eV units. */
+pic_status pic_get_energy_deposit(pic_ctx* ctx, int32_t d, int64_t* Q);
+pic_status pic_get_step(pic_ctx* ctx, int64_t* step);
+pic_status pic_set_step(pic_ctx* ctx, int64_t step);
+
+/* Event counters since creation. */
+typedef struct {
+    int64_t absorbed[2][2];
+    int64_t collisions_e[4]; /* elastic, excitation 1, excitation 2, ionization */
+    int64_t collisions_i[2]; /* isotropic, backward                          */
+    int64_t null_inelastic;  /* inelastic process selected below threshold   */
+    int64_t see_emitted;
+    int64_t candidates[2];
+    int64_t table_clamped[2];
+} pic_counters;
+pic_status pic_get_counters(pic_ctx* ctx, int32_t d, pic_counters* out);
+
+/* Derived per-discharge constants (host FP64 values before rounding). */
+typedef struct {
+    double dx, n_gas, kmax_e, kmax_i, numax_e, numax_i, pnull_e, pnull_i;
+    uint32_t thr_e, thr_i;
+    double K_e, K_i, dtdx, kappa_e, kappa_i, kappa_E, beta_e, omb_e;
+    double de2_exc[2], de2_iz, sig_n, sig_e0, sig_i0, sig_see, sig_see_n;
+} pic_derived;
+pic_status pic_get_derived(pic_ctx* ctx, int32_t d, pic_derived* out);
+/* Cumulative rate-coefficient tables of one gas: Te n_pts x 4, Ti n_pts x 2. */
+pic_status pic_get_tables(pic_ctx* ctx, int32_t gas, void* Te, void* Ti);
+
+/* Timing of the last pic_step call's sweep launches (CUDA events on the
+ * context stream): total milliseconds and launches.                       */
+pic_status pic_sweep_timing(pic_ctx* ctx, int32_t enable, double* total_ms, int64_t* launches);
+
+/* ---- self-checks of the device building blocks (host buffers) ---------- */
+/* Philox4x32-10 (Salmon et al., SC'11) on n counters (4 words each).      */
+pic_status pic_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
+/* Own log, sin(pi y), cos(pi y), Box-Muller and isotropic direction as used
+ * by the kernels, on n inputs.                                            */
+pic_status pic_debug_math(int64_t n, const float* x, const float* y, float* log_out,
+                          float* sin_out, float* cos_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,882 @@
+// pic_api.cu -- host runtime and C ABI (include/pic.h) of the PIC/MCC library.
+// Owns device memory, the stream, the per-discharge descriptors and the step
+// sequence (sweep -> finalize -> periodic sort), optionally replayed from CUDA
+// graphs of one rf period.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.h"
+#include "pic_launch.h"
+
+using namespace pic;
+
+#define H_E_CHARGE 1.602176634e-19
+#define H_M_ELEC 9.1093837015e-31
+#define H_K_BOLTZ 1.380649e-23
+#define H_TWO32 4294967296.0
+#define H_T_SEE_EV 2.0
+
+struct GasDev {
+    int n_pts, n_exc;
+    double de, mass;
+    void* Te;
+    void* Ti;
+    double kmax_e, kmax_i;
+};
+
+struct pic_ctx {
+    int fp64 = 0;
+    pic_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_disc = 0, n_gas = 0, max_N = 0;
+    unsigned long long seed = 0;
+    std::vector<pic_discharge> dis;
+    std::vector<GasDev> gas;
+    std::vector<pic_derived> der;
+    std::vector<Disc> hd;
+    Disc* d_discs = nullptr;
+    Ctl* d_ctl = nullptr;
+    unsigned long long *st_main = nullptr, *st_bagg = nullptr, *st_binc = nullptr;
+    unsigned* sort_hist = nullptr;
+    unsigned* sort_tot = nullptr;
+    long long* sort_hoff = nullptr;
+    std::vector<void*> allocs;
+    int cur = 0;
+    long long step = 0;
+    bool deposits_zero = true;
+    int sweep_grid = 0, num_sms = 0;
+    std::string err;
+    pic_counters cnt_at_reset[MAXD];
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t ev_used = 0;
+    // one-period graphs, keyed by (buffer parity at entry, step phase within the sort period)
+    struct GraphEntry {
+        int cur_in, phase, cur_out;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+};
+
+static pic_status fail(pic_ctx* c, pic_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+static pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, PIC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+static void* dalloc(pic_ctx* ctx, size_t bytes, cudaError_t* e) {
+    void* p = nullptr;
+    *e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (*e != cudaSuccess) return nullptr;
+    ctx->allocs.push_back(p);
+    *e = cudaMemsetAsync(p, 0, bytes ? bytes : 16, ctx->stream);
+    return p;
+}
+
+extern "C" void pic_default_options(pic_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = PIC_FP32;
+    o->sort_every = 0;
+    o->block = 256;
+    o->ppt = 4;
+    o->ctas_per_sm = 0;
+    o->use_graph = 0;
+    o->cuda_stream = nullptr;
+    o->load = 1;
+}
+
+extern "C" const char* pic_status_string(pic_status s) {
+    switch (s) {
+        case PIC_OK: return "ok";
+        case PIC_ERR_ARG: return "invalid argument";
+        case PIC_ERR_CUDA: return "CUDA error";
+        case PIC_ERR_CAPACITY: return "particle capacity exceeded";
+        case PIC_ERR_TIMEOUT: return "device wait timed out";
+        case PIC_ERR_TABLE: return "cross-section table rejected";
+        case PIC_ERR_NONFINITE: return "non-finite particle state";
+        case PIC_ERR_STATE: return "invalid call in current state";
+    }
+    return "unknown";
+}
+
+extern "C" const char* pic_last_error(const pic_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static uint32_t null_threshold(double numax, double dt, double* pnull) {
+    const double P = -expm1(-numax * dt);
+    *pnull = P;
+    double t = floor(P * H_TWO32);
+    if (t < 0.0) t = 0.0;
+    if (t > 4294967295.0) t = 4294967295.0;
+    return (uint32_t)t;
+}
+
+// Host FP64 derivation of the per-discharge constants (same expressions in the
+// documented order, so that the rounded values are reproducible).
+static void derive(const pic_discharge& d, const GasDev& g, const pic_gas& gi, pic_derived* o) {
+    const double M = g.mass, de = g.de, dt = d.dt_s;
+    o->dx = d.gap_m / (double)d.n_cells;
+    o->n_gas = d.p_Pa / (H_K_BOLTZ * d.T_gas_K);
+    o->K_e = (-H_E_CHARGE / H_M_ELEC) * (0.5 * dt);
+    o->K_i = (H_E_CHARGE / M) * (0.5 * dt);
+    o->dtdx = dt / o->dx;
+    o->kappa_e = 0.5 * H_M_ELEC / (H_E_CHARGE * de);
+    o->kappa_i = 0.25 * M / (H_E_CHARGE * de);
+    o->kappa_E = 0.5 * H_M_ELEC / H_E_CHARGE * 65536.0;
+    o->beta_e = H_M_ELEC / (H_M_ELEC + M);
+    o->omb_e = M / (H_M_ELEC + M);
+    for (int j = 0; j < 2; ++j) o->de2_exc[j] = 2.0 * H_E_CHARGE * (j < gi.n_exc ? gi.eps_exc_eV[j] : 0.0) / H_M_ELEC;
+    o->de2_iz = 2.0 * H_E_CHARGE * gi.eps_iz_eV / H_M_ELEC;
+    o->sig_n = sqrt(H_K_BOLTZ * d.T_gas_K / M);
+    o->sig_e0 = sqrt(H_E_CHARGE * d.weights.T_e0_eV / H_M_ELEC);
+    o->sig_i0 = sqrt(H_K_BOLTZ * d.weights.T_i0_K / M);
+    o->sig_see = sqrt(H_E_CHARGE * H_T_SEE_EV / H_M_ELEC);
+    o->sig_see_n = sqrt(2.0 * H_E_CHARGE * H_T_SEE_EV / H_M_ELEC);
+    o->kmax_e = g.kmax_e;
+    o->kmax_i = g.kmax_i;
+    o->numax_e = o->n_gas * o->kmax_e;
+    o->numax_i = o->n_gas * o->kmax_i;
+    o->thr_e = null_threshold(o->numax_e, dt, &o->pnull_e);
+    o->thr_i = null_threshold(o->numax_i, dt, &o->pnull_i);
+}
+
+template <typename T>
+static void fill_consts(Consts<T>& k, const pic_derived& o, const pic_discharge& d) {
+    k.K[0] = (T)o.K_e;
+    k.K[1] = (T)o.K_i;
+    k.dtdx = (T)o.dtdx;
+    k.kappa_e = (T)o.kappa_e;
+    k.kappa_i = (T)o.kappa_i;
+    k.kappa_E = (T)o.kappa_E;
+    k.beta = (T)o.beta_e;
+    k.omb = (T)o.omb_e;
+    k.de2_exc[0] = (T)o.de2_exc[0];
+    k.de2_exc[1] = (T)o.de2_exc[1];
+    k.de2_iz = (T)o.de2_iz;
+    k.sig_n = (T)o.sig_n;
+    k.sig_see = (T)o.sig_see;
+    k.sig_see_n = (T)o.sig_see_n;
+    k.kmax_e = (T)o.kmax_e;
+    k.kmax_i = (T)o.kmax_i;
+    k.gamma = (T)d.weights.gamma_see;
+    k.sig0[0] = (T)o.sig_e0;
+    k.sig0[1] = (T)o.sig_i0;
+}
+
+extern "C" void pic_destroy(pic_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& e : ctx->ev) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+static pic_status enqueue_sweep(pic_ctx* ctx);
+static pic_status enqueue_finalize(pic_ctx* ctx, int mode);
+static pic_status enqueue_sort(pic_ctx* ctx);
+
+extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int32_t n_gases,
+                                       const pic_discharge* dis, int32_t n_dis, uint64_t seed,
+                                       const pic_options* opt) {
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!gases || !dis || n_gases < 1 || n_dis < 1 || n_dis > MAXD) return PIC_ERR_ARG;
+    pic_ctx* ctx = new pic_ctx();
+    if (opt) ctx->opt = *opt;
+    else pic_default_options(&ctx->opt);
+    pic_options& o = ctx->opt;
+    if (o.block != 128 && o.block != 256) o.block = 256;
+    if (o.ppt != 2 && o.ppt != 4 && o.ppt != 8) o.ppt = 4;
+    if (o.precision != PIC_FP32 && o.precision != PIC_FP64) {
+        pic_destroy(ctx);
+        return PIC_ERR_ARG;
+    }
+    ctx->fp64 = o.precision == PIC_FP64;
+    ctx->seed = seed;
+    ctx->n_disc = n_dis;
+    ctx->n_gas = n_gases;
+    const size_t rsz = ctx->fp64 ? sizeof(double) : sizeof(float);
+    // validation
+    for (int i = 0; i < n_gases; ++i) {
+        const pic_gas& g = gases[i];
+        if (g.n_exc < 1 || g.n_exc > 2 || g.n_pts < 2 || g.n_pts > (1 << 24) || !(g.de_eV > 0) ||
+            !(g.mass_kg > 0) || !g.sigma_e || !g.sigma_i) {
+            pic_destroy(ctx);
+            return PIC_ERR_ARG;
+        }
+        const size_t ne = (size_t)g.n_pts * (2 + g.n_exc), ni = (size_t)g.n_pts * 2;
+        for (size_t k = 0; k < ne; ++k)
+            if (!(g.sigma_e[k] >= 0.0) || !std::isfinite(g.sigma_e[k])) {
+                pic_destroy(ctx);
+                return PIC_ERR_TABLE;
+            }
+        for (size_t k = 0; k < ni; ++k)
+            if (!(g.sigma_i[k] >= 0.0) || !std::isfinite(g.sigma_i[k])) {
+                pic_destroy(ctx);
+                return PIC_ERR_TABLE;
+            }
+    }
+    for (int i = 0; i < n_dis; ++i) {
+        const pic_discharge& d = dis[i];
+        const pic_weights& w = d.weights;
+        if (d.gas < 0 || d.gas >= n_gases || d.n_cells < 1 || d.n_cells > MAXN || !(d.gap_m > 0) || !(d.dt_s > 0) ||
+            !(d.p_Pa >= 0) || !(d.T_gas_K > 0) || w.n_e0 < 0 || w.n_i0 < 0 || w.capacity_e < w.n_e0 ||
+            w.capacity_i < w.n_i0 || w.capacity_e > (1ll << 30) - 1 || w.capacity_i > (1ll << 30) - 1 ||
+            !(w.gamma_see >= 0 && w.gamma_see <= 1)) {
+            pic_destroy(ctx);
+            return PIC_ERR_ARG;
+        }
+        ctx->max_N = std::max(ctx->max_N, d.n_cells);
+        ctx->dis.push_back(d);
+    }
+    // stream
+    if (o.cuda_stream) {
+        ctx->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            pic_status s = cuda_fail(ctx, e, "stream");
+            pic_destroy(ctx);
+            return s;
+        }
+        ctx->own_stream = true;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t ce;
+#define ALLOC(ptr, type, bytes)                                          \
+    do {                                                                 \
+        ptr = (type)dalloc(ctx, (bytes), &ce);                           \
+        if (ce != cudaSuccess) {                                         \
+            pic_status s_ = cuda_fail(ctx, ce, "allocation");            \
+            std::string m_ = ctx->err;                                   \
+            pic_destroy(ctx);                                            \
+            (void)m_;                                                    \
+            return s_;                                                   \
+        }                                                                \
+    } while (0)
+
+    // tables per gas
+    for (int i = 0; i < n_gases; ++i) {
+        const pic_gas& g = gases[i];
+        GasDev gd{};
+        gd.n_pts = g.n_pts;
+        gd.n_exc = g.n_exc;
+        gd.de = g.de_eV;
+        gd.mass = g.mass_kg;
+        const size_t ne = (size_t)g.n_pts * (2 + g.n_exc), ni = (size_t)g.n_pts * 2;
+        double *se = nullptr, *si = nullptr;
+        unsigned long long* km = nullptr;
+        if (cudaMalloc(&se, ne * 8) != cudaSuccess || cudaMalloc(&si, ni * 8) != cudaSuccess ||
+            cudaMalloc(&km, 16) != cudaSuccess) {
+            cudaFree(se);
+            cudaFree(si);
+            pic_destroy(ctx);
+            return PIC_ERR_CUDA;
+        }
+        cudaMemcpyAsync(se, g.sigma_e, ne * 8, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(si, g.sigma_i, ni * 8, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemsetAsync(km, 0, 16, ctx->stream);
+        ALLOC(gd.Te, void*, (size_t)g.n_pts * 4 * rsz);
+        ALLOC(gd.Ti, void*, (size_t)g.n_pts * 2 * rsz);
+        ce = launch_tables(ctx->fp64, g.n_pts, 2 + g.n_exc, g.de_eV, g.mass_kg, se, si, gd.Te, gd.Ti, km,
+                           ctx->stream);
+        unsigned long long kmh[2] = {0, 0};
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(kmh, km, 16, cudaMemcpyDeviceToHost, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        cudaFree(se);
+        cudaFree(si);
+        cudaFree(km);
+        if (ce != cudaSuccess) {
+            pic_status s = cuda_fail(ctx, ce, "tables");
+            pic_destroy(ctx);
+            return s;
+        }
+        std::memcpy(&gd.kmax_e, &kmh[0], 8);
+        std::memcpy(&gd.kmax_i, &kmh[1], 8);
+        ctx->gas.push_back(gd);
+    }
+
+    // look-back status words: one per sweep tile of the largest possible population
+    const long long tile = (long long)o.block * o.ppt;
+    long long max_tiles = 0;
+    for (auto& d : ctx->dis)
+        max_tiles += (d.weights.capacity_e + tile - 1) / tile + (d.weights.capacity_i + tile - 1) / tile + 2;
+    ALLOC(ctx->st_main, unsigned long long*, sizeof(unsigned long long) * max_tiles);
+    ALLOC(ctx->st_bagg, unsigned long long*, sizeof(unsigned long long) * max_tiles);
+    ALLOC(ctx->st_binc, unsigned long long*, sizeof(unsigned long long) * max_tiles);
+    // sort scratch: per store (cells x sort tiles) counts
+    {
+        std::vector<long long> hoff(2 * MAXD, 0);
+        long long acc = 0;
+        const long long st = sort_tile();
+        for (int i = 0; i < n_dis; ++i)
+            for (int sp = 0; sp < 2; ++sp) {
+                hoff[2 * i + sp] = acc;
+                const long long cap = sp ? ctx->dis[i].weights.capacity_i : ctx->dis[i].weights.capacity_e;
+                acc += (long long)ctx->dis[i].n_cells * ((cap + st - 1) / st + 1);
+            }
+        ALLOC(ctx->sort_hist, unsigned*, sizeof(unsigned) * (size_t)std::max(acc, 1ll));
+        ALLOC(ctx->sort_tot, unsigned*, sizeof(unsigned) * (size_t)(2 * MAXD) * MAXN);
+        ALLOC(ctx->sort_hoff, long long*, sizeof(long long) * 2 * MAXD);
+        cudaMemcpyAsync(ctx->sort_hoff, hoff.data(), sizeof(long long) * 2 * MAXD, cudaMemcpyHostToDevice,
+                        ctx->stream);
+    }
+
+    // per-discharge buffers and descriptors
+    for (int i = 0; i < n_dis; ++i) {
+        const pic_discharge& d = ctx->dis[i];
+        const GasDev& g = ctx->gas[d.gas];
+        pic_derived der{};
+        derive(d, g, gases[d.gas], &der);
+        ctx->der.push_back(der);
+        Disc D{};
+        D.N = d.n_cells;
+        D.n_exc = g.n_exc;
+        D.n_pts = g.n_pts;
+        D.gas = d.gas;
+        D.thr[0] = der.thr_e;
+        D.thr[1] = der.thr_i;
+        D.discharge_id = d.discharge_id;
+        D.steps_per_period = d.weights.steps_per_period;
+        D.dx = der.dx;
+        D.dt = d.dt_s;
+        D.V_rf = d.V_rf_V;
+        D.f_rf = d.f_rf_Hz;
+        D.w[0] = d.weights.w_e;
+        D.w[1] = d.weights.w_i;
+        D.has_see = d.weights.gamma_see > 0.0;
+        fill_consts<float>(D.cf, der, d);
+        fill_consts<double>(D.cd, der, d);
+        D.Te = g.Te;
+        D.Ti = g.Ti;
+        D.cap[0] = d.weights.capacity_e;
+        D.cap[1] = d.weights.capacity_i;
+        D.bcap = std::max(D.cap[0], D.cap[1]) / 8 + 4096;
+        const size_t rec = 4 * rsz;
+        for (int b = 0; b < 2; ++b)
+            for (int sp = 0; sp < 2; ++sp) {
+                ALLOC(D.c[b][sp], int32_t*, sizeof(int32_t) * (size_t)std::max(1ll, D.cap[sp]));
+                ALLOC(D.p[b][sp], void*, rec * (size_t)std::max(1ll, D.cap[sp]));
+            }
+        for (int sp = 0; sp < 2; ++sp) {
+            ALLOC(D.bc[sp], int32_t*, sizeof(int32_t) * (size_t)D.bcap);
+            ALLOC(D.bp[sp], void*, rec * (size_t)D.bcap);
+        }
+        const size_t N1 = (size_t)d.n_cells + 1;
+        ALLOC(D.E, void*, rsz * N1);
+        ALLOC(D.E64, double*, 8 * N1);
+        ALLOC(D.phi, double*, 8 * N1);
+        ALLOC(D.D[0], unsigned long long*, 8 * N1);
+        ALLOC(D.D[1], unsigned long long*, 8 * N1);
+        ALLOC(D.Q, unsigned long long*, 8 * N1);
+        ALLOC(D.Dprev, unsigned long long*, 8 * N1);
+        ALLOC(D.acc_D[0], double*, 8 * N1);
+        ALLOC(D.acc_D[1], double*, 8 * N1);
+        ALLOC(D.acc_Q, double*, 8 * N1);
+        ALLOC(D.acc_Dprev, double*, 8 * N1);
+        ALLOC(D.cnt, unsigned long long*, 8 * NCNT);
+        ctx->hd.push_back(D);
+        std::memset(&ctx->cnt_at_reset[i], 0, sizeof(pic_counters));
+    }
+    ALLOC(ctx->d_discs, Disc*, sizeof(Disc) * n_dis);
+    ALLOC(ctx->d_ctl, Ctl*, sizeof(Ctl));
+#undef ALLOC
+    cudaMemcpyAsync(ctx->d_discs, ctx->hd.data(), sizeof(Disc) * n_dis, cudaMemcpyHostToDevice, ctx->stream);
+    {
+        Ctl h{};
+        h.epoch = 1;
+        for (int i = 0; i < n_dis; ++i) {
+            h.count[i][0] = o.load ? ctx->dis[i].weights.n_e0 : 0;
+            h.count[i][1] = o.load ? ctx->dis[i].weights.n_i0 : 0;
+        }
+        cudaMemcpyAsync(ctx->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    // sweep grid: persistent CTAs
+    {
+        int occ = sweep_occupancy(ctx->fp64, o.block, o.ppt, ctx->max_N);
+        if (occ < 1) occ = 1;
+        int per = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
+        ctx->sweep_grid = std::max(1, ctx->num_sms * per);
+    }
+    if (o.load) {
+        const int gx = std::max(1, ctx->num_sms * 4);
+        ce = launch_load(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, seed, gx, ctx->stream);
+        if (ce == cudaSuccess) ce = launch_deposit(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, ctx->max_N, gx,
+                                                   ctx->stream);
+        if (ce == cudaSuccess) ce = launch_finalize(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, 4, ctx->stream);
+        if (ce == cudaSuccess) ce = launch_backkick(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, gx, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce != cudaSuccess) {
+            pic_status s = cuda_fail(ctx, ce, "initial load");
+            pic_destroy(ctx);
+            return s;
+        }
+    }
+    ctx->cur = 0;
+    ctx->step = 0;
+    ctx->deposits_zero = true;
+    *out = ctx;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_create(pic_ctx** out, const pic_gas* gas, double gap_m, double p_Pa, double T_gas_K,
+                                 double f_rf_Hz, double V_rf_V, int32_t n_cells, double dt_s,
+                                 const pic_weights* weights, uint64_t seed, const pic_options* opt) {
+    if (!gas || !weights) return PIC_ERR_ARG;
+    pic_discharge d{};
+    d.gas = 0;
+    d.n_cells = n_cells;
+    d.gap_m = gap_m;
+    d.p_Pa = p_Pa;
+    d.T_gas_K = T_gas_K;
+    d.f_rf_Hz = f_rf_Hz;
+    d.V_rf_V = V_rf_V;
+    d.dt_s = dt_s;
+    d.weights = *weights;
+    d.discharge_id = 0;
+    return pic_batch_create(out, gas, 1, &d, 1, seed, opt);
+}
+
+// ---------------------------------------------------------------------------
+static pic_status enqueue_sweep(pic_ctx* ctx) {
+    if (!ctx->deposits_zero) {
+        for (auto& D : ctx->hd) {
+            const size_t b = 8 * ((size_t)D.N + 1);
+            CK(cudaMemsetAsync(D.D[0], 0, b, ctx->stream), "memset");
+            CK(cudaMemsetAsync(D.D[1], 0, b, ctx->stream), "memset");
+            CK(cudaMemsetAsync(D.Q, 0, b, ctx->stream), "memset");
+        }
+    }
+    SweepLaunch L{};
+    L.fp64 = ctx->fp64;
+    L.block = ctx->opt.block;
+    L.ppt = ctx->opt.ppt;
+    L.grid = ctx->sweep_grid;
+    L.max_N = ctx->max_N;
+    L.n_disc = ctx->n_disc;
+    L.in_buf = ctx->cur;
+    L.discs = ctx->d_discs;
+    L.ctl = ctx->d_ctl;
+    L.st_main = ctx->st_main;
+    L.st_bagg = ctx->st_bagg;
+    L.st_binc = ctx->st_binc;
+    L.seed = ctx->seed;
+    L.stream = ctx->stream;
+    std::pair<cudaEvent_t, cudaEvent_t>* evp = nullptr;
+    if (ctx->timing) {
+        if (ctx->ev_used == ctx->ev.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            ctx->ev.push_back({a, b});
+        }
+        evp = &ctx->ev[ctx->ev_used++];
+        cudaEventRecord(evp->first, ctx->stream);
+    }
+    CK(launch_sweep(L), "sweep launch");
+    if (evp) cudaEventRecord(evp->second, ctx->stream);
+    ctx->deposits_zero = false;
+    return PIC_OK;
+}
+
+static pic_status enqueue_finalize(pic_ctx* ctx, int mode) {
+    CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, mode & 1 ? 1 - ctx->cur : ctx->cur, mode,
+                       ctx->stream),
+       "finalize launch");
+    if (mode & 1) ctx->cur = 1 - ctx->cur;
+    if (mode & 2) ctx->step += 1;
+    ctx->deposits_zero = true;
+    return PIC_OK;
+}
+
+static pic_status enqueue_sort(pic_ctx* ctx) {
+    const int gx = std::max(1, ctx->num_sms * 2);
+    CK(launch_sort(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->cur, 1 - ctx->cur, ctx->sort_hist,
+                   ctx->sort_hoff, ctx->sort_tot, ctx->max_N, gx, ctx->stream),
+       "sort launch");
+    ctx->cur = 1 - ctx->cur;
+    return PIC_OK;
+}
+
+// Sweep + births + solve: the sweep reads buffer cur and writes 1-cur; the
+// finalize appends births into 1-cur; cur flips.
+static pic_status enqueue_step(pic_ctx* ctx) {
+    pic_status s = enqueue_sweep(ctx);
+    if (s != PIC_OK) return s;
+    s = enqueue_finalize(ctx, 3);
+    if (s != PIC_OK) return s;
+    const int K = ctx->opt.sort_every;
+    if (K > 0 && ctx->step % K == 0) return enqueue_sort(ctx);
+    return PIC_OK;
+}
+
+static pic_status run_graph_period(pic_ctx* ctx, int P) {
+    const int K = ctx->opt.sort_every;
+    const int phase = K > 0 ? (int)(ctx->step % K) : 0;
+    for (auto& g : ctx->graphs)
+        if (g.cur_in == ctx->cur && g.phase == phase) {
+            CK(cudaGraphLaunch(g.exec, ctx->stream), "graph launch");
+            ctx->cur = g.cur_out;
+            ctx->step += P;
+            ctx->deposits_zero = true;
+            return PIC_OK;
+        }
+    // capture one period
+    const int cur0 = ctx->cur;
+    const long long step0 = ctx->step;
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    pic_status s = PIC_OK;
+    for (int i = 0; i < P && s == PIC_OK; ++i) s = enqueue_step(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->timing = timing;
+    if (s != PIC_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+    pic_ctx::GraphEntry ge{cur0, phase, ctx->cur, exec};
+    ctx->graphs.push_back(ge);
+    ctx->cur = cur0;
+    ctx->step = step0;
+    CK(cudaGraphLaunch(exec, ctx->stream), "graph launch");
+    ctx->cur = ge.cur_out;
+    ctx->step = step0 + P;
+    ctx->deposits_zero = true;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_step(pic_ctx* ctx, int64_t n_steps) {
+    if (!ctx || n_steps < 0) return PIC_ERR_ARG;
+    const int P = ctx->dis[0].weights.steps_per_period;
+    const int K = ctx->opt.sort_every;
+    const bool graphs = ctx->opt.use_graph && P > 0 && (K <= 0 || P % K == 0) && !ctx->timing;
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (graphs && left >= P) {
+            pic_status s = run_graph_period(ctx, P);
+            if (s != PIC_OK) return s;
+            left -= P;
+            continue;
+        }
+        pic_status s = enqueue_step(ctx);
+        if (s != PIC_OK) return s;
+        --left;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sweep(pic_ctx* ctx) {
+    if (!ctx) return PIC_ERR_ARG;
+    pic_status s = enqueue_sweep(ctx);
+    if (s != PIC_OK) return s;
+    // births appended and counts updated; no solve, no step advance
+    CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, 1 - ctx->cur, 1 | 8, ctx->stream),
+       "append launch");
+    ctx->cur = 1 - ctx->cur;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sort(pic_ctx* ctx) {
+    if (!ctx) return PIC_ERR_ARG;
+    return enqueue_sort(ctx);
+}
+
+extern "C" pic_status pic_solve(pic_ctx* ctx) {
+    if (!ctx) return PIC_ERR_ARG;
+    return enqueue_finalize(ctx, 2);
+}
+
+extern "C" pic_status pic_sync(pic_ctx* ctx) {
+    if (!ctx) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    int err = 0;
+    CK(cudaMemcpy(&err, &ctx->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (err & ERR_TIMEOUT) return fail(ctx, PIC_ERR_TIMEOUT, "device look-back wait timed out");
+    if (err & ERR_CAPACITY) return fail(ctx, PIC_ERR_CAPACITY, "particle or birth buffer capacity exceeded");
+    if (err & ERR_NONFINITE) return fail(ctx, PIC_ERR_NONFINITE, "non-finite particle coordinate");
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+static bool bad_d(pic_ctx* ctx, int d) { return !ctx || d < 0 || d >= ctx->n_disc; }
+
+extern "C" pic_status pic_get_count(pic_ctx* ctx, int32_t d, int32_t sp, int64_t* n) {
+    if (bad_d(ctx, d) || (sp & ~1) || !n) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    long long v = 0;
+    CK(cudaMemcpy(&v, &ctx->d_ctl->count[d][sp], 8, cudaMemcpyDeviceToHost), "count");
+    *n = v;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t cap, int32_t* c, void* f,
+                                    void* vx, void* vy, void* vz, int64_t* n_out) {
+    int64_t n = 0;
+    pic_status s = pic_get_count(ctx, d, sp, &n);
+    if (s != PIC_OK) return s;
+    if (n_out) *n_out = n;
+    if (n > cap) return fail(ctx, PIC_ERR_ARG, "host buffer too small");
+    const Disc& D = ctx->hd[d];
+    if (c) CK(cudaMemcpy(c, D.c[ctx->cur][sp], sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "state c");
+    const size_t r = ctx->fp64 ? 8 : 4;
+    std::vector<unsigned char> buf(4 * r * (size_t)n);
+    if (n) CK(cudaMemcpy(buf.data(), D.p[ctx->cur][sp], 4 * r * n, cudaMemcpyDeviceToHost), "state p");
+    void* outs[4] = {f, vx, vy, vz};
+    for (int k = 0; k < 4; ++k) {
+        if (!outs[k]) continue;
+        unsigned char* o = (unsigned char*)outs[k];
+        for (int64_t i = 0; i < n; ++i) std::memcpy(o + r * i, buf.data() + r * (4 * i + k), r);
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t n, const int32_t* c,
+                                    const void* f, const void* vx, const void* vy, const void* vz) {
+    if (bad_d(ctx, d) || (sp & ~1) || n < 0 || (n && (!c || !f || !vx || !vy || !vz))) return PIC_ERR_ARG;
+    const Disc& D = ctx->hd[d];
+    if (n > D.cap[sp]) return fail(ctx, PIC_ERR_CAPACITY, "state larger than capacity");
+    for (int64_t i = 0; i < n; ++i)
+        if (c[i] < 0 || c[i] >= D.N) return fail(ctx, PIC_ERR_ARG, "cell index out of range");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const size_t r = ctx->fp64 ? 8 : 4;
+    std::vector<unsigned char> buf(4 * r * (size_t)n);
+    const void* ins[4] = {f, vx, vy, vz};
+    for (int k = 0; k < 4; ++k)
+        for (int64_t i = 0; i < n; ++i) std::memcpy(buf.data() + r * (4 * i + k), (const unsigned char*)ins[k] + r * i, r);
+    if (n) {
+        CK(cudaMemcpy(D.c[ctx->cur][sp], c, sizeof(int32_t) * n, cudaMemcpyHostToDevice), "state c");
+        CK(cudaMemcpy(D.p[ctx->cur][sp], buf.data(), 4 * r * n, cudaMemcpyHostToDevice), "state p");
+    }
+    long long v = n;
+    CK(cudaMemcpy(&ctx->d_ctl->count[d][sp], &v, 8, cudaMemcpyHostToDevice), "count");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_field(pic_ctx* ctx, int32_t d, void* E, double* E64, double* phi) {
+    if (bad_d(ctx, d)) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    const size_t N1 = (size_t)D.N + 1, r = ctx->fp64 ? 8 : 4;
+    if (E) CK(cudaMemcpy(E, D.E, r * N1, cudaMemcpyDeviceToHost), "field");
+    if (E64) CK(cudaMemcpy(E64, D.E64, 8 * N1, cudaMemcpyDeviceToHost), "field64");
+    if (phi) CK(cudaMemcpy(phi, D.phi, 8 * N1, cudaMemcpyDeviceToHost), "phi");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_field(pic_ctx* ctx, int32_t d, const void* E) {
+    if (bad_d(ctx, d) || !E) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    CK(cudaMemcpy(D.E, E, (ctx->fp64 ? 8 : 4) * ((size_t)D.N + 1), cudaMemcpyHostToDevice), "field");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_deposit(pic_ctx* ctx, int32_t d, int32_t sp, int64_t* Dh) {
+    if (bad_d(ctx, d) || (sp & ~1) || !Dh) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    CK(cudaMemcpy(Dh, D.D[sp], 8 * ((size_t)D.N + 1), cudaMemcpyDeviceToHost), "deposit");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_deposit(pic_ctx* ctx, int32_t d, int32_t sp, const int64_t* Dh) {
+    if (bad_d(ctx, d) || (sp & ~1) || !Dh) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    CK(cudaMemcpy(D.D[sp], Dh, 8 * ((size_t)D.N + 1), cudaMemcpyHostToDevice), "deposit");
+    ctx->deposits_zero = false;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_energy_deposit(pic_ctx* ctx, int32_t d, int64_t* Q) {
+    if (bad_d(ctx, d) || !Q) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    CK(cudaMemcpy(Q, D.Q, 8 * ((size_t)D.N + 1), cudaMemcpyDeviceToHost), "energy deposit");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_step(pic_ctx* ctx, int64_t* step) {
+    if (!ctx || !step) return PIC_ERR_ARG;
+    *step = ctx->step;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_step(pic_ctx* ctx, int64_t step) {
+    if (!ctx || step < 0) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    long long v = step;
+    CK(cudaMemcpy(&ctx->d_ctl->step, &v, 8, cudaMemcpyHostToDevice), "step");
+    ctx->step = step;
+    return PIC_OK;
+}
+
+static pic_status read_counters(pic_ctx* ctx, int d, pic_counters* o) {
+    unsigned long long c[NCNT];
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    CK(cudaMemcpy(c, ctx->hd[d].cnt, sizeof(c), cudaMemcpyDeviceToHost), "counters");
+    std::memset(o, 0, sizeof(*o));
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) o->absorbed[a][b] = (int64_t)c[CNT_ABS + 2 * a + b];
+    for (int j = 0; j < 4; ++j) o->collisions_e[j] = (int64_t)c[CNT_COLL_E + j];
+    for (int j = 0; j < 2; ++j) o->collisions_i[j] = (int64_t)c[CNT_COLL_I + j];
+    o->null_inelastic = (int64_t)c[CNT_NULL_INEL];
+    o->see_emitted = (int64_t)c[CNT_SEE];
+    o->candidates[0] = (int64_t)c[CNT_CAND];
+    o->candidates[1] = (int64_t)c[CNT_CAND + 1];
+    o->table_clamped[0] = (int64_t)c[CNT_CLAMP];
+    o->table_clamped[1] = (int64_t)c[CNT_CLAMP + 1];
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_counters(pic_ctx* ctx, int32_t d, pic_counters* out) {
+    if (bad_d(ctx, d) || !out) return PIC_ERR_ARG;
+    return read_counters(ctx, d, out);
+}
+
+extern "C" pic_status pic_get_derived(pic_ctx* ctx, int32_t d, pic_derived* out) {
+    if (bad_d(ctx, d) || !out) return PIC_ERR_ARG;
+    *out = ctx->der[d];
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_tables(pic_ctx* ctx, int32_t g, void* Te, void* Ti) {
+    if (!ctx || g < 0 || g >= ctx->n_gas) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const GasDev& G = ctx->gas[g];
+    const size_t r = ctx->fp64 ? 8 : 4;
+    if (Te) CK(cudaMemcpy(Te, G.Te, (size_t)G.n_pts * 4 * r, cudaMemcpyDeviceToHost), "tables");
+    if (Ti) CK(cudaMemcpy(Ti, G.Ti, (size_t)G.n_pts * 2 * r, cudaMemcpyDeviceToHost), "tables");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
+    if (bad_d(ctx, d) || !out) return PIC_ERR_ARG;
+    pic_status s = pic_sync(ctx);
+    if (s != PIC_OK) return s;
+    const Disc& D = ctx->hd[d];
+    const int N = D.N;
+    const size_t N1 = (size_t)N + 1;
+    std::vector<double> aD0(N1), aD1(N1), aQ(N1), aP(N1);
+    CK(cudaMemcpy(aD0.data(), D.acc_D[0], 8 * N1, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(aD1.data(), D.acc_D[1], 8 * N1, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(aQ.data(), D.acc_Q, 8 * N1, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(aP.data(), D.acc_Dprev, 8 * N1, cudaMemcpyDeviceToHost), "moments");
+    long long steps = 0, cnt[2] = {0, 0};
+    double E0 = 0;
+    CK(cudaMemcpy(&steps, &ctx->d_ctl->acc_steps[d], 8, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(cnt, &ctx->d_ctl->count[d][0], 16, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(&E0, &ctx->d_ctl->E0_last[d], 8, cudaMemcpyDeviceToHost), "moments");
+    const double dx = D.dx, ns = steps > 0 ? (double)steps : 1.0;
+    for (int j = 0; j <= N; ++j) {
+        const double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
+        if (out->n_e) out->n_e[j] = D.w[0] * aD0[j] / (H_TWO32 * Vj * ns);
+        if (out->n_i) out->n_i[j] = D.w[1] * aD1[j] / (H_TWO32 * Vj * ns);
+        if (out->mean_eps) out->mean_eps[j] = aP[j] > 0.0 ? (aQ[j] / 65536.0) / (aP[j] / H_TWO32) : 0.0;
+    }
+    pic_counters c;
+    s = read_counters(ctx, d, &c);
+    if (s != PIC_OK) return s;
+    out->steps = steps;
+    out->count[0] = cnt[0];
+    out->count[1] = cnt[1];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            out->absorbed[a][b] = (double)(c.absorbed[a][b] - ctx->cnt_at_reset[d].absorbed[a][b]);
+            out->flux[a][b] = steps > 0 ? out->absorbed[a][b] * D.w[a] / ((double)steps * D.dt) : 0.0;
+        }
+    out->surface_charge = 8.8541878128e-12 * E0;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_reset_moments(pic_ctx* ctx) {
+    if (!ctx) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    for (int d = 0; d < ctx->n_disc; ++d) {
+        const Disc& D = ctx->hd[d];
+        const size_t b = 8 * ((size_t)D.N + 1);
+        CK(cudaMemset(D.acc_D[0], 0, b), "reset");
+        CK(cudaMemset(D.acc_D[1], 0, b), "reset");
+        CK(cudaMemset(D.acc_Q, 0, b), "reset");
+        CK(cudaMemset(D.acc_Dprev, 0, b), "reset");
+        long long z = 0;
+        CK(cudaMemcpy(&ctx->d_ctl->acc_steps[d], &z, 8, cudaMemcpyHostToDevice), "reset");
+        pic_status s = read_counters(ctx, d, &ctx->cnt_at_reset[d]);
+        if (s != PIC_OK) return s;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sweep_timing(pic_ctx* ctx, int32_t enable, double* total_ms, int64_t* launches) {
+    if (!ctx) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    double tot = 0.0;
+    for (size_t i = 0; i < ctx->ev_used; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev[i].first, ctx->ev[i].second);
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int64_t)ctx->ev_used;
+    ctx->ev_used = 0;
+    ctx->timing = enable != 0;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" pic_status pic_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out) {
+    if (n < 0 || (n && (!ctr || !key || !out))) return PIC_ERR_ARG;
+    if (!n) return PIC_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    if (cudaMalloc(&dc, 16 * n) != cudaSuccess || cudaMalloc(&dout, 16 * n) != cudaSuccess) {
+        cudaFree(dc);
+        return PIC_ERR_CUDA;
+    }
+    cudaMemcpy(dc, ctr, 16 * n, cudaMemcpyHostToDevice);
+    cudaError_t e = launch_debug_philox(n, dc, key[0], key[1], dout, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 16 * n, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dout);
+    return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}
+
+extern "C" pic_status pic_debug_math(int64_t n, const float* x, const float* y, float* lg, float* sn, float* cs) {
+    if (n < 0 || (n && (!x || !y || !lg || !sn || !cs))) return PIC_ERR_ARG;
+    if (!n) return PIC_OK;
+    float* b = nullptr;
+    if (cudaMalloc(&b, 20 * n) != cudaSuccess) return PIC_ERR_CUDA;
+    cudaMemcpy(b, x, 4 * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b + n, y, 4 * n, cudaMemcpyHostToDevice);
+    cudaError_t e = launch_debug_math(n, b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(lg, b + 2 * n, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sn, b + 3 * n, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(cs, b + 4 * n, 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(b);
+    return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}

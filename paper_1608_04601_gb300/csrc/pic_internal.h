@@ -1,0 +1,98 @@
+// pic_internal.h -- device-side data layout shared by the host runtime and the
+// kernels of the PIC/MCC library (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+constexpr int MAXD = 64;      // discharges per context
+constexpr int MAXN = 4096;    // cells per discharge
+constexpr int NCNT = 16;      // event counters per discharge
+
+// Event counter slots (u64 each), per discharge.
+enum {
+    CNT_ABS = 0,       // 4: [species][electrode]
+    CNT_COLL_E = 4,    // 4: elastic, exc1, exc2, ionization
+    CNT_COLL_I = 8,    // 2: isotropic, backward
+    CNT_NULL_INEL = 10,
+    CNT_SEE = 11,
+    CNT_CAND = 12,     // 2
+    CNT_CLAMP = 14     // 2
+};
+
+// Device error bits (Ctl::error).
+enum : int { ERR_CAPACITY = 1, ERR_TIMEOUT = 2, ERR_NONFINITE = 4 };
+
+// Per-particle constants of one discharge in the particle precision T.
+template <typename T>
+struct Consts {
+    T K[2];            // (q/m) dt/2, electrons and ions
+    T dtdx;            // dt / dx
+    T kappa_e;         // (m_e/2e)/de : speed^2 -> grid index (lab energy)
+    T kappa_i;         // (M/4e)/de   : relative speed^2 -> grid index (c.m. energy)
+    T kappa_E;         // (m_e/2e) 2^16 : speed^2 -> energy in 2^-16 eV
+    T beta, omb;       // m_e/(m_e+M), M/(m_e+M)
+    T de2_exc[2];      // excitation thresholds in speed^2 units
+    T de2_iz;          // ionization threshold in speed^2 units
+    T sig_n;           // sqrt(kT_gas/M)
+    T sig_see, sig_see_n;  // emitted electrons: tangential sigma, normal scale
+    T kmax_e, kmax_i;  // table maxima (m^3/s)
+    T gamma;           // secondary emission yield
+    T sig0[2];         // initial Maxwellians
+};
+
+struct Disc {
+    int N, n_exc, n_pts, gas;
+    uint32_t thr[2];          // null-collision candidate thresholds (of 2^32)
+    uint32_t discharge_id;
+    int steps_per_period;
+    double dx, dt, V_rf, f_rf, w[2];
+    int has_see, pad_;
+    Consts<float> cf;
+    Consts<double> cd;
+    const void* Te;           // n_pts rows x 4 (T): cumulative sigma*v, electrons
+    const void* Ti;           // n_pts rows x 2 (T): cumulative sigma*g, ions
+    int32_t* c[2][2];         // [buffer][species] cell index
+    void* p[2][2];            // [buffer][species] {f, vx, vy, vz} records
+    long long cap[2];         // capacity per species
+    int32_t* bc[2];           // births of the other species, by parent species
+    void* bp[2];
+    long long bcap;
+    void* E;                  // node field for the gather (T), N+1
+    double* E64;              // node field, FP64
+    double* phi;              // potential, FP64
+    unsigned long long* D[2]; // CIC deposits at x_{n+1}, 2^32 per particle
+    unsigned long long* Q;    // electron energy moment at x_n, 2^-16 eV
+    unsigned long long* Dprev;// electron deposit at x_n
+    double* acc_D[2];
+    double* acc_Q;
+    double* acc_Dprev;
+    unsigned long long* cnt;  // NCNT counters
+};
+
+// Control block; one per context, in device memory.
+struct Ctl {
+    long long step;           // current step index n
+    unsigned int tile_ctr;    // sweep tile dispenser
+    unsigned int done;        // sweep CTAs finished
+    unsigned int epoch;       // sweep launch counter (look-back status tag)
+    unsigned int fin_done;    // finalize CTAs finished
+    int error;                // ERR_* bits
+    int pad_;
+    long long count[MAXD][2];     // superparticles per store (sweep input)
+    long long out_main[MAXD][2];  // same-species outputs of the last sweep
+    long long out_birth[MAXD][2]; // other-species births of the last sweep, by parent species
+    long long acc_steps[MAXD];
+    double E0_last[MAXD];
+};
+
+struct alignas(32) d4 {
+    double x, y, z, w;
+};
+
+template <typename T> struct Rec;
+template <> struct Rec<float> { using type = float4; };
+template <> struct Rec<double> { using type = d4; };
+
+}  // namespace pic

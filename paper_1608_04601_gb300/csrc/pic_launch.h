@@ -1,0 +1,35 @@
+// pic_launch.h -- host-callable launch wrappers of the kernels in pic_kernels.cu.
+#pragma once
+#include "pic_internal.h"
+
+namespace pic {
+
+struct SweepLaunch {
+    int fp64, block, ppt, grid, max_N, n_disc, in_buf;
+    const Disc* discs;
+    Ctl* ctl;
+    unsigned long long *st_main, *st_bagg, *st_binc;
+    unsigned long long seed;
+    cudaStream_t stream;
+};
+
+cudaError_t launch_sweep(const SweepLaunch& L);
+int sweep_occupancy(int fp64, int block, int ppt, int max_N);
+cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, cudaStream_t st);
+cudaError_t launch_load(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
+                        int grid_x, cudaStream_t st);
+cudaError_t launch_deposit(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int buf, int max_N, int grid_x,
+                           cudaStream_t st);
+cudaError_t launch_backkick(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int buf, int grid_x,
+                            cudaStream_t st);
+cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, const double* se, const double* si,
+                          void* Te, void* Ti, unsigned long long* kmax, cudaStream_t st);
+cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int src, int dst, unsigned* hist,
+                        const long long* hoff, unsigned* tot, int max_N, int grid_x, cudaStream_t st);
+long long sort_tile();
+cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                                cudaStream_t st);
+cudaError_t launch_debug_math(long long n, const float* x, const float* y, float* lg, float* sn, float* cs,
+                              cudaStream_t st);
+
+}  // namespace pic
