@@ -356,7 +356,7 @@ static void derive(orc_ctx* o) {
     d->dtdx = dt / d->dx;
     d->kappa_e = 0.5 * M_ELEC / (E_CHARGE * de);
     d->kappa_i = 0.25 * M / (E_CHARGE * de);
-    d->kappa_E = 0.5 * M_ELEC / E_CHARGE * 65536.0;
+    d->kappa_E = 0.5 * M_ELEC / E_CHARGE * 4096.0;
     d->beta_e = M_ELEC / (M_ELEC + M);
     d->omb_e = M / (M_ELEC + M);
     for (int j = 0; j < 2; ++j) d->de2_exc[j] = 2.0 * E_CHARGE * o->gas.eps_exc_eV[j] / M_ELEC;
@@ -557,9 +557,9 @@ int orc_sweep(orc_ctx* o) {
             real ef = gather(o, c, f);
             vz = R_FMA(o->K_e, ef, vz);
             real e2 = R_FMA(vx, vx, R_FMA(vy, vy, vz * vz));
-            {   /* energy moment at (x_n, v_n), 2^-16 eV fixed point */
+            {   /* energy moment at (x_n, v_n), 2^-12 eV fixed point, clamped at 2^26 (16384 eV) */
                 real eq = e2 * o->kappa_E;
-                if (!(eq <= (real)0x1p40)) eq = (real)0x1p40;
+                if (!(eq <= (real)0x1p26)) eq = (real)0x1p26;
                 int64_t Et = (int64_t)R_RINT(eq);
                 int64_t Eh = (int64_t)R_RINT(eq * f);
                 o->Q[c] += Et - Eh;
@@ -814,7 +814,7 @@ int orc_moments(const orc_ctx* o, double* n_e, double* n_i, double* mean_eps, or
         double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
         if (n_e) n_e[j] = o->p.w_e * o->acc_D[0][j] / (TWO32 * Vj * ns);
         if (n_i) n_i[j] = o->p.w_i * o->acc_D[1][j] / (TWO32 * Vj * ns);
-        if (mean_eps) mean_eps[j] = o->acc_Dprev[j] > 0.0 ? (o->acc_Q[j] / 65536.0) / (o->acc_Dprev[j] / TWO32) : 0.0;
+        if (mean_eps) mean_eps[j] = o->acc_Dprev[j] > 0.0 ? (o->acc_Q[j] / 4096.0) / (o->acc_Dprev[j] / TWO32) : 0.0;
     }
     if (info) {
         info->steps = o->acc_steps;

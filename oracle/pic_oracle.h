@@ -98,7 +98,7 @@ int      orc_get_phi(const orc_ctx* o, double* phi);        /* N+1, V, FP64    *
 int      orc_get_efield64(const orc_ctx* o, double* E);     /* N+1, FP64       */
 int      orc_get_deposit(const orc_ctx* o, int species, int64_t* D);   /* N+1 */
 int      orc_set_deposit(orc_ctx* o, int species, const int64_t* D);
-int      orc_get_energy_deposit(const orc_ctx* o, int64_t* Q);         /* N+1 */
+int      orc_get_energy_deposit(const orc_ctx* o, int64_t* Q);         /* N+1, 2^-12 eV */
 int64_t  orc_get_step(const orc_ctx* o);
 void     orc_set_step(orc_ctx* o, int64_t n);
 void     orc_get_counters(const orc_ctx* o, orc_counters* out);

@@ -136,7 +136,7 @@ static void derive(const pic_discharge& d, const GasDev& g, const pic_gas& gi, p
     o->dtdx = dt / o->dx;
     o->kappa_e = 0.5 * H_M_ELEC / (H_E_CHARGE * de);
     o->kappa_i = 0.25 * M / (H_E_CHARGE * de);
-    o->kappa_E = 0.5 * H_M_ELEC / H_E_CHARGE * 65536.0;
+    o->kappa_E = 0.5 * H_M_ELEC / H_E_CHARGE * 4096.0;
     o->beta_e = H_M_ELEC / (H_M_ELEC + M);
     o->omb_e = M / (H_M_ELEC + M);
     for (int j = 0; j < 2; ++j) o->de2_exc[j] = 2.0 * H_E_CHARGE * (j < gi.n_exc ? gi.eps_exc_eV[j] : 0.0) / H_M_ELEC;
@@ -798,7 +798,7 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
         const double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
         if (out->n_e) out->n_e[j] = D.w[0] * aD0[j] / (H_TWO32 * Vj * ns);
         if (out->n_i) out->n_i[j] = D.w[1] * aD1[j] / (H_TWO32 * Vj * ns);
-        if (out->mean_eps) out->mean_eps[j] = aP[j] > 0.0 ? (aQ[j] / 65536.0) / (aP[j] / H_TWO32) : 0.0;
+        if (out->mean_eps) out->mean_eps[j] = aP[j] > 0.0 ? (aQ[j] / 4096.0) / (aP[j] / H_TWO32) : 0.0;
     }
     pic_counters c;
     s = read_counters(ctx, d, &c);

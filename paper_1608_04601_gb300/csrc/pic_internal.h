@@ -31,7 +31,7 @@ struct Consts {
     T dtdx;            // dt / dx
     T kappa_e;         // (m_e/2e)/de : speed^2 -> grid index (lab energy)
     T kappa_i;         // (M/4e)/de   : relative speed^2 -> grid index (c.m. energy)
-    T kappa_E;         // (m_e/2e) 2^16 : speed^2 -> energy in 2^-16 eV
+    T kappa_E;         // (m_e/2e) 2^12 : speed^2 -> energy in 2^-12 eV
     T beta, omb;       // m_e/(m_e+M), M/(m_e+M)
     T de2_exc[2];      // excitation thresholds in speed^2 units
     T de2_iz;          // ionization threshold in speed^2 units
@@ -63,7 +63,7 @@ struct Disc {
     double* E64;              // node field, FP64
     double* phi;              // potential, FP64
     unsigned long long* D[2]; // CIC deposits at x_{n+1}, 2^32 per particle
-    unsigned long long* Q;    // electron energy moment at x_n, 2^-16 eV
+    unsigned long long* Q;    // electron energy moment at x_n, 2^-12 eV
     unsigned long long* Dprev;// electron deposit at x_n
     double* acc_D[2];
     double* acc_Q;

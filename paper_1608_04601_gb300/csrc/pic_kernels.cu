@@ -84,14 +84,85 @@ __device__ __forceinline__ int drift(int N, T dtdx, int c, T f, T vz, int& cn, T
     return -1;
 }
 
+// Exact 64-bit add into a shared-memory word with native 32-bit atomics: the low
+// word's returned old value tells whether this add carried into the high word.
+__device__ __forceinline__ void sadd64(unsigned long long* p, unsigned long long v) {
+    unsigned* w = reinterpret_cast<unsigned*>(p);
+    const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
+    const unsigned old = atomicAdd(&w[0], lo);
+    const unsigned up = hi + ((unsigned)(old + lo) < old ? 1u : 0u);
+    if (up) atomicAdd(&w[1], up);
+}
+
 __device__ __forceinline__ void hist_add(unsigned long long* h, int c, unsigned long long F) {
     atomicAdd(&h[c], (1ull << 32) - F);
     if (F) atomicAdd(&h[c + 1], F);
 }
 
-template <typename T>
-__device__ __forceinline__ unsigned long long cic_F(T f) {
-    return (unsigned long long)rint_ll(mul_(f, (T)TWO32_D));
+// Same, into a shared-memory histogram.
+__device__ __forceinline__ void shist_add(unsigned long long* h, int c, unsigned long long F) {
+    sadd64(&h[c], (1ull << 32) - F);
+    if (F) sadd64(&h[c + 1], F);
+}
+
+// Round-to-nearest-even conversion of a value in [0, 2^32) to an unsigned integer.
+__device__ __forceinline__ unsigned long long rint_u32(float a) { return __float2uint_rn(a); }
+__device__ __forceinline__ unsigned long long rint_u32(double a) { return __double2uint_rn(a); }
+
+__device__ __forceinline__ unsigned long long cic_F(float f) {
+    return (unsigned long long)__float2uint_rn(__fmul_rn(f, 4294967296.0f));  // f < 1: below 2^32
+}
+__device__ __forceinline__ unsigned long long cic_F(double f) {
+    return __double2ull_rn(__dmul_rn(f, TWO32_D));  // may round to 2^32
+}
+
+// Warp-aggregated shared-memory histogram update. key < 0: nothing. Lanes whose keys equal their
+// left neighbour's form a run (the store is kept cell-sorted, so runs are long); one 64-bit warp
+// scan of the packed values gives each run's sum, and the run's last lane applies it:
+//   deposit (pair = false): v = 2^40 + F  ->  node key += count 2^32 - sum F, node key+1 += sum F
+//   moment  (pair = true):  v = lo + hi 2^32 -> node key += sum lo, node key+1 += sum hi
+// When most keys in the warp differ, plain atomics are cheaper and are used instead.
+template <bool PAIR>
+__device__ __forceinline__ void warp_hist(unsigned long long* h, int key, unsigned long long v, int lane) {
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    if (__popc(heads) > 12) {
+        if (key >= 0) {
+            if (PAIR) {
+                const unsigned long long lo = v & 0xFFFFFFFFull, hi = v >> 32;
+                if (lo) sadd64(&h[key], lo);
+                if (hi) sadd64(&h[key + 1], hi);
+            } else {
+                const unsigned long long F = v & ((1ull << 40) - 1);
+                sadd64(&h[key], (1ull << 32) - F);
+                if (F) sadd64(&h[key + 1], F);
+            }
+        }
+        return;
+    }
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    const unsigned below = heads & (0xFFFFFFFFu >> (31 - lane));
+    const int hl = 31 - __clz(below);
+    const unsigned long long before = __shfl_sync(FULL, x, hl > 0 ? hl - 1 : 0);
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && key >= 0) {
+        const unsigned long long sum = x - (hl > 0 ? before : 0ull);
+        if (PAIR) {
+            const unsigned long long lo = sum & 0xFFFFFFFFull, hi = sum >> 32;
+            if (lo) sadd64(&h[key], lo);
+            if (hi) sadd64(&h[key + 1], hi);
+        } else {
+            const unsigned long long cnt = sum >> 40, F = sum & ((1ull << 40) - 1);
+            sadd64(&h[key], (cnt << 32) - F);
+            if (F) sadd64(&h[key + 1], F);
+        }
+    }
 }
 
 // Advance one particle by one step. Returns flags: bit0 particle stays,
@@ -99,7 +170,7 @@ __device__ __forceinline__ unsigned long long cic_F(T f) {
 // bit3 candidate for a collision.
 template <typename T>
 __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict__ sE, unsigned long long* sH,
-                                            unsigned long long* sQ, unsigned long long* sC, uint32_t slot,
+                                            unsigned long long& qv, unsigned* sC, uint32_t slot,
                                             long long step, unsigned long long seed, int c, T f, T vx, T vy, T vz,
                                             Part<T>& p0, Part<T>& p1, Part<T>& p2, int& err) {
     using Row4 = typename T4<T>::type;
@@ -112,12 +183,12 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
     if (S.sp == 0) {
         vz = fma_(K.K[0], ef, vz);  // v_n
         const T e2 = fma_(vx, vx, fma_(vy, vy, mul_(vz, vz)));
-        {
+        {   // energy moment at (x_n, v_n) in 2^-12 eV, clamped at 2^26 (16384 eV)
             T eq = mul_(e2, K.kappa_E);
-            if (!(eq <= (T)0x1p40)) eq = (T)0x1p40;
-            const long long Et = rint_ll(eq), Eh = rint_ll(mul_(eq, f));
-            atomicAdd(&sQ[c], (unsigned long long)(Et - Eh));
-            if (Eh) atomicAdd(&sQ[c + 1], (unsigned long long)Eh);
+            if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
+            const unsigned long long Et = rint_u32(eq);
+            const unsigned long long Eh = rint_u32(mul_(eq, f));
+            qv = (Et - Eh) | (Eh << 32);
         }
         const U4 r = draw(seed, slot, step, 0, 0, S.did);
         bool child = false;
@@ -130,7 +201,7 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
             if (!(xi < (T)(S.n_pts - 1))) {
                 const Row4 a = Te[S.n_pts - 1];
                 C0 = a.x; C1 = a.y; C2 = a.z; C3 = a.w;
-                atomicAdd(&sC[CNT_CLAMP + 0], 1ull);
+                atomicAdd(&sC[CNT_CLAMP + 0], 1u);
             } else {
                 const int i = (int)xi;
                 const T fr = sub_(xi, (T)i);
@@ -151,7 +222,7 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
                     vx = fma_(K.beta, vx, mul_(og, nx));
                     vy = fma_(K.beta, vy, mul_(og, ny));
                     vz = fma_(K.beta, vz, mul_(og, nz));
-                    atomicAdd(&sC[CNT_COLL_E + 0], 1ull);
+                    atomicAdd(&sC[CNT_COLL_E + 0], 1u);
                 } else if (j <= S.n_exc) {
                     // excitation of level j
                     const T e2n = sub_(e2, K.de2_exc[j - 1]);
@@ -161,9 +232,9 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
                         vx = mul_(sp, nx);
                         vy = mul_(sp, ny);
                         vz = mul_(sp, nz);
-                        atomicAdd(&sC[CNT_COLL_E + j], 1ull);
+                        atomicAdd(&sC[CNT_COLL_E + j], 1u);
                     } else {
-                        atomicAdd(&sC[CNT_NULL_INEL], 1ull);
+                        atomicAdd(&sC[CNT_NULL_INEL], 1u);
                     }
                 } else {  // ionization: remaining energy shared equally
                     const T e2r = sub_(e2, K.de2_iz);
@@ -186,9 +257,9 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
                         ivy = mul_(K.sig_n, (T)b1);
                         ivz = mul_(K.sig_n, (T)b2);
                         child = true;
-                        atomicAdd(&sC[CNT_COLL_E + 3], 1ull);
+                        atomicAdd(&sC[CNT_COLL_E + 3], 1u);
                     } else {
-                        atomicAdd(&sC[CNT_NULL_INEL], 1ull);
+                        atomicAdd(&sC[CNT_NULL_INEL], 1u);
                     }
                 }
             }
@@ -199,20 +270,19 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
         int side = drift(N, K.dtdx, c, f, vz, cn, fn, err);
         if (side < 0) {
             p0 = Part<T>{cn, fn, vx, vy, vz};
-            hist_add(sH, cn, cic_F(fn));
             out |= 1u;
         } else {
-            atomicAdd(&sC[CNT_ABS + side], 1ull);
+            atomicAdd(&sC[CNT_ABS + side], 1u);
         }
         if (child) {
             cvz = fma_(K.K[0], ef, cvz);
             side = drift(N, K.dtdx, c, f, cvz, cn, fn, err);
             if (side < 0) {
                 p1 = Part<T>{cn, fn, cvx, cvy, cvz};
-                hist_add(sH, cn, cic_F(fn));
+                shist_add(sH, cn, cic_F(fn));
                 out |= 2u;
             } else {
-                atomicAdd(&sC[CNT_ABS + side], 1ull);
+                atomicAdd(&sC[CNT_ABS + side], 1u);
             }
             ivz = fma_(K.K[1], ef, ivz);
             side = drift(N, K.dtdx, c, f, ivz, cn, fn, err);
@@ -221,7 +291,7 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
                 hist_add(S.Dother, cn, cic_F(fn));
                 out |= 4u;
             } else {
-                atomicAdd(&sC[CNT_ABS + 2 + side], 1ull);
+                atomicAdd(&sC[CNT_ABS + 2 + side], 1u);
             }
         }
     } else {
@@ -242,7 +312,7 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
             if (!(xi < (T)(S.n_pts - 1))) {
                 const Row2 a = Ti[S.n_pts - 1];
                 C0 = a.x; C1 = a.y;
-                atomicAdd(&sC[CNT_CLAMP + 1], 1ull);
+                atomicAdd(&sC[CNT_CLAMP + 1], 1u);
             } else {
                 const int i = (int)xi;
                 const T fr = sub_(xi, (T)i);
@@ -258,12 +328,12 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
                 vx = fma_(hg, nx, mul_(add_(vx, vnx), (T)0.5));
                 vy = fma_(hg, ny, mul_(add_(vy, vny), (T)0.5));
                 vz = fma_(hg, nz, mul_(add_(vz, vnz), (T)0.5));
-                atomicAdd(&sC[CNT_COLL_I + 0], 1ull);
+                atomicAdd(&sC[CNT_COLL_I + 0], 1u);
             } else if (R < C1) {  // backward: the ion takes the atom's velocity
                 vx = vnx;
                 vy = vny;
                 vz = vnz;
-                atomicAdd(&sC[CNT_COLL_I + 1], 1ull);
+                atomicAdd(&sC[CNT_COLL_I + 1], 1u);
             }
         }
         vz = fma_(K.K[1], ef, vz);
@@ -272,10 +342,9 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
         const int side = drift(N, K.dtdx, c, f, vz, cn, fn, err);
         if (side < 0) {
             p0 = Part<T>{cn, fn, vx, vy, vz};
-            hist_add(sH, cn, cic_F(fn));
             out |= 1u;
         } else {
-            atomicAdd(&sC[CNT_ABS + 2 + side], 1ull);
+            atomicAdd(&sC[CNT_ABS + 2 + side], 1u);
             if (S.has_see) {
                 const U4 w = draw(seed, slot, step, 1, 3, S.did);
                 if ((T)u01(w.x) < K.gamma) {
@@ -286,7 +355,7 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
                     const T fe = side == 0 ? (T)0 : one_minus_ulp<T>();
                     p2 = Part<T>{ce, fe, mul_(K.sig_see, (T)t0), mul_(K.sig_see, (T)t1), side == 0 ? vn : -vn};
                     hist_add(S.Dother, ce, cic_F(fe));
-                    atomicAdd(&sC[CNT_SEE], 1ull);
+                    atomicAdd(&sC[CNT_SEE], 1u);
                     out |= 4u;
                 }
             }
@@ -328,7 +397,7 @@ __device__ __forceinline__ void load_rec<double>(const void* p, long long i, dou
 
 // ---------------------------------------------------------------------------
 template <typename T, int BLOCK, int PPT>
-__global__ void __launch_bounds__(BLOCK) k_sweep(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k_sweep(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
                                                  unsigned long long* __restrict__ st_main,
                                                  unsigned long long* __restrict__ st_bagg,
                                                  unsigned long long* __restrict__ st_binc, int in_buf,
@@ -348,7 +417,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep(const Disc* __restrict__ discs,
     __shared__ uint32_t s_wsum[PPT][NW];
     __shared__ uint32_t s_ktot[PPT];
     __shared__ unsigned long long s_excl[2];
-    __shared__ unsigned long long s_cnt[NCNT];
+    __shared__ unsigned s_cnt[NCNT];
     __shared__ int s_err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -381,7 +450,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep(const Disc* __restrict__ discs,
                 if (q) atomicAdd(&S.Qg[j], q);
             }
         }
-        if (tid < NCNT && s_cnt[tid]) atomicAdd(&S.cnt[tid], s_cnt[tid]);
+        if (tid < NCNT && s_cnt[tid]) atomicAdd(&S.cnt[tid], (unsigned long long)s_cnt[tid]);
         __syncthreads();
     };
 
@@ -467,13 +536,18 @@ __global__ void __launch_bounds__(BLOCK) k_sweep(const Disc* __restrict__ discs,
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             fl[k] = 0;
+            unsigned long long qv = 0;
             if (cin[k] >= 0) {
                 const uint32_t slot = (uint32_t)(base + (long long)k * BLOCK + tid);
-                fl[k] = advance<T>(S, s_E, s_hist, s_Q, s_cnt, slot, step, seed, cin[k], fin[k], vxin[k], vyin[k],
+                fl[k] = advance<T>(S, s_E, s_hist, qv, s_cnt, slot, step, seed, cin[k], fin[k], vxin[k], vyin[k],
                                    vzin[k], P0[k], P1[k], P2[k], err);
             }
             const unsigned cm = __ballot_sync(FULL, (fl[k] & 8u) != 0);
-            if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + S.sp], (unsigned long long)__popc(cm));
+            if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + S.sp], (unsigned)__popc(cm));
+            // deposit of the particle at x_{n+1}, and (electrons) the energy moment at x_n
+            const bool alive = (fl[k] & 1u) != 0;
+            warp_hist<false>(s_hist, alive ? P0[k].c : -1, alive ? (1ull << 40) + cic_F(P0[k].f) : 0ull, lane);
+            if (S.sp == 0) warp_hist<true>(s_Q, cin[k], qv, lane);
         }
         // block scan of (same-species outputs | births << 16) per k, in slot order
         uint32_t v[PPT], incl[PPT];
@@ -530,35 +604,44 @@ __global__ void __launch_bounds__(BLOCK) k_sweep(const Disc* __restrict__ discs,
                     st_bagg[g] = B;
                     st_release(&st_main[g], mk_status(epoch, 1, A));
                 }
+                // Look back in windows of LB_W x 32 predecessors: all of a window's status
+                // words are requested at once, then its 32-tile groups are examined nearest
+                // first; the walk stops at the nearest inclusive prefix.
+                constexpr int LB_W = 8;
                 long long j = g - 1;
-                for (;;) {
-                    const long long idx = j - lane;
-                    unsigned flag = 2;
-                    unsigned long long va = 0, vb = 0;
-                    if (idx >= first) {
-                        unsigned long long w = 0;
-                        flag = 0;
-                        for (int it = 0; it < LOOKBACK_SPIN_LIMIT; ++it) {
-                            w = ld_acquire(&st_main[idx]);
-                            if ((unsigned)(w >> 32) == epoch) {
-                                flag = (unsigned)(w >> 30) & 3u;
-                                if (flag) break;
+                bool found = false;
+                while (!found) {
+                    unsigned long long w[LB_W];
+#pragma unroll
+                    for (int i = 0; i < LB_W; ++i) {
+                        const long long idx = j - i * 32 - lane;
+                        w[i] = idx >= first ? ld_acquire(&st_main[idx]) : mk_status(epoch, 2, 0);
+                    }
+#pragma unroll
+                    for (int i = 0; i < LB_W && !found; ++i) {
+                        const long long idx = j - i * 32 - lane;
+                        unsigned flag = 2;
+                        if (idx >= first) {
+                            flag = ((unsigned)(w[i] >> 32) == epoch) ? (unsigned)(w[i] >> 30) & 3u : 0u;
+                            for (int it = 0; !flag && it < LOOKBACK_SPIN_LIMIT; ++it) {
+                                __nanosleep(32);
+                                w[i] = ld_acquire(&st_main[idx]);
+                                if ((unsigned)(w[i] >> 32) == epoch) flag = (unsigned)(w[i] >> 30) & 3u;
                             }
-                            __nanosleep(32);
+                            if (!flag) {
+                                err |= ERR_TIMEOUT;
+                                flag = 2;
+                                w[i] = 0;
+                            }
                         }
-                        if (!flag) {
-                            err |= ERR_TIMEOUT;
-                            flag = 2;
-                            w = 0;
-                        }
-                        va = w & 0x3FFFFFFFull;
-                        vb = (flag == 2) ? *((volatile unsigned long long*)&st_binc[idx])
-                                         : *((volatile unsigned long long*)&st_bagg[idx]);
-                    }
-                    const unsigned pm = __ballot_sync(FULL, flag == 2);
-                    if (pm) {
-                        const int L = __ffs(pm) - 1;
-                        unsigned long long a = lane <= L ? va : 0ull, b = lane <= L ? vb : 0ull;
+                        const unsigned long long va = idx >= first ? (w[i] & 0x3FFFFFFFull) : 0ull;
+                        const unsigned pm = __ballot_sync(FULL, flag == 2);
+                        const int L = pm ? __ffs(pm) - 1 : 31;
+                        unsigned long long vb = 0;
+                        if (idx >= first && lane <= L)
+                            vb = (flag == 2) ? *((volatile unsigned long long*)&st_binc[idx])
+                                             : *((volatile unsigned long long*)&st_bagg[idx]);
+                        unsigned long long a = lane <= L ? va : 0ull, b = vb;
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) {
                             a += __shfl_xor_sync(FULL, a, o);
@@ -566,18 +649,9 @@ __global__ void __launch_bounds__(BLOCK) k_sweep(const Disc* __restrict__ discs,
                         }
                         exA += a;
                         exB += b;
-                        break;
-                    } else {
-                        unsigned long long a = va, b = vb;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            a += __shfl_xor_sync(FULL, a, o);
-                            b += __shfl_xor_sync(FULL, b, o);
-                        }
-                        exA += a;
-                        exB += b;
-                        j -= 32;
+                        if (pm) found = true;
                     }
+                    j -= LB_W * 32;
                 }
                 if (lane == 0) {
                     st_binc[g] = exB + B;
@@ -754,6 +828,9 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
     }
     __syncthreads();
     block_scan_inclusive<BLOCK>(a, N, s_warp);  // a[j] = R_j, j = 0..N-1
+    double* Rr = rho + (MAXN + 1);              // keep R for the field (third shared array)
+    for (int j = tid; j < N; j += BLOCK) Rr[j] = a[j];
+    __syncthreads();
     // exclusive scan of R into S: S_j = sum_{i<j} R_i, j = 0..N
     double* Sx = a;  // reuse: shift by one
     {
@@ -763,6 +840,9 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
     __syncthreads();
     const double SN = N > 0 ? Sx[N - 1] : 0.0;
     const double g1 = (0.0 - V0 + SN) / (double)N;
+    // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
+    // (the central difference of phi, without the cancellation of large phi values), and Gauss's
+    // law over the half cells at the electrodes.
     double* phi = D.phi;
     for (int j = tid; j <= N; j += BLOCK) {
         const double Sj = j == 0 ? 0.0 : Sx[j - 1];
@@ -772,12 +852,11 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
         phi[j] = ph;
     }
     __syncthreads();
-    __threadfence_block();
     for (int j = tid; j <= N; j += BLOCK) {
         double E;
-        if (j == 0) E = (phi[0] - phi[1]) / dx - rho[0] * dx / (2.0 * EPS0);
-        else if (j == N) E = (phi[N - 1] - phi[N]) / dx + rho[N] * dx / (2.0 * EPS0);
-        else E = (phi[j - 1] - phi[j + 1]) / (2.0 * dx);
+        if (j == 0) E = -g1 / dx - rho[0] * dx / (2.0 * EPS0);
+        else if (j == N) E = -(g1 - Rr[N - 1]) / dx + rho[N] * dx / (2.0 * EPS0);
+        else E = -((g1 - Rr[j - 1]) + (g1 - Rr[j])) / (2.0 * dx);
         D.E64[j] = E;
         reinterpret_cast<T*>(D.E)[j] = (T)E;
         if (j == 0) ctl->E0_last[d] = E;
@@ -855,7 +934,7 @@ __global__ void k_deposit(const Disc* __restrict__ discs, const Ctl* __restrict_
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         T f, vx, vy, vz;
         load_rec<T>(D.p[buf][sp], k, f, vx, vy, vz);
-        hist_add(s_h, D.c[buf][sp][k], cic_F(f));
+        shist_add(s_h, D.c[buf][sp][k], cic_F(f));
     }
     __syncthreads();
     for (int j = threadIdx.x; j <= N; j += blockDim.x)
@@ -1121,15 +1200,38 @@ __global__ void k_debug_math(long long n, const float* __restrict__ x, const flo
 
 // ---------------------------------------------------------------------------
 // Launch wrappers used by the host runtime.
+#include <mutex>
+#include <vector>
+
 #include "pic_launch.h"
 
 namespace pic {
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, size). Kernels
+// are told apart by their address (instantiations can share a type).
+template <typename K>
+static cudaError_t smem_attr(K kern, size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    const void* key = reinterpret_cast<const void*>(kern);
+    for (auto& p : done)
+        if (p.first == key) {
+            if (smem <= p.second) return cudaSuccess;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) p.second = smem;
+            return e;
+        }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done.push_back({key, smem});
+    return e;
+}
 
 template <typename T, int BLOCK, int PPT>
 static cudaError_t launch_sweep_t(const SweepLaunch& L) {
     const size_t smem = (size_t)(L.max_N + 1) * (16 + sizeof(T));
     auto kern = k_sweep<T, BLOCK, PPT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<L.grid, BLOCK, smem, L.stream>>>(L.discs, L.n_disc, L.ctl, L.st_main, L.st_bagg, L.st_binc, L.in_buf,
                                             L.seed, L.max_N);
@@ -1156,7 +1258,7 @@ template <typename T, int BLOCK, int PPT>
 static int occ_t(int max_N) {
     int nb = 0;
     const size_t smem = (size_t)(max_N + 1) * (16 + sizeof(T));
-    cudaFuncSetAttribute(k_sweep<T, BLOCK, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_attr(k_sweep<T, BLOCK, PPT>, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<T, BLOCK, PPT>, BLOCK, smem);
     return nb;
 }
@@ -1177,12 +1279,12 @@ int sweep_occupancy(int fp64, int block, int ppt, int max_N) {
 
 cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode,
                             cudaStream_t st) {
-    const size_t smem = sizeof(double) * 2 * (MAXN + 1);
+    const size_t smem = sizeof(double) * 3 * (MAXN + 1);
     if (fp64) {
-        cudaFuncSetAttribute(k_finalize<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_attr(k_finalize<double>, smem);
         k_finalize<double><<<n_disc, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
     } else {
-        cudaFuncSetAttribute(k_finalize<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_attr(k_finalize<float>, smem);
         k_finalize<float><<<n_disc, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
     }
     return cudaGetLastError();
@@ -1235,10 +1337,10 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(unsigned) * SORT_NW * max_N;
     if (fp64) {
-        cudaFuncSetAttribute(k_sort_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_attr(k_sort_scatter<double>, smem);
         k_sort_scatter<double><<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, dst, hist, hoff, tot, max_N);
     } else {
-        cudaFuncSetAttribute(k_sort_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_attr(k_sort_scatter<float>, smem);
         k_sort_scatter<float><<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, dst, hist, hoff, tot, max_N);
     }
     return cudaGetLastError();

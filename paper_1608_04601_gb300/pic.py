@@ -44,7 +44,7 @@ class Simulation:
     precision: "fp32" (FP32 particles, fixed-point deposits, FP64 field) or "fp64".
     """
 
-    def __init__(self, gases, discharges, seed: int = 1, precision: str = "fp32", sort_every: int = 0,
+    def __init__(self, gases, discharges, seed=None, precision: str = "fp32", sort_every: int = 0,
                  block: int = 256, ppt: int = 4, ctas_per_sm: int = 0, use_graph: bool = False,
                  stream=None, load: bool = True, capacity=None):
         self.L = NV.lib()
@@ -79,6 +79,8 @@ class Simulation:
             opt.cuda_stream = torch.cuda.current_stream().cuda_stream
         elif stream is not None:
             opt.cuda_stream = int(stream)
+        if seed is None:
+            seed = self.discharges[0][0].seed
         h = C.c_void_p()
         st = self.L.pic_batch_create(C.byref(h), garr, len(gs), darr, len(self.discharges), seed, C.byref(opt))
         del keep

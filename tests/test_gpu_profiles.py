@@ -1,0 +1,94 @@
+"""Cycle-averaged profiles of a whole discharge: FP32 GPU path vs FP64 oracle, several seeds each.
+
+Once a single field value rounds differently the two runs follow different random histories, so
+whole discharges are compared statistically (the paper's own check between its two PIC codes is
+of this kind, section "Results"). Criterion: relative L2 distance of the seed-averaged profiles
+(n_e, n_i, mean electron energy) and the relative difference of the seed-averaged ion fluxes to
+each electrode are within max(3 %, 3 sigma), sigma being the standard deviation of the difference
+of the two seed means, estimated from the run-to-run spread on each side.
+
+Workload: the 128-cell He-like discharge at 30 Pa, 200 V (400 steps per rf period), 2e4 + 2e4
+superparticles, 12 periods: 4 to settle and 8 averaged.
+"""
+import concurrent.futures as cf
+import multiprocessing as mp
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SEEDS = [11, 12, 13, 14, 15, 16]
+SETTLE, AVG = 4, 8
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _discharge(seed):
+    from paper_1608_04601_gb300.workloads import c1
+    return c1().scaled(seed=seed)
+
+
+def _gas():
+    from paper_1608_04601_gb300 import xsections as X
+    return X.he_like(eps_max_eV=400.0, de_eV=1e-2)
+
+
+def _oracle_run(seed):
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    d = _discharge(seed)
+    o = O.Oracle(_gas(), d, "f64", sort_every=1)
+    o.step(SETTLE * d.steps_per_period)
+    o.reset_moments()
+    o.step(AVG * d.steps_per_period)
+    m = o.moments()
+    T = AVG * d.steps_per_period * d.dt_s
+    flux = [m["absorbed"][1][k] * d.w_i / T for k in (0, 1)]
+    return {"n_e": m["n_e"], "n_i": m["n_i"], "mean_eps": m["mean_eps"], "flux_i": np.array(flux)}
+
+
+def _gpu_run(seed):
+    from paper_1608_04601_gb300 import pic
+    d = _discharge(seed)
+    sim = pic.Simulation(_gas(), d, precision="fp32", sort_every=4, use_graph=True)
+    sim.step(SETTLE * d.steps_per_period)
+    sim.sync()
+    sim.reset_moments()
+    sim.step(AVG * d.steps_per_period)
+    m = sim.moments(0)
+    sim.close()
+    return {"n_e": m["n_e"], "n_i": m["n_i"], "mean_eps": m["mean_eps"], "flux_i": np.array(m["flux"][1])}
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_cycle_averaged_profiles_agree_with_oracle():
+    import __graft_entry__ as g
+    g.build()
+    # oracle runs in processes started by spawn (this process holds a CUDA context)
+    with cf.ProcessPoolExecutor(max_workers=min(len(SEEDS), os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        fut = [ex.submit(_oracle_run, s) for s in SEEDS]
+        gpu = [_gpu_run(s) for s in SEEDS]
+        orc = [f.result() for f in fut]
+    report = []
+    for key in ("n_e", "n_i", "mean_eps", "flux_i"):
+        G = np.stack([r[key] for r in gpu])
+        R = np.stack([r[key] for r in orc])
+        if key == "mean_eps":  # ignore the wall nodes, where electrons are too few to average
+            G, R = G[:, 2:-2], R[:, 2:-2]
+        gm, rm = G.mean(0), R.mean(0)
+        # run-to-run spread of each side as a relative-L2 scatter about its mean
+        sg = np.sqrt(np.mean([np.sum((x - gm) ** 2) for x in G]) * len(G) / (len(G) - 1)) / np.linalg.norm(rm)
+        so = np.sqrt(np.mean([np.sum((x - rm) ** 2) for x in R]) * len(R) / (len(R) - 1)) / np.linalg.norm(rm)
+        sigma = math.sqrt(sg ** 2 / len(G) + so ** 2 / len(R))
+        d = _rel_l2(gm, rm)
+        bound = max(0.03, 3 * sigma)
+        report.append(f"{key}: rel L2 {d:.4f}, sigma {sigma:.4f}, bound {bound:.4f}")
+        assert d <= bound, report
+    print("\n".join(report))
