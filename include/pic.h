@@ -183,7 +183,8 @@ pic_status pic_set_field(pic_ctx* ctx, int32_t d, const void* E);
 /* 64-bit fixed-point CIC deposits of the last sweep (2^32 per particle). */
 pic_status pic_get_deposit(pic_ctx* ctx, int32_t d, int32_t species, int64_t* D);
 pic_status pic_set_deposit(pic_ctx* ctx, int32_t d, int32_t species, const int64_t* D);
-/* Electron energy moment of the last sweep at (x_n, v_n), 2^-16 eV units. */
+/* Electron energy moment of the last sweep at (x_n, v_n), 2^-12 eV units
+ * (per-particle energies clamped at 16384 eV). */
 pic_status pic_get_energy_deposit(pic_ctx* ctx, int32_t d, int64_t* Q);
 pic_status pic_get_step(pic_ctx* ctx, int64_t* step);
 pic_status pic_set_step(pic_ctx* ctx, int64_t step);
@@ -222,6 +223,33 @@ pic_status pic_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t key[2
  * by the kernels, on n inputs.                                            */
 pic_status pic_debug_math(int64_t n, const float* x, const float* y, float* log_out,
                           float* sin_out, float* cos_out);
+
+/* ---- allocation-free entry point ----------------------------------------
+ * The paper has no counterpart to this entry point. It serves callers that
+ * cannot allocate device memory while they run -- code with its own memory
+ * arena that forbids cudaMalloc/cudaFree (they synchronise the device and can
+ * fail late), plug-ins that are handed only device pointers, services that
+ * must not grow their footprint. pic_sort_noalloc stably sorts one particle
+ * store by cell index (the same order as pic_sort):
+ *   c_in, rec_in   device arrays of n cells and n records {f, vx, vy, vz}
+ *                  (float4, or four doubles for PIC_FP64), caller-owned;
+ *   c_out, rec_out device arrays of n entries, caller-owned, not overlapping
+ *                  the inputs; cells must lie in [0, n_cells);
+ *   cuda_stream    stream to enqueue on (NULL: the legacy default stream).
+ * Its scratch is a fixed array of PIC_NOALLOC_SCRATCH_BYTES compiled into the
+ * library (every GPU that loads the library holds it until the process
+ * exits); the call allocates nothing. Limit: n_cells * (1 + ceil(n / 4096))
+ * <= PIC_NOALLOC_SCRATCH_BYTES / 4, else PIC_ERR_CAPACITY (e.g. 512 cells:
+ * up to 8.38e6 particles; 2048 cells: up to 2.09e6). The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture. All calls share the one array and each call rewrites
+ * all of it that it reads, so consecutive calls are independent, but calls
+ * that overlap on the GPU (other streams or threads) race: serialise them.
+ * Returns PIC_ERR_ARG for invalid arguments, PIC_ERR_CUDA if a launch fails;
+ * asynchronous otherwise.                                                  */
+#define PIC_NOALLOC_SCRATCH_BYTES (4u << 20)
+pic_status pic_sort_noalloc(const int32_t* c_in, const void* rec_in, int32_t* c_out, void* rec_out,
+                            int64_t n, int32_t n_cells, int32_t precision, void* cuda_stream);
 
 #ifdef __cplusplus
 }

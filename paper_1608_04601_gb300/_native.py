@@ -110,6 +110,7 @@ PROTOTYPES = {
     "pic_sweep_timing": (C.c_int, [_vp, _i32, C.POINTER(C.c_double), C.POINTER(_i64)]),
     "pic_debug_philox": (C.c_int, [_i64, _vp, _vp, _vp]),
     "pic_debug_math": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
+    "pic_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp]),
 }
 
 _lib = None
