@@ -203,10 +203,54 @@ def run_gpu(args, rank: int, world: int):
         sim.close()
         return {"value": ps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h / steps)}
 
+    def measure_batch(steps: int, warmup: int, sort_every: int):
+        """32 discharges of uneven counts (He/Ar-like x 4 pressures x 4 voltages, 1e5..4e6 each) in one
+        persistent sweep launch per step, against the same discharges advanced one at a time."""
+        from paper_1608_04601_gb300 import xsections as X
+        from paper_1608_04601_gb300.workloads import c4
+        ds = c4(seed=1)
+        gases = [X.he_like(eps_max_eV=1000.0), X.ar_like(eps_max_eV=1000.0)]
+        pairs = [(dd, 0 if dd.gas == "he" else 1) for dd in ds]
+
+        def timed(sim, n):
+            sim.step(warmup)
+            sim.sync()
+            tot, ps = 0.0, 0.0
+            for k in range(n):
+                c = sum(sim.count(i, sp) for i in range(len(sim.N)) for sp in (0, 1))
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.step(1)
+                b.record(stream)
+                b.synchronize()
+                tot += a.elapsed_time(b)
+                ps += c
+            return tot, ps
+
+        sim = pic.Simulation(gases, pairs, seed=1, precision="fp32", sort_every=sort_every, stream="torch",
+                             block=args.block, ppt=args.ppt)
+        t_b, ps_b = timed(sim, steps)
+        sim.close()
+        t_s, ps_s = 0.0, 0.0
+        for pr in pairs:
+            one = pic.Simulation(gases, [pr], seed=1, precision="fp32", sort_every=sort_every, stream="torch",
+                                 block=args.block, ppt=args.ppt)
+            t, ps = timed(one, max(2, steps // 4))
+            one.close()
+            t_s += t / max(2, steps // 4)
+            ps_s += ps / max(2, steps // 4)
+        return {"workload": "32 discharges: {He,Ar}-like x {10,20,40,80} Pa x {150,250,350,500} V, 2.5 cm, "
+                            "512 cells, 1e5..4e6 superparticles per species each (seed 1)",
+                "value": ps_b / (t_b * 1e-3), "unit": UNIT, "ms_per_step": t_b / steps,
+                "one_at_a_time": {"value": ps_s / (t_s * 1e-3), "ms_per_step": t_s},
+                "particles": int(ps_b / steps)}
+
     sort_every = args.sort_every
     main = measure("fp32", args.steps, args.warmup, sort_every)
     fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
     e2e = measure_e2e("fp32", max(3, min(10, args.steps)), sort_every)
+    batch = measure_batch(max(4, args.steps // 2), 3, sort_every) if not args.no_batch else None
 
     # aggregate over ranks: the job took as long as its slowest rank, and did every rank's work
     total_ms, ps = reduce_over_ranks(main["total_ms"], main["ps"], world, "cuda")
@@ -238,6 +282,8 @@ def run_gpu(args, rank: int, world: int):
                          "sweep_gbs": BYTES_PER_PS["fp64"] * fp64["ps"] / (fp64["sweep_ms"] * 1e-3) / 1e9,
                          "bytes_per_particle_step": BYTES_PER_PS["fp64"]},
            "e2e": e2e, "clocks": main["clocks"], "gpu_launches": main["gpu_launches"]}
+    if batch:
+        res["batch_c4"] = batch
     return res
 
 
@@ -272,6 +318,7 @@ def main():
     ap.add_argument("--ppt", type=int, default=4)
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -26,7 +26,7 @@
  *   - Work is enqueued on the context's CUDA stream (the caller's, if given
  *     in pic_options.cuda_stream). Calls that return host data synchronise
  *     that stream first; pic_sync() synchronises and reports errors that the
- *     device raised (capacity overflow, look-back timeout, non-finite state).
+ *     device raised (capacity overflow, bounded-wait timeout, non-finite state).
  *   - Species index 0 = electrons, 1 = ions. Discharge index counts from 0 in
  *     the order given to pic_batch_create.
  *   - Particle state is structure-of-arrays: int32 cell c in [0, N), in-cell

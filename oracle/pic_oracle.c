@@ -77,7 +77,7 @@ typedef double real;
 #define TWO32 4294967296.0
 
 enum { SP_E = 0, SP_I = 1 };
-enum { CALL_MAIN = 0, CALL_AUX = 1, CALL_AUX2 = 2, CALL_SEE = 3,
+enum { CALL_MAIN = 0, CALL_AUX = 1, CALL_AUX2 = 2, CALL_SEE = 3, CALL_CAND = 4,
        CALL_LOAD0 = 0xF0, CALL_LOAD1 = 0xF1 };
 
 typedef struct {
@@ -143,6 +143,14 @@ static void draw(const orc_ctx* o, uint32_t slot, int species, int call, uint32_
                        o->p.discharge_id};
     uint32_t key[2] = {(uint32_t)o->p.seed, (uint32_t)(o->p.seed >> 32)};
     orc_philox4x32_10(ctr, key, r);
+}
+
+/* Candidate word of a slot: slots 4q..4q+3 share one Philox call (call 4,
+ * first counter word q) and take its words 0..3 in order.                   */
+static uint32_t candidate_word(const orc_ctx* o, uint32_t slot, int species) {
+    uint32_t r[4];
+    draw(o, slot >> 2, species, CALL_CAND, r);
+    return r[slot & 3];
 }
 
 /* u = (top 23 bits + 1/2) * 2^-23, in [2^-24, 1 - 2^-24], exact in float
@@ -565,11 +573,11 @@ int orc_sweep(orc_ctx* o) {
                 o->Q[c] += Et - Eh;
                 o->Q[c + 1] += Eh;
             }
-            uint32_t r[4];
-            draw(o, slot, SP_E, CALL_MAIN, r);
             int have_child = 0;
             real ce_vx = 0, ce_vy = 0, ce_vz = 0, ci_vx = 0, ci_vy = 0, ci_vz = 0;
-            if (r[0] < o->d.thr_e) {
+            if (candidate_word(o, slot, SP_E) < o->d.thr_e) {
+                uint32_t r[4];
+                draw(o, slot, SP_E, CALL_MAIN, r);
                 o->cnt.candidates[SP_E]++;
                 real C[4];
                 o->cnt.table_clamped[SP_E] += lookup(o->Te, ncol_e, o->n_pts, e2 * o->kappa_e, C);
@@ -669,9 +677,9 @@ int orc_sweep(orc_ctx* o) {
             real f = s->f[k], vx = s->vx[k], vy = s->vy[k], vz = s->vz[k];
             real ef = gather(o, c, f);
             vz = R_FMA(o->K_i, ef, vz);
-            uint32_t r[4];
-            draw(o, slot, SP_I, CALL_MAIN, r);
-            if (r[0] < o->d.thr_i) {
+            if (candidate_word(o, slot, SP_I) < o->d.thr_i) {
+                uint32_t r[4];
+                draw(o, slot, SP_I, CALL_MAIN, r);
                 o->cnt.candidates[SP_I]++;
                 uint32_t q[4];
                 draw(o, slot, SP_I, CALL_AUX, q);

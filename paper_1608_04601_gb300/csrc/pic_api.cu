@@ -41,7 +41,6 @@ struct pic_ctx {
     std::vector<Disc> hd;
     Disc* d_discs = nullptr;
     Ctl* d_ctl = nullptr;
-    unsigned long long *st_main = nullptr, *st_bagg = nullptr, *st_binc = nullptr;
     unsigned* sort_hist = nullptr;
     unsigned* sort_tot = nullptr;
     long long* sort_hoff = nullptr;
@@ -317,14 +316,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ctx->gas.push_back(gd);
     }
 
-    // look-back status words: one per sweep tile of the largest possible population
     const long long tile = (long long)o.block * o.ppt;
-    long long max_tiles = 0;
-    for (auto& d : ctx->dis)
-        max_tiles += (d.weights.capacity_e + tile - 1) / tile + (d.weights.capacity_i + tile - 1) / tile + 2;
-    ALLOC(ctx->st_main, unsigned long long*, sizeof(unsigned long long) * max_tiles);
-    ALLOC(ctx->st_bagg, unsigned long long*, sizeof(unsigned long long) * max_tiles);
-    ALLOC(ctx->st_binc, unsigned long long*, sizeof(unsigned long long) * max_tiles);
     // sort scratch: per store (cells x sort tiles) counts
     {
         std::vector<long long> hoff(2 * MAXD, 0);
@@ -366,6 +358,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.w[0] = d.weights.w_e;
         D.w[1] = d.weights.w_i;
         D.has_see = d.weights.gamma_see > 0.0;
+        D.tile = (int)tile;
         fill_consts<float>(D.cf, der, d);
         fill_consts<double>(D.cd, der, d);
         D.Te = g.Te;
@@ -374,14 +367,31 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.cap[1] = d.weights.capacity_i;
         D.bcap = std::max(D.cap[0], D.cap[1]) / 8 + 4096;
         const size_t rec = 4 * rsz;
+        for (int sp = 0; sp < 2; ++sp) {
+            // record buffers: 2 tile records per input tile, then the births region
+            D.max_tiles[sp] = (D.cap[sp] + tile - 1) / tile;
+            D.R0[sp] = D.max_tiles[sp] * 2 * tile;
+            D.rcap[sp] = D.R0[sp] + D.bcap;
+            if (D.rcap[sp] > 0x7FFFFFF0ll) {
+                pic_status s_ = fail(ctx, PIC_ERR_ARG, "capacity too large for 32-bit segment offsets");
+                pic_destroy(ctx);
+                return s_;
+            }
+        }
         for (int b = 0; b < 2; ++b)
             for (int sp = 0; sp < 2; ++sp) {
-                ALLOC(D.c[b][sp], int32_t*, sizeof(int32_t) * (size_t)std::max(1ll, D.cap[sp]));
-                ALLOC(D.p[b][sp], void*, rec * (size_t)std::max(1ll, D.cap[sp]));
+                ALLOC(D.c[b][sp], int32_t*, sizeof(int32_t) * (size_t)(D.rcap[sp] + 16));
+                ALLOC(D.p[b][sp], void*, rec * (size_t)(D.rcap[sp] + 16));
             }
         for (int sp = 0; sp < 2; ++sp) {
-            ALLOC(D.bc[sp], int32_t*, sizeof(int32_t) * (size_t)D.bcap);
-            ALLOC(D.bp[sp], void*, rec * (size_t)D.bcap);
+            const size_t mt = (size_t)D.max_tiles[sp];
+            ALLOC(D.bc[sp], int32_t*, sizeof(int32_t) * (mt * tile + 16));
+            ALLOC(D.bp[sp], void*, rec * (mt * tile + 16));
+            ALLOC(D.seg_start[sp], int*, sizeof(int) * (mt + 3));
+            ALLOC(D.seg_src[sp], int*, sizeof(int) * (mt + 2));
+            ALLOC(D.first_seg[sp], int*, sizeof(int) * (mt + 2));
+            ALLOC(D.cnt_main[sp], int*, sizeof(int) * (mt + 1));
+            ALLOC(D.cnt_birth[sp], int*, sizeof(int) * (mt + 1));
         }
         const size_t N1 = (size_t)d.n_cells + 1;
         ALLOC(D.E, void*, rsz * N1);
@@ -405,13 +415,18 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
     cudaMemcpyAsync(ctx->d_discs, ctx->hd.data(), sizeof(Disc) * n_dis, cudaMemcpyHostToDevice, ctx->stream);
     {
         Ctl h{};
-        h.epoch = 1;
         for (int i = 0; i < n_dis; ++i) {
             h.count[i][0] = o.load ? ctx->dis[i].weights.n_e0 : 0;
             h.count[i][1] = o.load ? ctx->dis[i].weights.n_i0 : 0;
         }
         cudaMemcpyAsync(ctx->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream);
-        cudaStreamSynchronize(ctx->stream);
+        ce = launch_set_dense(ctx->d_discs, n_dis, ctx->d_ctl, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce != cudaSuccess) {
+            pic_status s = cuda_fail(ctx, ce, "store set-up");
+            pic_destroy(ctx);
+            return s;
+        }
     }
     // sweep grid: persistent CTAs
     {
@@ -479,9 +494,6 @@ static pic_status enqueue_sweep(pic_ctx* ctx) {
     L.in_buf = ctx->cur;
     L.discs = ctx->d_discs;
     L.ctl = ctx->d_ctl;
-    L.st_main = ctx->st_main;
-    L.st_bagg = ctx->st_bagg;
-    L.st_binc = ctx->st_binc;
     L.seed = ctx->seed;
     L.stream = ctx->stream;
     std::pair<cudaEvent_t, cudaEvent_t>* evp = nullptr;
@@ -516,6 +528,7 @@ static pic_status enqueue_sort(pic_ctx* ctx) {
     CK(launch_sort(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->cur, 1 - ctx->cur, ctx->sort_hist,
                    ctx->sort_hoff, ctx->sort_tot, ctx->max_N, gx, ctx->stream),
        "sort launch");
+    CK(launch_set_dense(ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->stream), "sort launch");
     ctx->cur = 1 - ctx->cur;
     return PIC_OK;
 }
@@ -617,7 +630,7 @@ extern "C" pic_status pic_sync(pic_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     int err = 0;
     CK(cudaMemcpy(&err, &ctx->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost), "error word");
-    if (err & ERR_TIMEOUT) return fail(ctx, PIC_ERR_TIMEOUT, "device look-back wait timed out");
+    if (err & ERR_TIMEOUT) return fail(ctx, PIC_ERR_TIMEOUT, "a bounded device-side wait timed out");
     if (err & ERR_CAPACITY) return fail(ctx, PIC_ERR_CAPACITY, "particle or birth buffer capacity exceeded");
     if (err & ERR_NONFINITE) return fail(ctx, PIC_ERR_NONFINITE, "non-finite particle coordinate");
     return PIC_OK;
@@ -643,15 +656,31 @@ extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     if (n_out) *n_out = n;
     if (n > cap) return fail(ctx, PIC_ERR_ARG, "host buffer too small");
     const Disc& D = ctx->hd[d];
-    if (c) CK(cudaMemcpy(c, D.c[ctx->cur][sp], sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "state c");
+    int nseg = 0;
+    CK(cudaMemcpy(&nseg, &ctx->d_ctl->nseg[d][sp], sizeof(int), cudaMemcpyDeviceToHost), "segments");
+    std::vector<int> st(nseg + 1), sr(nseg > 0 ? nseg : 1);
+    if (nseg > 0) {
+        CK(cudaMemcpy(st.data(), D.seg_start[sp], sizeof(int) * (nseg + 1), cudaMemcpyDeviceToHost), "segments");
+        CK(cudaMemcpy(sr.data(), D.seg_src[sp], sizeof(int) * nseg, cudaMemcpyDeviceToHost), "segments");
+    }
+    long long span = 0;  // buffer records that hold the store
+    for (int k = 0; k < nseg; ++k)
+        if (st[k + 1] > st[k]) span = std::max(span, (long long)sr[k] + (st[k + 1] - st[k]));
     const size_t r = ctx->fp64 ? 8 : 4;
-    std::vector<unsigned char> buf(4 * r * (size_t)n);
-    if (n) CK(cudaMemcpy(buf.data(), D.p[ctx->cur][sp], 4 * r * n, cudaMemcpyDeviceToHost), "state p");
+    std::vector<int32_t> cb((size_t)span + 1);
+    std::vector<unsigned char> buf(4 * r * ((size_t)span + 1));
+    if (span) {
+        CK(cudaMemcpy(cb.data(), D.c[ctx->cur][sp], sizeof(int32_t) * span, cudaMemcpyDeviceToHost), "state c");
+        CK(cudaMemcpy(buf.data(), D.p[ctx->cur][sp], 4 * r * span, cudaMemcpyDeviceToHost), "state p");
+    }
     void* outs[4] = {f, vx, vy, vz};
-    for (int k = 0; k < 4; ++k) {
-        if (!outs[k]) continue;
-        unsigned char* o = (unsigned char*)outs[k];
-        for (int64_t i = 0; i < n; ++i) std::memcpy(o + r * i, buf.data() + r * (4 * i + k), r);
+    for (int k = 0; k < nseg; ++k) {
+        for (long long i = st[k]; i < st[k + 1] && i < n; ++i) {
+            const long long o = sr[k] + (i - st[k]);
+            if (c) c[i] = cb[o];
+            for (int q = 0; q < 4; ++q)
+                if (outs[q]) std::memcpy((unsigned char*)outs[q] + r * i, buf.data() + r * (4 * o + q), r);
+        }
     }
     return PIC_OK;
 }
@@ -675,6 +704,11 @@ extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     }
     long long v = n;
     CK(cudaMemcpy(&ctx->d_ctl->count[d][sp], &v, 8, cudaMemcpyHostToDevice), "count");
+    const int seg[2] = {0, (int)n}, zero = 0, one = 1;
+    CK(cudaMemcpy(D.seg_start[sp], seg, sizeof(seg), cudaMemcpyHostToDevice), "segments");
+    CK(cudaMemcpy(D.seg_src[sp], &zero, sizeof(int), cudaMemcpyHostToDevice), "segments");
+    CK(cudaMemcpy(D.first_seg[sp], &zero, sizeof(int), cudaMemcpyHostToDevice), "segments");
+    CK(cudaMemcpy(&ctx->d_ctl->nseg[d][sp], &one, sizeof(int), cudaMemcpyHostToDevice), "segments");
     return PIC_OK;
 }
 

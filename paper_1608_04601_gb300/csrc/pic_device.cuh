@@ -151,14 +151,4 @@ __device__ __forceinline__ void iso_dir(float ua, float ub, double& nx, double& 
     nz = ct;
 }
 
-// ---- ordered global status words for the decoupled look-back ----------------
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 }  // namespace pic

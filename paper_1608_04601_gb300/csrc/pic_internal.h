@@ -42,23 +42,40 @@ struct Consts {
     T sig0[2];         // initial Maxwellians
 };
 
+// A particle store (one species of one discharge) is a sequence of segments
+// of a record buffer: segment k holds slots [seg_start[k], seg_start[k+1]) at
+// buffer offsets seg_src[k] + (slot - seg_start[k]). After a load, an upload
+// or a sort the store is one dense segment; after a sweep every input tile of
+// TILE slots owns a region of 2 TILE records of the output buffer (a particle
+// and its same-species newborn at most), and the births of the other species
+// follow as one last segment in a region after all tile regions. Slots, and so
+// the random streams, number the particles exactly as a dense compacted store
+// would.
 struct Disc {
     int N, n_exc, n_pts, gas;
     uint32_t thr[2];          // null-collision candidate thresholds (of 2^32)
     uint32_t discharge_id;
     int steps_per_period;
     double dx, dt, V_rf, f_rf, w[2];
-    int has_see, pad_;
+    int has_see, tile;        // sweep tile (slots) of this context
     Consts<float> cf;
     Consts<double> cd;
     const void* Te;           // n_pts rows x 4 (T): cumulative sigma*v, electrons
     const void* Ti;           // n_pts rows x 2 (T): cumulative sigma*g, ions
     int32_t* c[2][2];         // [buffer][species] cell index
     void* p[2][2];            // [buffer][species] {f, vx, vy, vz} records
-    long long cap[2];         // capacity per species
-    int32_t* bc[2];           // births of the other species, by parent species
-    void* bp[2];
-    long long bcap;
+    long long cap[2];         // capacity per species (superparticles)
+    long long max_tiles[2];   // ceil(cap / tile)
+    long long R0[2];          // offset of the births region in a record buffer
+    long long rcap[2];        // records per buffer: max_tiles 2 tile + bcap
+    int* seg_start[2];        // [max_tiles + 2] segment table of the current store
+    int* seg_src[2];          // [max_tiles + 1]
+    int* first_seg[2];        // [max_tiles + 1] segment holding slot j tile
+    int* cnt_main[2];         // [max_tiles] same-species outputs of each sweep tile
+    int* cnt_birth[2];        // [max_tiles] other-species births of each sweep tile
+    int32_t* bc[2];           // births of the other species, by parent species:
+    void* bp[2];              //   tile t owns records [t tile, (t+1) tile)
+    long long bcap;           // births region size in the record buffers
     void* E;                  // node field for the gather (T), N+1
     double* E64;              // node field, FP64
     double* phi;              // potential, FP64
@@ -76,13 +93,11 @@ struct Ctl {
     long long step;           // current step index n
     unsigned int tile_ctr;    // sweep tile dispenser
     unsigned int done;        // sweep CTAs finished
-    unsigned int epoch;       // sweep launch counter (look-back status tag)
     unsigned int fin_done;    // finalize CTAs finished
     int error;                // ERR_* bits
-    int pad_;
-    long long count[MAXD][2];     // superparticles per store (sweep input)
-    long long out_main[MAXD][2];  // same-species outputs of the last sweep
-    long long out_birth[MAXD][2]; // other-species births of the last sweep, by parent species
+    long long count[MAXD][2]; // superparticles per store
+    long long count_in[MAXD][2]; // the counts the last sweep read (its tiles)
+    int nseg[MAXD][2];        // segments per store
     long long acc_steps[MAXD];
     double E0_last[MAXD];
 };

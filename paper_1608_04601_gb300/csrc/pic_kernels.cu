@@ -1,20 +1,23 @@
 // pic_kernels.cu -- CUDA kernels (sm_103a) of the 1d3v PIC/MCC time step of
 // arXiv:1608.04601, section "PIC/MCC simulation procedure".
 //
-// One time step is three launches:
+// One time step is two launches (and the sort every K steps):
 //   k_sweep     persistent; every CTA takes tiles of particles in increasing
 //               order from a global dispenser. Per particle: CIC gather of E_n
 //               (node field held in shared memory), half kick, null-collision
-//               MCC on Philox streams, half kick, drift, wall test; per tile a
-//               block scan and a decoupled look-back over the tiles of its
-//               store give every surviving / newborn particle its output slot
-//               (survivors in input order, each followed by its same-species
-//               newborn); CIC deposit into a shared-memory int64 histogram
-//               that is flushed with global atomics.
-//   k_finalize  one CTA per discharge: births of the other species appended,
-//               Poisson (Eq. poisson, rf Dirichlet boundary) in FP64 by two
-//               block scans, node field, cycle-average accumulators.
-//   sort        every K steps: stable counting sort of each store by cell.
+//               MCC on Philox streams, half kick, drift, wall test. A block
+//               scan orders each tile's outputs (particles in slot order, each
+//               followed by its same-species newborn), written into the tile's
+//               own region of the output buffer; no tile waits for another.
+//               CIC deposit into a shared-memory int64 histogram, flushed
+//               with global atomics.
+//   k_finalize  one CTA per discharge: the new segment tables (an exclusive
+//               scan of the per-tile output counts), births of the other
+//               species compacted behind them, Poisson (Eq. poisson, rf
+//               Dirichlet boundary) in FP64 by two block scans, node field,
+//               cycle-average accumulators.
+//   sort        every K steps: stable counting sort of each store by cell
+//               into a dense store.
 #include "pic_internal.h"
 #include "pic_device.cuh"
 
@@ -27,7 +30,6 @@ namespace pic {
 #define TWO32_D 4294967296.0
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;  // ~seconds: then report ERR_TIMEOUT and go on
 
 template <typename T> __device__ __forceinline__ const Consts<T>& consts_of(const Disc& d);
 template <> __device__ __forceinline__ const Consts<float>& consts_of<float>(const Disc& d) { return d.cf; }
@@ -62,10 +64,58 @@ struct Seg {
     unsigned long long* Dother;
     unsigned long long* Qg;
     unsigned long long* cnt;
+    const int* seg_start;
+    const int* seg_src;
+    const int* first_seg;
+    int nseg;
+    int* cnt_main;
+    int* cnt_birth;
 };
 
-__device__ __forceinline__ unsigned long long mk_status(unsigned epoch, unsigned flag, unsigned long long v) {
-    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (v & 0x3FFFFFFFull);
+// Window of the segment table staged in shared memory for one tile: segments
+// k0 .. k0+nw-1 and the start of segment k0+nw.
+constexpr int SEGWIN = 32;
+struct SegWin {
+    int k0, nw;
+    int start[SEGWIN + 1];
+    int src[SEGWIN];
+};
+
+// Loaded by one warp: the window starting at segment k0.
+__device__ __forceinline__ void seg_window_load(SegWin& W, const int* __restrict__ seg_start,
+                                                const int* __restrict__ seg_src, int nseg, int k0, int lane) {
+    const int nw = min(SEGWIN, nseg - k0);
+    if (lane == 0) {
+        W.k0 = k0;
+        W.nw = nw;
+        W.start[SEGWIN] = 0x7FFFFFFF;
+    }
+    const int k = k0 + lane;
+    W.start[lane] = (lane <= nw && k <= nseg) ? seg_start[k] : 0x7FFFFFFF;
+    W.src[lane] = (lane < nw) ? seg_src[k] : 0;
+    if (lane == 0 && nw == SEGWIN) W.start[SEGWIN] = seg_start[k0 + SEGWIN];
+}
+
+// Buffer offset of a slot: the last segment whose start is <= slot holds it.
+__device__ __forceinline__ long long seg_offset(const SegWin& W, const int* __restrict__ seg_start,
+                                                const int* __restrict__ seg_src, int nseg, long long slot) {
+    if (slot < (long long)W.start[1]) return (long long)W.src[0] + (slot - W.start[0]);  // first segment
+    if (slot < (long long)W.start[W.nw]) {
+        int lo = 0, hi = W.nw - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((long long)W.start[mid] <= slot) lo = mid;
+            else hi = mid - 1;
+        }
+        return (long long)W.src[lo] + (slot - W.start[lo]);
+    }
+    int lo = W.k0 + W.nw, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)seg_start[mid] <= slot) lo = mid;
+        else hi = mid - 1;
+    }
+    return (long long)seg_src[lo] + (slot - seg_start[lo]);
 }
 
 // Drift x_{n+1} = x_n + v_z dt in cell units. Returns -1 (inside) with the new
@@ -116,178 +166,149 @@ __device__ __forceinline__ unsigned long long cic_F(double f) {
     return __double2ull_rn(__dmul_rn(f, TWO32_D));  // may round to 2^32
 }
 
-// Warp-aggregated shared-memory histogram update. key < 0: nothing. Lanes whose keys equal their
-// left neighbour's form a run (the store is kept cell-sorted, so runs are long); one 64-bit warp
-// scan of the packed values gives each run's sum, and the run's last lane applies it:
-//   deposit (pair = false): v = 2^40 + F  ->  node key += count 2^32 - sum F, node key+1 += sum F
-//   moment  (pair = true):  v = lo + hi 2^32 -> node key += sum lo, node key+1 += sum hi
-// When most keys in the warp differ, plain atomics are cheaper and are used instead.
+// Warp-aggregated shared-memory histogram update. key < 0: nothing. Lanes with
+// equal keys are grouped (match_any); each group's sums are reduced in 32-bit
+// parts (redux) and its first lane applies them:
+//   deposit (PAIR = false): v = 2^40 + F  ->  node key += count 2^32 - sum F, node key+1 += sum F
+//   moment  (PAIR = true):  v = lo + hi 2^32 (lo, hi < 2^26) -> node key += sum lo, key+1 += sum hi
 template <bool PAIR>
 __device__ __forceinline__ void warp_hist(unsigned long long* h, int key, unsigned long long v, int lane) {
-    const int prev = __shfl_up_sync(FULL, key, 1);
-    const bool head = lane == 0 || prev != key;
-    const unsigned heads = __ballot_sync(FULL, head);
-    if (__popc(heads) > 12) {
-        if (key >= 0) {
-            if (PAIR) {
-                const unsigned long long lo = v & 0xFFFFFFFFull, hi = v >> 32;
-                if (lo) sadd64(&h[key], lo);
-                if (hi) sadd64(&h[key + 1], hi);
-            } else {
-                const unsigned long long F = v & ((1ull << 40) - 1);
-                sadd64(&h[key], (1ull << 32) - F);
-                if (F) sadd64(&h[key + 1], F);
-            }
-        }
-        return;
-    }
-    unsigned long long x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += t;
-    }
-    const unsigned below = heads & (0xFFFFFFFFu >> (31 - lane));
-    const int hl = 31 - __clz(below);
-    const unsigned long long before = __shfl_sync(FULL, x, hl > 0 ? hl - 1 : 0);
-    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (tail && key >= 0) {
-        const unsigned long long sum = x - (hl > 0 ? before : 0ull);
-        if (PAIR) {
-            const unsigned long long lo = sum & 0xFFFFFFFFull, hi = sum >> 32;
+    const unsigned peers = __match_any_sync(FULL, key);
+    const bool leader = lane == __ffs(peers) - 1;
+    if (PAIR) {
+        const unsigned lo = __reduce_add_sync(peers, (unsigned)v);
+        const unsigned hi = __reduce_add_sync(peers, (unsigned)(v >> 32));
+        if (leader && key >= 0) {
             if (lo) sadd64(&h[key], lo);
             if (hi) sadd64(&h[key + 1], hi);
-        } else {
-            const unsigned long long cnt = sum >> 40, F = sum & ((1ull << 40) - 1);
-            sadd64(&h[key], (cnt << 32) - F);
-            if (F) sadd64(&h[key + 1], F);
+        }
+    } else {
+        const unsigned long long F = v & ((1ull << 40) - 1);  // <= 2^32
+        const unsigned fh = __reduce_add_sync(peers, (unsigned)(F >> 16));
+        const unsigned fl = __reduce_add_sync(peers, (unsigned)(F & 0xFFFFu));
+        if (leader && key >= 0) {
+            const unsigned long long sF = ((unsigned long long)fh << 16) + fl;
+            sadd64(&h[key], ((unsigned long long)__popc(peers) << 32) - sF);
+            if (sF) sadd64(&h[key + 1], sF);
         }
     }
 }
 
-// Advance one particle by one step. Returns flags: bit0 particle stays,
-// bit1 same-species newborn stays, bit2 other-species birth stays,
-// bit3 candidate for a collision.
+// One collision candidate, queued by its warp in shared memory: the owner
+// writes the particle (cell, offset, gathered field, v_n); the lane that
+// processes the collision writes back the new velocity and the newborns after
+// their first drift.
 template <typename T>
-__device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict__ sE, unsigned long long* sH,
-                                            unsigned long long& qv, unsigned* sC, uint32_t slot,
-                                            long long step, unsigned long long seed, int c, T f, T vx, T vy, T vz,
-                                            Part<T>& p0, Part<T>& p1, Part<T>& p2, int& err) {
+struct QEnt {
+    uint32_t slot;
+    int c;
+    uint32_t out;     // bit1 same-species newborn stays, bit2 other-species birth stays
+    int pad_;
+    T f, ef;
+    T vx, vy, vz;     // in: v_n; out: velocity after the collision
+    Part<T> p1, p2;   // newborns (same species, other species) at x_{n+1}
+};
+
+// The collision of a queued candidate (null-collision method: process
+// selection against the cumulative rate tables, then the kinematics).
+template <typename T>
+__device__ __noinline__ void collide(const Seg<T>& S, QEnt<T>& q, long long step, unsigned long long seed,
+                                     unsigned long long* sH, unsigned* sC, int& err) {
     using Row4 = typename T4<T>::type;
     using Row2 = typename T4<T>::two;
     const Consts<T>& K = S.k;
     const int N = S.N;
+    const uint32_t slot = q.slot;
+    T vx = q.vx, vy = q.vy, vz = q.vz;
     uint32_t out = 0;
-    const T E0 = sE[c], E1 = sE[c + 1];
-    const T ef = fma_(f, sub_(E1, E0), E0);
     if (S.sp == 0) {
-        vz = fma_(K.K[0], ef, vz);  // v_n
         const T e2 = fma_(vx, vx, fma_(vy, vy, mul_(vz, vz)));
-        {   // energy moment at (x_n, v_n) in 2^-12 eV, clamped at 2^26 (16384 eV)
-            T eq = mul_(e2, K.kappa_E);
-            if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
-            const unsigned long long Et = rint_u32(eq);
-            const unsigned long long Eh = rint_u32(mul_(eq, f));
-            qv = (Et - Eh) | (Eh << 32);
-        }
-        const U4 r = draw(seed, slot, step, 0, 0, S.did);
         bool child = false;
         T cvx = 0, cvy = 0, cvz = 0, ivx = 0, ivy = 0, ivz = 0;
-        if (r.x < S.thr) {
-            out |= 8u;
-            const T xi = mul_(e2, K.kappa_e);
-            const Row4* Te = reinterpret_cast<const Row4*>(S.Te);
-            T C0, C1, C2, C3;
-            if (!(xi < (T)(S.n_pts - 1))) {
-                const Row4 a = Te[S.n_pts - 1];
-                C0 = a.x; C1 = a.y; C2 = a.z; C3 = a.w;
-                atomicAdd(&sC[CNT_CLAMP + 0], 1u);
-            } else {
-                const int i = (int)xi;
-                const T fr = sub_(xi, (T)i);
-                const Row4 a = Te[i], b = Te[i + 1];
-                C0 = fma_(fr, sub_(b.x, a.x), a.x);
-                C1 = fma_(fr, sub_(b.y, a.y), a.y);
-                C2 = fma_(fr, sub_(b.z, a.z), a.z);
-                C3 = fma_(fr, sub_(b.w, a.w), a.w);
-            }
-            const T R = mul_((T)u01(r.y), K.kmax_e);
-            const int j = (R < C0) ? 0 : (R < C1) ? 1 : (R < C2) ? 2 : (R < C3) ? 3 : 4;
-            if (j < 4) {
-                T nx, ny, nz;
-                if (j == 0) {  // elastic, target at rest: v' = beta v + (1-beta)|v| n
-                    const T g = sqrt_(e2);
+        const U4 r = draw(seed, slot, step, 0, 0, S.did);
+        const T xi = mul_(e2, K.kappa_e);
+        const Row4* Te = reinterpret_cast<const Row4*>(S.Te);
+        T C0, C1, C2, C3;
+        if (!(xi < (T)(S.n_pts - 1))) {
+            const Row4 a = Te[S.n_pts - 1];
+            C0 = a.x; C1 = a.y; C2 = a.z; C3 = a.w;
+            atomicAdd(&sC[CNT_CLAMP + 0], 1u);
+        } else {
+            const int i = (int)xi;
+            const T fr = sub_(xi, (T)i);
+            const Row4 a = Te[i], b = Te[i + 1];
+            C0 = fma_(fr, sub_(b.x, a.x), a.x);
+            C1 = fma_(fr, sub_(b.y, a.y), a.y);
+            C2 = fma_(fr, sub_(b.z, a.z), a.z);
+            C3 = fma_(fr, sub_(b.w, a.w), a.w);
+        }
+        const T R = mul_((T)u01(r.y), K.kmax_e);
+        const int j = (R < C0) ? 0 : (R < C1) ? 1 : (R < C2) ? 2 : (R < C3) ? 3 : 4;
+        if (j < 4) {
+            T nx, ny, nz;
+            if (j == 0) {  // elastic, target at rest: v' = beta v + (1-beta)|v| n
+                const T g = sqrt_(e2);
+                iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
+                const T og = mul_(K.omb, g);
+                vx = fma_(K.beta, vx, mul_(og, nx));
+                vy = fma_(K.beta, vy, mul_(og, ny));
+                vz = fma_(K.beta, vz, mul_(og, nz));
+                atomicAdd(&sC[CNT_COLL_E + 0], 1u);
+            } else if (j <= S.n_exc) {  // excitation of level j
+                const T e2n = sub_(e2, K.de2_exc[j - 1]);
+                if (e2n > (T)0) {
+                    const T sp = sqrt_(e2n);
                     iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
-                    const T og = mul_(K.omb, g);
-                    vx = fma_(K.beta, vx, mul_(og, nx));
-                    vy = fma_(K.beta, vy, mul_(og, ny));
-                    vz = fma_(K.beta, vz, mul_(og, nz));
-                    atomicAdd(&sC[CNT_COLL_E + 0], 1u);
-                } else if (j <= S.n_exc) {
-                    // excitation of level j
-                    const T e2n = sub_(e2, K.de2_exc[j - 1]);
-                    if (e2n > (T)0) {
-                        const T sp = sqrt_(e2n);
-                        iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
-                        vx = mul_(sp, nx);
-                        vy = mul_(sp, ny);
-                        vz = mul_(sp, nz);
-                        atomicAdd(&sC[CNT_COLL_E + j], 1u);
-                    } else {
-                        atomicAdd(&sC[CNT_NULL_INEL], 1u);
-                    }
-                } else {  // ionization: remaining energy shared equally
-                    const T e2r = sub_(e2, K.de2_iz);
-                    if (e2r > (T)0) {
-                        const T sp = sqrt_(mul_((T)0.5, e2r));
-                        iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
-                        vx = mul_(sp, nx);
-                        vy = mul_(sp, ny);
-                        vz = mul_(sp, nz);
-                        const U4 q = draw(seed, slot, step, 0, 1, S.did);
-                        const U4 w = draw(seed, slot, step, 0, 2, S.did);
-                        iso_dir(u01(q.x), u01(q.y), nx, ny, nz);
-                        cvx = mul_(sp, nx);
-                        cvy = mul_(sp, ny);
-                        cvz = mul_(sp, nz);
-                        float b0, b1, b2, b3;
-                        box_muller(u01(q.z), u01(q.w), b0, b1);
-                        box_muller(u01(w.x), u01(w.y), b2, b3);
-                        ivx = mul_(K.sig_n, (T)b0);
-                        ivy = mul_(K.sig_n, (T)b1);
-                        ivz = mul_(K.sig_n, (T)b2);
-                        child = true;
-                        atomicAdd(&sC[CNT_COLL_E + 3], 1u);
-                    } else {
-                        atomicAdd(&sC[CNT_NULL_INEL], 1u);
-                    }
+                    vx = mul_(sp, nx);
+                    vy = mul_(sp, ny);
+                    vz = mul_(sp, nz);
+                    atomicAdd(&sC[CNT_COLL_E + j], 1u);
+                } else {
+                    atomicAdd(&sC[CNT_NULL_INEL], 1u);
+                }
+            } else {  // ionization: remaining energy shared equally
+                const T e2r = sub_(e2, K.de2_iz);
+                if (e2r > (T)0) {
+                    const T sp = sqrt_(mul_((T)0.5, e2r));
+                    iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
+                    vx = mul_(sp, nx);
+                    vy = mul_(sp, ny);
+                    vz = mul_(sp, nz);
+                    const U4 q1 = draw(seed, slot, step, 0, 1, S.did);
+                    const U4 w = draw(seed, slot, step, 0, 2, S.did);
+                    iso_dir(u01(q1.x), u01(q1.y), nx, ny, nz);
+                    cvx = mul_(sp, nx);
+                    cvy = mul_(sp, ny);
+                    cvz = mul_(sp, nz);
+                    float b0, b1, b2, b3;
+                    box_muller(u01(q1.z), u01(q1.w), b0, b1);
+                    box_muller(u01(w.x), u01(w.y), b2, b3);
+                    ivx = mul_(K.sig_n, (T)b0);
+                    ivy = mul_(K.sig_n, (T)b1);
+                    ivz = mul_(K.sig_n, (T)b2);
+                    child = true;
+                    atomicAdd(&sC[CNT_COLL_E + 3], 1u);
+                } else {
+                    atomicAdd(&sC[CNT_NULL_INEL], 1u);
                 }
             }
         }
-        vz = fma_(K.K[0], ef, vz);
-        int cn;
-        T fn;
-        int side = drift(N, K.dtdx, c, f, vz, cn, fn, err);
-        if (side < 0) {
-            p0 = Part<T>{cn, fn, vx, vy, vz};
-            out |= 1u;
-        } else {
-            atomicAdd(&sC[CNT_ABS + side], 1u);
-        }
-        if (child) {
-            cvz = fma_(K.K[0], ef, cvz);
-            side = drift(N, K.dtdx, c, f, cvz, cn, fn, err);
+        if (child) {  // newborns: second half kick and drift from the parent's position
+            int cn;
+            T fn;
+            cvz = fma_(K.K[0], q.ef, cvz);
+            int side = drift(N, K.dtdx, q.c, q.f, cvz, cn, fn, err);
             if (side < 0) {
-                p1 = Part<T>{cn, fn, cvx, cvy, cvz};
+                q.p1 = Part<T>{cn, fn, cvx, cvy, cvz};
                 shist_add(sH, cn, cic_F(fn));
                 out |= 2u;
             } else {
                 atomicAdd(&sC[CNT_ABS + side], 1u);
             }
-            ivz = fma_(K.K[1], ef, ivz);
-            side = drift(N, K.dtdx, c, f, ivz, cn, fn, err);
+            ivz = fma_(K.K[1], q.ef, ivz);
+            side = drift(N, K.dtdx, q.c, q.f, ivz, cn, fn, err);
             if (side < 0) {
-                p2 = Part<T>{cn, fn, ivx, ivy, ivz};
+                q.p2 = Part<T>{cn, fn, ivx, ivy, ivz};
                 hist_add(S.Dother, cn, cic_F(fn));
                 out |= 4u;
             } else {
@@ -295,73 +316,66 @@ __device__ __forceinline__ uint32_t advance(const Seg<T>& S, const T* __restrict
             }
         }
     } else {
-        vz = fma_(K.K[1], ef, vz);  // v_n
         const U4 r = draw(seed, slot, step, 1, 0, S.did);
-        if (r.x < S.thr) {
-            out |= 8u;
-            const U4 q = draw(seed, slot, step, 1, 1, S.did);
-            float a0, a1, a2, a3;
-            box_muller(u01(q.x), u01(q.y), a0, a1);
-            box_muller(u01(q.z), u01(q.w), a2, a3);
-            const T vnx = mul_(K.sig_n, (T)a0), vny = mul_(K.sig_n, (T)a1), vnz = mul_(K.sig_n, (T)a2);
-            const T gx = sub_(vx, vnx), gy = sub_(vy, vny), gz = sub_(vz, vnz);
-            const T g2 = fma_(gx, gx, fma_(gy, gy, mul_(gz, gz)));
-            const T xi = mul_(g2, K.kappa_i);
-            const Row2* Ti = reinterpret_cast<const Row2*>(S.Ti);
-            T C0, C1;
-            if (!(xi < (T)(S.n_pts - 1))) {
-                const Row2 a = Ti[S.n_pts - 1];
-                C0 = a.x; C1 = a.y;
-                atomicAdd(&sC[CNT_CLAMP + 1], 1u);
-            } else {
-                const int i = (int)xi;
-                const T fr = sub_(xi, (T)i);
-                const Row2 a = Ti[i], b = Ti[i + 1];
-                C0 = fma_(fr, sub_(b.x, a.x), a.x);
-                C1 = fma_(fr, sub_(b.y, a.y), a.y);
-            }
-            const T R = mul_((T)u01(r.y), K.kmax_i);
-            if (R < C0) {  // isotropic in the centre-of-mass frame, equal masses
-                const T hg = mul_((T)0.5, sqrt_(g2));
-                T nx, ny, nz;
-                iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
-                vx = fma_(hg, nx, mul_(add_(vx, vnx), (T)0.5));
-                vy = fma_(hg, ny, mul_(add_(vy, vny), (T)0.5));
-                vz = fma_(hg, nz, mul_(add_(vz, vnz), (T)0.5));
-                atomicAdd(&sC[CNT_COLL_I + 0], 1u);
-            } else if (R < C1) {  // backward: the ion takes the atom's velocity
-                vx = vnx;
-                vy = vny;
-                vz = vnz;
-                atomicAdd(&sC[CNT_COLL_I + 1], 1u);
-            }
-        }
-        vz = fma_(K.K[1], ef, vz);
-        int cn;
-        T fn;
-        const int side = drift(N, K.dtdx, c, f, vz, cn, fn, err);
-        if (side < 0) {
-            p0 = Part<T>{cn, fn, vx, vy, vz};
-            out |= 1u;
+        const U4 q1 = draw(seed, slot, step, 1, 1, S.did);
+        float a0, a1, a2, a3;
+        box_muller(u01(q1.x), u01(q1.y), a0, a1);
+        box_muller(u01(q1.z), u01(q1.w), a2, a3);
+        const T vnx = mul_(K.sig_n, (T)a0), vny = mul_(K.sig_n, (T)a1), vnz = mul_(K.sig_n, (T)a2);
+        const T gx = sub_(vx, vnx), gy = sub_(vy, vny), gz = sub_(vz, vnz);
+        const T g2 = fma_(gx, gx, fma_(gy, gy, mul_(gz, gz)));
+        const T xi = mul_(g2, K.kappa_i);
+        const Row2* Ti = reinterpret_cast<const Row2*>(S.Ti);
+        T C0, C1;
+        if (!(xi < (T)(S.n_pts - 1))) {
+            const Row2 a = Ti[S.n_pts - 1];
+            C0 = a.x; C1 = a.y;
+            atomicAdd(&sC[CNT_CLAMP + 1], 1u);
         } else {
-            atomicAdd(&sC[CNT_ABS + 2 + side], 1u);
-            if (S.has_see) {
-                const U4 w = draw(seed, slot, step, 1, 3, S.did);
-                if ((T)u01(w.x) < K.gamma) {
-                    const T vn = mul_(K.sig_see_n, (T)__fsqrt_rn(-own_logf(u01(w.y))));
-                    float t0, t1;
-                    box_muller(u01(w.z), u01(w.w), t0, t1);
-                    const int ce = side == 0 ? 0 : N - 1;
-                    const T fe = side == 0 ? (T)0 : one_minus_ulp<T>();
-                    p2 = Part<T>{ce, fe, mul_(K.sig_see, (T)t0), mul_(K.sig_see, (T)t1), side == 0 ? vn : -vn};
-                    hist_add(S.Dother, ce, cic_F(fe));
-                    atomicAdd(&sC[CNT_SEE], 1u);
-                    out |= 4u;
-                }
-            }
+            const int i = (int)xi;
+            const T fr = sub_(xi, (T)i);
+            const Row2 a = Ti[i], b = Ti[i + 1];
+            C0 = fma_(fr, sub_(b.x, a.x), a.x);
+            C1 = fma_(fr, sub_(b.y, a.y), a.y);
+        }
+        const T R = mul_((T)u01(r.y), K.kmax_i);
+        if (R < C0) {  // isotropic in the centre-of-mass frame, equal masses
+            const T hg = mul_((T)0.5, sqrt_(g2));
+            T nx, ny, nz;
+            iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
+            vx = fma_(hg, nx, mul_(add_(vx, vnx), (T)0.5));
+            vy = fma_(hg, ny, mul_(add_(vy, vny), (T)0.5));
+            vz = fma_(hg, nz, mul_(add_(vz, vnz), (T)0.5));
+            atomicAdd(&sC[CNT_COLL_I + 0], 1u);
+        } else if (R < C1) {  // backward: the ion takes the atom's velocity
+            vx = vnx;
+            vy = vny;
+            vz = vnz;
+            atomicAdd(&sC[CNT_COLL_I + 1], 1u);
         }
     }
-    return out;
+    q.vx = vx;
+    q.vy = vy;
+    q.vz = vz;
+    q.out = out;
+}
+
+// Secondary electron of an ion absorbed at electrode `side` (added option).
+template <typename T>
+__device__ __noinline__ bool emit_see(const Seg<T>& S, uint32_t slot, long long step, unsigned long long seed,
+                                      int side, Part<T>& p, unsigned* sC) {
+    const Consts<T>& K = S.k;
+    const U4 w = draw(seed, slot, step, 1, 3, S.did);
+    if (!((T)u01(w.x) < K.gamma)) return false;
+    const T vn = mul_(K.sig_see_n, (T)__fsqrt_rn(-own_logf(u01(w.y))));
+    float t0, t1;
+    box_muller(u01(w.z), u01(w.w), t0, t1);
+    const int ce = side == 0 ? 0 : S.N - 1;
+    const T fe = side == 0 ? (T)0 : one_minus_ulp<T>();
+    p = Part<T>{ce, fe, mul_(K.sig_see, (T)t0), mul_(K.sig_see, (T)t1), side == 0 ? vn : -vn};
+    hist_add(S.Dother, ce, cic_F(fe));
+    atomicAdd(&sC[CNT_SEE], 1u);
+    return true;
 }
 
 template <typename T>
@@ -395,28 +409,45 @@ __device__ __forceinline__ void load_rec<double>(const void* p, long long i, dou
     f = a.x; vx = a.y; vy = b.x; vz = b.y;
 }
 
-// ---------------------------------------------------------------------------
+// Dynamic shared memory of the sweep: histogram and energy moment (u64, N+1
+// each), the node field (T, N+1), then the warps' candidate queues.
+template <typename T>
+__host__ __device__ constexpr size_t sweep_queue_offset(int max_N) {
+    return (((size_t)(max_N + 1) * (16 + sizeof(T)) + 15) / 16) * 16;
+}
 template <typename T, int BLOCK, int PPT>
-__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k_sweep(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
-                                                 unsigned long long* __restrict__ st_main,
-                                                 unsigned long long* __restrict__ st_bagg,
-                                                 unsigned long long* __restrict__ st_binc, int in_buf,
-                                                 unsigned long long seed, int max_N) {
+__host__ __device__ constexpr size_t sweep_smem(int max_N) {
+    return sweep_queue_offset<T>(max_N) + sizeof(QEnt<T>) * (BLOCK / 32) * 32 * (PPT < 2 ? PPT : 2);
+}
+
+// ---------------------------------------------------------------------------
+// The sweep. Persistent CTAs take tiles of TILE = BLOCK x PPT slots of every
+// store (discharge, species) in increasing order from a global dispenser.
+// Tile t of a store reads its slots through the store's segment table and
+// writes its outputs, in slot order, into its own region of the output buffer:
+// same-species outputs at [2 TILE t, ...), other-species births at [TILE t, ...)
+// of the birth buffer; it records both counts. No tile waits for another.
+template <typename T, int BLOCK, int PPT>
+__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
+    k_sweep(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl, int in_buf, unsigned long long seed,
+            int max_N) {
     constexpr int TILE = BLOCK * PPT;
     constexpr int NW = BLOCK / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem_raw);
     unsigned long long* s_Q = s_hist + (max_N + 1);
     T* s_E = reinterpret_cast<T*>(s_Q + (max_N + 1));
+    QEnt<T>* s_q = reinterpret_cast<QEnt<T>*>(smem_raw + sweep_queue_offset<T>(max_N));
 
     __shared__ long long s_segstart[2 * MAXD + 1];
     __shared__ Seg<T> S;
+    __shared__ SegWin W;
     __shared__ unsigned int s_tile;
-    __shared__ unsigned int s_epoch;
     __shared__ long long s_step;
-    __shared__ uint32_t s_wsum[PPT][NW];
-    __shared__ uint32_t s_ktot[PPT];
-    __shared__ unsigned long long s_excl[2];
+    constexpr int BATCH = PPT < 2 ? PPT : 2;   // iterations whose candidates share one queue pass
+    constexpr int QCAP = 32 * BATCH;           // queue entries per warp
+    __shared__ uint32_t s_wsum[BATCH][NW];
+    __shared__ uint32_t s_ktot[BATCH];
     __shared__ unsigned s_cnt[NCNT];
     __shared__ int s_err;
 
@@ -429,13 +460,11 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k
             acc += (n + TILE - 1) / TILE;
         }
         s_segstart[2 * n_disc] = acc;
-        s_epoch = ctl->epoch;
         s_step = ctl->step;
         s_err = 0;
     }
     __syncthreads();
     const long long total_tiles = s_segstart[2 * n_disc];
-    const unsigned epoch = s_epoch;
     const long long step = s_step;
     int cur_seg = -1, cur_d = -1;
     int err = 0;
@@ -461,7 +490,7 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k
         if (g >= total_tiles) break;
         int seg = 0;
         {
-            int lo = 0, hi = 2 * n_disc - 1;  // largest seg with segstart <= g and non-empty
+            int lo = 0, hi = 2 * n_disc - 1;  // largest store with segstart <= g
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (s_segstart[mid] <= g) lo = mid;
@@ -500,6 +529,12 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k
                 S.Dother = D.D[1 - sp];
                 S.Qg = D.Q;
                 S.cnt = D.cnt;
+                S.seg_start = D.seg_start[sp];
+                S.seg_src = D.seg_src[sp];
+                S.first_seg = D.first_seg[sp];
+                S.nseg = ctl->nseg[d][sp];
+                S.cnt_main = D.cnt_main[sp];
+                S.cnt_birth = D.cnt_birth[sp];
             }
             if (tid < NCNT) s_cnt[tid] = 0;
             __syncthreads();
@@ -518,6 +553,9 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k
 
         const long long ts = g - S.tile0;
         const long long base = ts * TILE;
+        if (warp == 0)
+            seg_window_load(W, S.seg_start, S.seg_src, S.nseg, S.nseg <= 1 ? 0 : S.first_seg[ts], lane);
+        __syncthreads();
         int cin[PPT];
         T fin[PPT], vxin[PPT], vyin[PPT], vzin[PPT];
 #pragma unroll
@@ -525,171 +563,171 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k
             const long long slot = base + (long long)k * BLOCK + tid;
             cin[k] = -1;
             if (slot < S.n) {
-                const int cc = __ldcs(S.cin + slot);
-                load_rec<T>(S.pin, slot, fin[k], vxin[k], vyin[k], vzin[k]);
+                const long long off = seg_offset(W, S.seg_start, S.seg_src, S.nseg, slot);
+                const int cc = __ldcs(S.cin + off);
+                load_rec<T>(S.pin, off, fin[k], vxin[k], vyin[k], vzin[k]);
                 if ((unsigned)cc < (unsigned)S.N) cin[k] = cc;
                 else err |= ERR_NONFINITE;  // corrupt cell index: dropped and reported
             }
         }
-        Part<T> P0[PPT], P1[PPT], P2[PPT];
-        uint32_t fl[PPT];
+        // Candidate words: slots 4q..4q+3 take the four words of one Philox call (call 4,
+        // counter word 0 = q). Lane l of warp w computes group q = (base + k BLOCK + 32 w) / 4 + j
+        // for k = i / 8, j = i % 8, i = l + 32 m; iteration k takes its word by shuffle.
+        constexpr int NG = (8 * PPT + 31) / 32;
+        U4 cw[NG];
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            fl[k] = 0;
-            unsigned long long qv = 0;
-            if (cin[k] >= 0) {
-                const uint32_t slot = (uint32_t)(base + (long long)k * BLOCK + tid);
-                fl[k] = advance<T>(S, s_E, s_hist, qv, s_cnt, slot, step, seed, cin[k], fin[k], vxin[k], vyin[k],
-                                   vzin[k], P0[k], P1[k], P2[k], err);
-            }
-            const unsigned cm = __ballot_sync(FULL, (fl[k] & 8u) != 0);
-            if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + S.sp], (unsigned)__popc(cm));
-            // deposit of the particle at x_{n+1}, and (electrons) the energy moment at x_n
-            const bool alive = (fl[k] & 1u) != 0;
-            warp_hist<false>(s_hist, alive ? P0[k].c : -1, alive ? (1ull << 40) + cic_F(P0[k].f) : 0ull, lane);
-            if (S.sp == 0) warp_hist<true>(s_Q, cin[k], qv, lane);
+        for (int m = 0; m < NG; ++m) {
+            const int i = lane + 32 * m;
+            const long long q = (base + (long long)(i >> 3) * BLOCK + 32 * warp) / 4 + (i & 7);
+            cw[m] = draw(seed, (uint32_t)q, step, S.sp, 4, S.did);
         }
-        // block scan of (same-species outputs | births << 16) per k, in slot order
-        uint32_t v[PPT], incl[PPT];
+        QEnt<T>* Q = s_q + warp * QCAP;
+        const T Ksp = S.k.K[S.sp];
+        long long offA = ts * (2 * TILE), offB = ts * TILE;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            v[k] = (fl[k] & 1u) + ((fl[k] >> 1) & 1u) + (((fl[k] >> 2) & 1u) << 16);
-            incl[k] = v[k];
-        }
+        for (int b = 0; b < PPT; b += BATCH) {
+            // phase A: gather, first half kick, energy moment, candidate test; candidates queued
+            T ef[BATCH];
+            uint32_t fl[BATCH];
+            int qi[BATCH];
+            int qn = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const uint32_t t = __shfl_up_sync(FULL, incl[k], o);
-                if (lane >= o) incl[k] += t;
-            }
-        }
-        if (lane == 31) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) s_wsum[k][warp] = incl[k];
-        }
-        __syncthreads();
-        if (warp == 0) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const uint32_t own = lane < NW ? s_wsum[k][lane] : 0u;
-                uint32_t x = own;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(FULL, x, o);
-                    if (lane >= o) x += t;
-                }
-                if (lane < NW) s_wsum[k][lane] = x - own;
-                if (lane == NW - 1) s_ktot[k] = x;
-            }
-        }
-        __syncthreads();
-        unsigned long long A = 0, B = 0;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            A += s_ktot[k] & 0xFFFFu;
-            B += s_ktot[k] >> 16;
-        }
-        // decoupled look-back over the tiles of this store
-        if (warp == 0) {
-            unsigned long long exA = 0, exB = 0;
-            const long long first = S.tile0;
-            if (g == first) {
-                if (lane == 0) {
-                    st_binc[g] = B;
-                    st_release(&st_main[g], mk_status(epoch, 2, A));
-                }
-            } else {
-                if (lane == 0) {
-                    st_bagg[g] = B;
-                    st_release(&st_main[g], mk_status(epoch, 1, A));
-                }
-                // Look back in windows of LB_W x 32 predecessors: all of a window's status
-                // words are requested at once, then its 32-tile groups are examined nearest
-                // first; the walk stops at the nearest inclusive prefix.
-                constexpr int LB_W = 8;
-                long long j = g - 1;
-                bool found = false;
-                while (!found) {
-                    unsigned long long w[LB_W];
-#pragma unroll
-                    for (int i = 0; i < LB_W; ++i) {
-                        const long long idx = j - i * 32 - lane;
-                        w[i] = idx >= first ? ld_acquire(&st_main[idx]) : mk_status(epoch, 2, 0);
+            for (int kk = 0; kk < BATCH; ++kk) {
+                const int k = b + kk;
+                const int src_lane = (8 * k + (lane >> 2)) & 31;
+                const U4& g4 = cw[(8 * k) >> 5];
+                const uint32_t w0 = __shfl_sync(FULL, g4.x, src_lane), w1 = __shfl_sync(FULL, g4.y, src_lane);
+                const uint32_t w2 = __shfl_sync(FULL, g4.z, src_lane), w3 = __shfl_sync(FULL, g4.w, src_lane);
+                const int wi = lane & 3;
+                const uint32_t cword = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
+                const bool valid = cin[k] >= 0;
+                unsigned long long qv = 0;
+                ef[kk] = 0;
+                if (valid) {
+                    const int c = cin[k];
+                    const T E0 = s_E[c], E1 = s_E[c + 1];
+                    ef[kk] = fma_(fin[k], sub_(E1, E0), E0);
+                    vzin[k] = fma_(Ksp, ef[kk], vzin[k]);  // v_n
+                    if (S.sp == 0) {  // energy moment at (x_n, v_n), 2^-12 eV, clamped at 2^26
+                        const T e2 = fma_(vxin[k], vxin[k], fma_(vyin[k], vyin[k], mul_(vzin[k], vzin[k])));
+                        T eq = mul_(e2, S.k.kappa_E);
+                        if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
+                        const unsigned long long Et = rint_u32(eq);
+                        const unsigned long long Eh = rint_u32(mul_(eq, fin[k]));
+                        qv = (Et - Eh) | (Eh << 32);
                     }
+                }
+                if (S.sp == 0) warp_hist<true>(s_Q, cin[k], qv, lane);
+                const bool cand = valid && cword < S.thr;
+                const unsigned cm = __ballot_sync(FULL, cand);
+                if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + S.sp], (unsigned)__popc(cm));
+                qi[kk] = qn + __popc(cm & ((1u << lane) - 1u));
+                if (cand) {
+                    QEnt<T>& e = Q[qi[kk]];
+                    e.slot = (uint32_t)(base + (long long)k * BLOCK + tid);
+                    e.c = cin[k];
+                    e.f = fin[k];
+                    e.ef = ef[kk];
+                    e.vx = vxin[k];
+                    e.vy = vyin[k];
+                    e.vz = vzin[k];
+                }
+                qn += __popc(cm);
+                fl[kk] = cand ? 8u : 0u;
+            }
+            __syncwarp();
+            // phase B: the warp works through its queue, 32 candidates at a time
+            for (int q = lane; q < qn; q += 32) collide<T>(S, Q[q], step, seed, s_hist, s_cnt, err);
+            __syncwarp();
+            // phase C: second half kick, drift, walls, deposit
+            Part<T> P0[BATCH], Pse[BATCH];
 #pragma unroll
-                    for (int i = 0; i < LB_W && !found; ++i) {
-                        const long long idx = j - i * 32 - lane;
-                        unsigned flag = 2;
-                        if (idx >= first) {
-                            flag = ((unsigned)(w[i] >> 32) == epoch) ? (unsigned)(w[i] >> 30) & 3u : 0u;
-                            for (int it = 0; !flag && it < LOOKBACK_SPIN_LIMIT; ++it) {
-                                __nanosleep(32);
-                                w[i] = ld_acquire(&st_main[idx]);
-                                if ((unsigned)(w[i] >> 32) == epoch) flag = (unsigned)(w[i] >> 30) & 3u;
-                            }
-                            if (!flag) {
-                                err |= ERR_TIMEOUT;
-                                flag = 2;
-                                w[i] = 0;
-                            }
-                        }
-                        const unsigned long long va = idx >= first ? (w[i] & 0x3FFFFFFFull) : 0ull;
-                        const unsigned pm = __ballot_sync(FULL, flag == 2);
-                        const int L = pm ? __ffs(pm) - 1 : 31;
-                        unsigned long long vb = 0;
-                        if (idx >= first && lane <= L)
-                            vb = (flag == 2) ? *((volatile unsigned long long*)&st_binc[idx])
-                                             : *((volatile unsigned long long*)&st_bagg[idx]);
-                        unsigned long long a = lane <= L ? va : 0ull, b = vb;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            a += __shfl_xor_sync(FULL, a, o);
-                            b += __shfl_xor_sync(FULL, b, o);
-                        }
-                        exA += a;
-                        exB += b;
-                        if (pm) found = true;
+            for (int kk = 0; kk < BATCH; ++kk) {
+                const int k = b + kk;
+                bool alive = false;
+                if (cin[k] >= 0) {
+                    T vx = vxin[k], vy = vyin[k], vz = vzin[k];
+                    if (fl[kk] & 8u) {
+                        const QEnt<T>& e = Q[qi[kk]];
+                        vx = e.vx;
+                        vy = e.vy;
+                        vz = e.vz;
+                        fl[kk] |= e.out;
                     }
-                    j -= LB_W * 32;
+                    vz = fma_(Ksp, ef[kk], vz);
+                    int cn;
+                    T fn;
+                    const int side = drift(S.N, S.k.dtdx, cin[k], fin[k], vz, cn, fn, err);
+                    if (side < 0) {
+                        P0[kk] = Part<T>{cn, fn, vx, vy, vz};
+                        alive = true;
+                        fl[kk] |= 1u;
+                    } else {
+                        atomicAdd(&s_cnt[CNT_ABS + 2 * S.sp + side], 1u);
+                        if (S.sp == 1 && S.has_see &&
+                            emit_see<T>(S, (uint32_t)(base + (long long)k * BLOCK + tid), step, seed, side, Pse[kk],
+                                        s_cnt))
+                            fl[kk] |= 4u;
+                    }
                 }
-                if (lane == 0) {
-                    st_binc[g] = exB + B;
-                    st_release(&st_main[g], mk_status(epoch, 2, exA + A));
-                }
+                warp_hist<false>(s_hist, alive ? P0[kk].c : -1, alive ? (1ull << 40) + cic_F(P0[kk].f) : 0ull,
+                                 lane);
             }
-            if (lane == 0) {
-                s_excl[0] = exA;
-                s_excl[1] = exB;
-                if (ts == S.ntiles - 1) {
-                    ctl->out_main[S.d][S.sp] = (long long)(exA + A);
-                    ctl->out_birth[S.d][S.sp] = (long long)(exB + B);
-                }
-            }
-        }
-        __syncthreads();
-        // scatter the outputs
-        unsigned long long offA = s_excl[0], offB = s_excl[1];
+            // block scan of (same-species outputs | births << 16) per k of the batch, in slot order
+            uint32_t v[BATCH], incl[BATCH];
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const uint32_t ex = incl[k] - v[k] + s_wsum[k][warp];
-            unsigned long long ia = offA + (ex & 0xFFFFu);
-            const unsigned long long ib = offB + (ex >> 16);
-            if (fl[k] & 1u) {
-                if ((long long)ia < S.cap) store_rec<T>(S.cout, S.pout, (long long)ia, P0[k]);
-                else err |= ERR_CAPACITY;
-                ++ia;
+            for (int kk = 0; kk < BATCH; ++kk) {
+                v[kk] = (fl[kk] & 1u) + ((fl[kk] >> 1) & 1u) + (((fl[kk] >> 2) & 1u) << 16);
+                incl[kk] = v[kk];
             }
-            if (fl[k] & 2u) {
-                if ((long long)ia < S.cap) store_rec<T>(S.cout, S.pout, (long long)ia, P1[k]);
-                else err |= ERR_CAPACITY;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int kk = 0; kk < BATCH; ++kk) {
+                    const uint32_t t = __shfl_up_sync(FULL, incl[kk], o);
+                    if (lane >= o) incl[kk] += t;
+                }
             }
-            if (fl[k] & 4u) {
-                if ((long long)ib < S.bcap) store_rec<T>(S.bc, S.bp, (long long)ib, P2[k]);
-                else err |= ERR_CAPACITY;
+            if (lane == 31) {
+#pragma unroll
+                for (int kk = 0; kk < BATCH; ++kk) s_wsum[kk][warp] = incl[kk];
             }
-            offA += s_ktot[k] & 0xFFFFu;
-            offB += s_ktot[k] >> 16;
+            __syncthreads();
+            if (warp == 0) {
+#pragma unroll
+                for (int kk = 0; kk < BATCH; ++kk) {
+                    const uint32_t own = lane < NW ? s_wsum[kk][lane] : 0u;
+                    uint32_t x = own;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, x, o);
+                        if (lane >= o) x += t;
+                    }
+                    if (lane < NW) s_wsum[kk][lane] = x - own;
+                    if (lane == NW - 1) s_ktot[kk] = x;
+                }
+            }
+            __syncthreads();
+            // phase D: write the batch's outputs into the tile's regions, in slot order
+#pragma unroll
+            for (int kk = 0; kk < BATCH; ++kk) {
+                const uint32_t ex = incl[kk] - v[kk] + s_wsum[kk][warp];
+                long long ia = offA + (ex & 0xFFFFu);
+                const long long ib = offB + (ex >> 16);
+                if (fl[kk] & 1u) {
+                    store_rec<T>(S.cout, S.pout, ia, P0[kk]);
+                    ++ia;
+                }
+                if (fl[kk] & 2u) store_rec<T>(S.cout, S.pout, ia, Q[qi[kk]].p1);
+                if (fl[kk] & 4u) store_rec<T>(S.bc, S.bp, ib, S.sp == 0 ? Q[qi[kk]].p2 : Pse[kk]);
+                offA += s_ktot[kk] & 0xFFFFu;
+                offB += s_ktot[kk] >> 16;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            S.cnt_main[ts] = (int)(offA - ts * (2 * TILE));
+            S.cnt_birth[ts] = (int)(offB - ts * TILE);
         }
         __syncthreads();
     }
@@ -701,9 +739,9 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK) k
         __threadfence();
         const unsigned prev = atomicAdd(&ctl->done, 1u);
         if (prev == gridDim.x - 1) {
+            for (int i = 0; i < 2 * n_disc; ++i) ctl->count_in[i >> 1][i & 1] = ctl->count[i >> 1][i & 1];
             ctl->tile_ctr = 0;
             ctl->done = 0;
-            ctl->epoch = epoch + 1;
             __threadfence();
         }
     }
@@ -747,6 +785,48 @@ __device__ void block_scan_inclusive(double* a, int n, double* s_warp) {
     __syncthreads();
 }
 
+// Exclusive scan of n int counts (global memory) by a whole block: every thread
+// takes a contiguous chunk; visit(t, prefix, count) is called for every entry in
+// order within the chunk. Returns the total (to every thread).
+template <int BLOCK, typename F>
+__device__ long long block_chunk_scan(const int* __restrict__ cnt, long long n, long long* s_w, F&& visit) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = BLOCK / 32;
+    const long long per = (n + BLOCK - 1) / BLOCK;
+    const long long lo = tid * per, hi = min(n, lo + per);
+    long long run = 0;
+    for (long long t = lo; t < hi; ++t) run += cnt[t];
+    long long x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const long long own = lane < NW ? s_w[lane] : 0;
+        long long y = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long z = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < NW) s_w[lane] = y - own;
+        if (lane == NW - 1) s_w[32] = y;
+    }
+    __syncthreads();
+    long long ex = s_w[warp] + x - run;
+    for (long long t = lo; t < hi; ++t) {
+        const int c = cnt[t];
+        visit(t, ex, c);
+        ex += c;
+    }
+    const long long total = s_w[32];
+    __syncthreads();
+    return total;
+}
+
 // mode bits: 1 append births and update counts; 2 accumulate moments and
 // advance the step; 4 initial solve at t = n dt (load); 8 births only (no
 // solve, deposits kept).
@@ -757,58 +837,94 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
     extern __shared__ __align__(16) double s_f[];
     __shared__ double s_warp[32];
     __shared__ long long s_n[2][3];
+    __shared__ long long s_lscan[33];
     __shared__ int s_err;
-    const int d = blockIdx.x, tid = threadIdx.x;
+    const int d = blockIdx.x, tid = threadIdx.x, role = blockIdx.y;
     const Disc& D = discs[d];
     const int N = D.N;
     if (tid == 0) s_err = 0;
     __syncthreads();
 
-    if (mode & 1) {
+    // role 1, 2: the new segment table and births of store role-1; role 0: the field
+    if ((mode & 1) && role > 0) {
+        // New segment tables from the sweep's per-tile counts: store sp's segments are its own
+        // tiles' regions (slot order), then one segment of the births of sp that the other
+        // species' tiles produced, compacted here into the births region.
         using R = typename Rec<T>::type;
+        const int TILE = D.tile;
         if (tid == 0) {
-            for (int sp = 0; sp < 2; ++sp) {
-                const long long n_in = ctl->count[d][sp];
-                s_n[sp][0] = n_in > 0 ? ctl->out_main[d][sp] : 0;   // same-species outputs
-                s_n[sp][1] = n_in > 0 ? ctl->out_birth[d][sp] : 0;  // births of the other species
-            }
+            for (int sp = 0; sp < 2; ++sp) s_n[sp][0] = (ctl->count_in[d][sp] + TILE - 1) / TILE;  // input tiles
         }
         __syncthreads();
-        for (int sp_new = 0; sp_new < 2; ++sp_new) {
-            const int sp_par = 1 - sp_new;
-            const long long nb = s_n[sp_par][1];
-            const long long n0 = s_n[sp_new][0];
-            int32_t* cdst = D.c[out_buf][sp_new];
-            R* pdst = reinterpret_cast<R*>(D.p[out_buf][sp_new]);
-            const int32_t* csrc = D.bc[sp_par];
-            const R* psrc = reinterpret_cast<const R*>(D.bp[sp_par]);
-            for (long long k = tid; k < nb; k += BLOCK) {
-                const long long dst = n0 + k;
-                if (k < D.bcap && dst < D.cap[sp_new]) {
-                    cdst[dst] = csrc[k];
-                    pdst[dst] = psrc[k];
-                } else {
+        {
+            const int sp = role - 1;
+            const int par = 1 - sp;
+            const long long tiles = s_n[sp][0], ptiles = s_n[par][0];
+            int* st = D.seg_start[sp];
+            int* sr = D.seg_src[sp];
+            const long long main_total = block_chunk_scan<BLOCK>(D.cnt_main[sp], tiles, s_lscan,
+                [&](long long t, long long ex, int c) {
+                    st[t] = (int)ex;
+                    sr[t] = (int)(t * 2 * TILE);
+                });
+            int32_t* cdst = D.c[out_buf][sp];
+            R* pdst = reinterpret_cast<R*>(D.p[out_buf][sp]);
+            const int32_t* csrc = D.bc[par];
+            const R* psrc = reinterpret_cast<const R*>(D.bp[par]);
+            const long long R0 = D.R0[sp], bcap = D.bcap;
+            const long long nb = block_chunk_scan<BLOCK>(D.cnt_birth[par], ptiles, s_lscan,
+                [&](long long t, long long ex, int c) {
+                    for (int k = 0; k < c; ++k) {
+                        if (ex + k < bcap) {
+                            cdst[R0 + ex + k] = csrc[t * TILE + k];
+                            pdst[R0 + ex + k] = psrc[t * TILE + k];
+                        } else {
+                            s_err = ERR_CAPACITY;
+                        }
+                    }
+                });
+            const long long nbk = nb < bcap ? nb : bcap;
+            const int nseg = (int)tiles + (nbk > 0 ? 1 : 0);
+            long long n_new = main_total + nbk;
+            if (tid == 0) {
+                if (nbk > 0) {
+                    st[tiles] = (int)main_total;
+                    sr[tiles] = (int)R0;
+                }
+                st[nseg] = (int)n_new;
+                if (n_new > D.cap[sp]) {
                     s_err = ERR_CAPACITY;
+                    n_new = D.cap[sp];
+                }
+                ctl->count[d][sp] = n_new;
+                ctl->nseg[d][sp] = nseg;
+            }
+            __syncthreads();
+            // first segment of every tile of the next sweep: the segment holding slot j TILE
+            const long long jmax = D.max_tiles[sp];
+            for (int k = tid; k < nseg; k += BLOCK) {
+                const long long s0 = st[k], s1 = st[k + 1];
+                if (s1 > s0) {
+                    const long long j1 = (s1 + TILE - 1) / TILE;
+                    for (long long j = (s0 + TILE - 1) / TILE; j < j1 && j <= jmax; ++j) D.first_seg[sp][j] = k;
                 }
             }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int sp = 0; sp < 2; ++sp) {
-                long long n = s_n[sp][0] + s_n[1 - sp][1];
-                if (s_n[sp][0] > D.cap[sp] || s_n[1 - sp][1] > D.bcap) s_err = ERR_CAPACITY;
-                if (n > D.cap[sp]) {
-                    n = D.cap[sp];
-                    s_err = ERR_CAPACITY;
-                }
-                ctl->count[d][sp] = n;
-            }
+            __syncthreads();
         }
     }
 
-    if (mode & 8) {
+    if (role > 0 || (mode & 8)) {
         __syncthreads();
         if (tid == 0 && s_err) atomicOr(&ctl->error, s_err);
+        if (tid == 0 && (mode & 2)) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
+            if (prev == gridDim.x * gridDim.y - 1) {
+                ctl->fin_done = 0;
+                ctl->step = ctl->step + 1;
+                __threadfence();
+            }
+        }
         return;
     }
 
@@ -882,7 +998,7 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
         if (mode & 2) {
             __threadfence();
             const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
-            if (prev == gridDim.x - 1) {
+            if (prev == gridDim.x * gridDim.y - 1) {
                 ctl->fin_done = 0;
                 ctl->step = step + 1;
                 __threadfence();
@@ -992,27 +1108,34 @@ __global__ void k_tables(int n_pts, int n_proc, double de, double M, const doubl
 // warp w owns a contiguous run of SORT_R x 32 particles in input order.
 constexpr int SORT_BLOCK = 256, SORT_NW = SORT_BLOCK / 32, SORT_R = 16, SORT_TILE = SORT_BLOCK * SORT_R;
 
-// Per tile: count of each cell -> hist[seg][c * T_s + t].
+// Per tile: count of each cell -> hist[seg][c * T_s + t]. Input read through
+// the store's segment table.
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                            int buf, unsigned* __restrict__ hist,
                                                            const long long* __restrict__ hoff) {
     extern __shared__ __align__(16) unsigned s_c[];
+    __shared__ SegWin W;
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
     const long long n = ctl->count[d][sp];
+    const int nseg = ctl->nseg[d][sp];
     const long long Ts = (n + SORT_TILE - 1) / SORT_TILE;
     const int32_t* cc = D.c[buf][sp];
     unsigned* H = hist + hoff[seg];
     const int lane = threadIdx.x & 31;
+    const int per_sweep_tile = SORT_TILE / D.tile;
     for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = threadIdx.x; j < N; j += SORT_BLOCK) s_c[j] = 0;
+        if (threadIdx.x < 32)
+            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_sweep_tile],
+                            lane);
         __syncthreads();
         for (int i = threadIdx.x; i < SORT_TILE; i += SORT_BLOCK) {
             const long long k = t * SORT_TILE + i;
-            const int key = k < n ? cc[k] : N;
+            const int key = k < n ? cc[seg_offset(W, D.seg_start[sp], D.seg_src[sp], nseg, k)] : N;
             const unsigned peers = __match_any_sync(FULL, key);
-            if (key < N && lane == __ffs(peers) - 1) atomicAdd(&s_c[key], (unsigned)__popc(peers));
+            if ((unsigned)key < (unsigned)N && lane == __ffs(peers) - 1) atomicAdd(&s_c[key], (unsigned)__popc(peers));
         }
         __syncthreads();
         for (int j = threadIdx.x; j < N; j += SORT_BLOCK) H[(long long)j * Ts + t] = s_c[j];
@@ -1108,7 +1231,8 @@ __global__ void __launch_bounds__(1024) k_sort_cells(const Disc* __restrict__ di
 }
 
 // Scatter: per-warp counts, prefix over warps, then each warp places its run
-// in order (rank among equal cells by match_any).
+// in order (rank among equal cells by match_any). Input through the segment
+// table; output dense.
 template <typename T>
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restrict__ discs,
                                                              const Ctl* __restrict__ ctl, int src, int dst,
@@ -1116,10 +1240,12 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
                                                              const long long* __restrict__ hoff,
                                                              const unsigned* __restrict__ tot, int max_N) {
     extern __shared__ __align__(16) unsigned s_w[];  // [SORT_NW][max_N]
+    __shared__ SegWin W;
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
     const long long n = ctl->count[d][sp];
+    const int nseg = ctl->nseg[d][sp];
     const long long Ts = (n + SORT_TILE - 1) / SORT_TILE;
     const int32_t* cs = D.c[src][sp];
     int32_t* cd = D.c[dst][sp];
@@ -1130,16 +1256,20 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
     const unsigned* cstart = tot + (long long)seg * MAXN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned* W = s_w + warp * max_N;
+    unsigned* Wc = s_w + warp * max_N;
+    const int per_sweep_tile = SORT_TILE / D.tile;
     for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = tid; j < SORT_NW * max_N; j += SORT_BLOCK) s_w[j] = 0;
+        if (warp == 0)
+            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_sweep_tile],
+                            lane);
         __syncthreads();
         const long long wbase = t * SORT_TILE + (long long)warp * (SORT_R * 32);
         for (int r = 0; r < SORT_R; ++r) {
             const long long k = wbase + r * 32 + lane;
-            const int key = k < n ? cs[k] : N;
+            const int key = k < n ? cs[seg_offset(W, D.seg_start[sp], D.seg_src[sp], nseg, k)] : N;
             const unsigned peers = __match_any_sync(FULL, key);
-            if (key < N && lane == __ffs(peers) - 1) W[key] += __popc(peers);
+            if ((unsigned)key < (unsigned)N && lane == __ffs(peers) - 1) Wc[key] += __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -1155,22 +1285,40 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
         __syncthreads();
         for (int r = 0; r < SORT_R; ++r) {
             const long long k = wbase + r * 32 + lane;
-            const int key = k < n ? cs[k] : N;
+            long long off = 0;
+            int key = N;
+            if (k < n) {
+                off = seg_offset(W, D.seg_start[sp], D.seg_src[sp], nseg, k);
+                key = cs[off];
+            }
             const unsigned peers = __match_any_sync(FULL, key);
-            const unsigned b = key < N ? W[key] : 0u;
+            const unsigned b = (unsigned)key < (unsigned)N ? Wc[key] : 0u;
             __syncwarp();
-            if (key < N) {
+            if ((unsigned)key < (unsigned)N) {
                 const long long o = (long long)cstart[key] + H[(long long)key * Ts + t] + b + __popc(peers & lt);
                 if (o < n) {
                     cd[o] = key;
-                    pd[o] = ps[k];
+                    pd[o] = ps[off];
                 }
-                if (lane == __ffs(peers) - 1) W[key] = b + __popc(peers);
+                if (lane == __ffs(peers) - 1) Wc[key] = b + __popc(peers);
             }
             __syncwarp();
         }
         __syncthreads();
     }
+}
+
+// Every store becomes one dense segment [0, count) (after a load, an upload or a sort).
+__global__ void k_set_dense(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl) {
+    const int i = threadIdx.x;
+    if (i >= 2 * n_disc) return;
+    const int d = i >> 1, sp = i & 1;
+    const Disc& D = discs[d];
+    D.seg_start[sp][0] = 0;
+    D.seg_start[sp][1] = (int)ctl->count[d][sp];
+    D.seg_src[sp][0] = 0;
+    D.first_seg[sp][0] = 0;
+    ctl->nseg[d][sp] = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -1229,12 +1377,11 @@ static cudaError_t smem_attr(K kern, size_t smem) {
 
 template <typename T, int BLOCK, int PPT>
 static cudaError_t launch_sweep_t(const SweepLaunch& L) {
-    const size_t smem = (size_t)(L.max_N + 1) * (16 + sizeof(T));
+    const size_t smem = sweep_smem<T, BLOCK, PPT>(L.max_N);
     auto kern = k_sweep<T, BLOCK, PPT>;
     cudaError_t e = smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<L.grid, BLOCK, smem, L.stream>>>(L.discs, L.n_disc, L.ctl, L.st_main, L.st_bagg, L.st_binc, L.in_buf,
-                                            L.seed, L.max_N);
+    kern<<<L.grid, BLOCK, smem, L.stream>>>(L.discs, L.n_disc, L.ctl, L.in_buf, L.seed, L.max_N);
     return cudaGetLastError();
 }
 
@@ -1257,7 +1404,7 @@ cudaError_t launch_sweep(const SweepLaunch& L) {
 template <typename T, int BLOCK, int PPT>
 static int occ_t(int max_N) {
     int nb = 0;
-    const size_t smem = (size_t)(max_N + 1) * (16 + sizeof(T));
+    const size_t smem = sweep_smem<T, BLOCK, PPT>(max_N);
     smem_attr(k_sweep<T, BLOCK, PPT>, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<T, BLOCK, PPT>, BLOCK, smem);
     return nb;
@@ -1282,10 +1429,10 @@ cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, i
     const size_t smem = sizeof(double) * 3 * (MAXN + 1);
     if (fp64) {
         smem_attr(k_finalize<double>, smem);
-        k_finalize<double><<<n_disc, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
+        k_finalize<double><<<dim3(n_disc, 3), 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
     } else {
         smem_attr(k_finalize<float>, smem);
-        k_finalize<float><<<n_disc, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
+        k_finalize<float><<<dim3(n_disc, 3), 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
     }
     return cudaGetLastError();
 }
@@ -1347,6 +1494,11 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
 }
 
 long long sort_tile() { return SORT_TILE; }
+
+cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st) {
+    k_set_dense<<<1, 128, 0, st>>>(discs, n_disc, ctl);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st) {

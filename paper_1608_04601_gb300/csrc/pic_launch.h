@@ -8,7 +8,6 @@ struct SweepLaunch {
     int fp64, block, ppt, grid, max_N, n_disc, in_buf;
     const Disc* discs;
     Ctl* ctl;
-    unsigned long long *st_main, *st_bagg, *st_binc;
     unsigned long long seed;
     cudaStream_t stream;
 };
@@ -27,6 +26,7 @@ cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, 
 cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int src, int dst, unsigned* hist,
                         const long long* hoff, unsigned* tot, int max_N, int grid_x, cudaStream_t st);
 long long sort_tile();
+cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_debug_math(long long n, const float* x, const float* y, float* lg, float* sn, float* cs,

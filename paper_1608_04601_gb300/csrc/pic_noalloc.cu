@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(NA_BLOCK) na_count(const int32_t* __restrict__
             const long long k = t * NA_TILE + i;
             const int key = k < n ? c[k] : N;
             const unsigned peers = __match_any_sync(NA_FULL, key);
-            if (key < N && lane == __ffs(peers) - 1) atomicAdd(&s_c[key], (unsigned)__popc(peers));
+            if ((unsigned)key < (unsigned)N && lane == __ffs(peers) - 1) atomicAdd(&s_c[key], (unsigned)__popc(peers));
         }
         __syncthreads();
         for (int j = threadIdx.x; j < N; j += NA_BLOCK) hist[(long long)j * Ts + t] = s_c[j];
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(NA_BLOCK) na_scatter(const int32_t* __restrict
             const long long k = wbase + r * 32 + lane;
             const int key = k < n ? cs[k] : N;
             const unsigned peers = __match_any_sync(NA_FULL, key);
-            if (key < N && lane == __ffs(peers) - 1) W[key] += __popc(peers);
+            if ((unsigned)key < (unsigned)N && lane == __ffs(peers) - 1) W[key] += __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -159,9 +159,9 @@ __global__ void __launch_bounds__(NA_BLOCK) na_scatter(const int32_t* __restrict
             const long long k = wbase + r * 32 + lane;
             const int key = k < n ? cs[k] : N;
             const unsigned peers = __match_any_sync(NA_FULL, key);
-            const unsigned b = key < N ? W[key] : 0u;
+            const unsigned b = (unsigned)key < (unsigned)N ? W[key] : 0u;
             __syncwarp();
-            if (key < N) {
+            if ((unsigned)key < (unsigned)N) {
                 const long long o = (long long)cstart[key] + hist[(long long)key * Ts + t] + b + __popc(peers & lt);
                 if (o < n) {
                     cd[o] = key;
