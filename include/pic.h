@@ -134,7 +134,11 @@ pic_status pic_create(pic_ctx** out, const pic_gas* gas, double gap_m, double p_
 
 /* Enqueues n_steps full time steps: sweep (gather, half kick, MCC, half
  * kick, drift, walls, compaction, deposit), births appended, periodic sort,
- * Poisson at t_{n+1}, moments accumulated. Asynchronous.                  */
+ * Poisson at t_{n+1}, moments accumulated. Asynchronous.
+ * Order of a store after a sweep: the survivors in input-slot order, then
+ * the newborns in parent-slot order (electrons: ionization electrons, then
+ * secondary electrons of absorbed ions; ions: ionization ions). The slot
+ * order keys every random stream, so the order is part of the result.    */
 pic_status pic_step(pic_ctx* ctx, int64_t n_steps);
 
 /* The parts of one step, for tests and custom drivers:
@@ -211,6 +215,27 @@ typedef struct {
 pic_status pic_get_derived(pic_ctx* ctx, int32_t d, pic_derived* out);
 /* Cumulative rate-coefficient tables of one gas: Te n_pts x 4, Ti n_pts x 2. */
 pic_status pic_get_tables(pic_ctx* ctx, int32_t gas, void* Te, void* Ti);
+
+/* Warm start: replaces every store by superparticles sampled from given
+ * cycle-averaged profiles, instead of the uniform cold load. profiles is a host
+ * array [n_discharges][3][n_pts] on the uniform grid z_j = j gap / (n_pts-1):
+ * electron density, ion density (m^-3), mean electron energy (eV). Counts are
+ * the profile integrals over the weights; positions follow the inverse of the
+ * piecewise-constant CDF; electrons are Maxwellian at kT = 2/3 <eps>(z), ions at
+ * T_i0 (Philox calls 0xF2, 0xF3 at step 0). Then, as after the cold load:
+ * deposit, field at t = 0, half back-kick. Only before the first step
+ * (PIC_ERR_STATE otherwise); PIC_ERR_CAPACITY if a count exceeds capacity.
+ * The paper notes that initial values change the time to the periodic state,
+ * not the state (section "Numerical parameters and initial values").        */
+pic_status pic_load_profiles(pic_ctx* ctx, int32_t n_pts, const double* profiles);
+
+/* Mean superparticle count of each species over rf periods first .. first+n-1
+ * (periods counted from step 0; a period ends after steps_per_period steps),
+ * into host out[2*k + species]. *periods_done receives the periods completed.
+ * The last 65536 periods are kept. The steady-state criterion of the warm start
+ * compares these means 50 periods apart.                                    */
+pic_status pic_period_counts(pic_ctx* ctx, int32_t d, int64_t first, int64_t n, double* out,
+                             int64_t* periods_done);
 
 /* Timing of the last pic_step call's sweep launches (CUDA events on the
  * context stream): total milliseconds and launches.                       */

@@ -111,6 +111,8 @@ def _lib(prec: str):
         L.orc_get_tables.argtypes = [vp, vp, vp]
         L.orc_moments.argtypes = [vp, vp, vp, vp, C.POINTER(OrcMomentInfo)]
         L.orc_reset_moments.argtypes = [vp]
+        L.orc_load_profiles.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.orc_load_profiles.restype = C.c_int
         L.orc_real_bytes.restype = C.c_int
         L.orc_philox4x32_10.argtypes = [vp, vp, vp]
         L.orc_uniform.argtypes = [C.c_uint32]
@@ -221,6 +223,11 @@ class Oracle:
     def load(self):
         if self.L.orc_load(self.h):
             raise RuntimeError("orc_load failed")
+
+    def load_profiles(self, n_e, n_i, mean_eps):
+        a = [np.ascontiguousarray(x, np.float64) for x in (n_e, n_i, mean_eps)]
+        if self.L.orc_load_profiles(self.h, a[0].size, *[_p(x) for x in a]):
+            raise RuntimeError("orc_load_profiles failed")
 
     def sweep(self):
         if self.L.orc_sweep(self.h):

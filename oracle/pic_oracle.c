@@ -78,7 +78,7 @@ typedef double real;
 
 enum { SP_E = 0, SP_I = 1 };
 enum { CALL_MAIN = 0, CALL_AUX = 1, CALL_AUX2 = 2, CALL_SEE = 3, CALL_CAND = 4,
-       CALL_LOAD0 = 0xF0, CALL_LOAD1 = 0xF1 };
+       CALL_LOAD0 = 0xF0, CALL_LOAD1 = 0xF1, CALL_WARM0 = 0xF2, CALL_WARM1 = 0xF3 };
 
 typedef struct {
     int32_t* c;
@@ -532,22 +532,116 @@ int orc_load(orc_ctx* o) {
     return 0;
 }
 
+/* The common end of a load: deposit, field at t = 0, half back-kick. */
+static void finish_load(orc_ctx* o) {
+    int N = o->N;
+    for (int sp = 0; sp < 2; ++sp) {
+        memset(o->D[sp], 0, sizeof(int64_t) * (size_t)(N + 1));
+        store* s = &o->s[sp];
+        for (int64_t k = 0; k < s->n; ++k) deposit(o->D[sp], s->c[k], s->f[k]);
+    }
+    o->step = -1;
+    orc_solve(o);
+    o->step = 0;
+    for (int sp = 0; sp < 2; ++sp) {
+        store* s = &o->s[sp];
+        real mK = -(sp == SP_E ? o->K_e : o->K_i);
+        for (int64_t k = 0; k < s->n; ++k) s->vz[k] = R_FMA(mK, gather(o, s->c[k], s->f[k]), s->vz[k]);
+    }
+    memcpy(o->Dprev_e, o->D[SP_E], sizeof(int64_t) * (size_t)(N + 1));
+}
+
+int orc_load_profiles(orc_ctx* o, int P, const double* n_e, const double* n_i, const double* mean_eps) {
+    const int N = o->N;
+    if (P < 2) return -1;
+    real* cdf = (real*)malloc(sizeof(real) * (size_t)P);
+    real* eps = (real*)malloc(sizeof(real) * (size_t)P);
+    const double dz = o->p.gap_m / (double)(P - 1);
+    const real scale = (real)((double)N / (double)(P - 1));
+    const real K23 = (real)(2.0 * E_CHARGE / (3.0 * M_ELEC));
+    for (int j = 0; j < P; ++j) eps[j] = (real)(mean_eps[j] > 0.0 ? mean_eps[j] : 0.0);
+    for (int sp = 0; sp < 2; ++sp) {
+        const double* prof = sp == SP_E ? n_e : n_i;
+        const double w = sp == SP_E ? o->p.w_e : o->p.w_i;
+        double A = 0.0;
+        for (int j = 0; j + 1 < P; ++j) {
+            double a = 0.5 * (fmax(prof[j], 0.0) + fmax(prof[j + 1], 0.0)) * dz;
+            A += a;
+        }
+        int64_t n = A > 0.0 ? (int64_t)floor(A / w + 0.5) : 0;
+        double run = 0.0;
+        cdf[0] = (real)0;
+        for (int j = 0; j + 1 < P; ++j) {
+            run += 0.5 * (fmax(prof[j], 0.0) + fmax(prof[j + 1], 0.0)) * dz;
+            cdf[j + 1] = (real)(A > 0.0 ? run / A : 0.0);
+        }
+        cdf[P - 1] = (real)1;
+        store* s = &o->s[sp];
+        s->n = 0;
+        if (store_reserve(s, n > 0 ? n : 1)) return -1;
+        for (int64_t k = 0; k < n; ++k) {
+            uint32_t r[4], q[4];
+            draw(o, (uint32_t)k, sp, CALL_WARM0, r);
+            draw(o, (uint32_t)k, sp, CALL_WARM1, q);
+            const real u = (real)U24(r[0]);
+            int lo = 0, hi = P - 2;   /* largest j in [0, P-2] with cdf[j] <= u */
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (cdf[mid] <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            const int j = lo;
+            const real den = cdf[j + 1] - cdf[j];
+            real t = den > (real)0 ? (u - cdf[j]) / den : (real)0;
+            if (t >= (real)1) t = R_ONE_MINUS_ULP;
+            const real x = ((real)j + t) * scale;
+            int32_t c = (int32_t)x;
+            real f;
+            if (c >= N) {
+                c = N - 1;
+                f = R_ONE_MINUS_ULP;
+            } else {
+                f = x - (real)c;
+            }
+            real sig;
+            if (sp == SP_E) {
+                real el = R_FMA(t, eps[j + 1] - eps[j], eps[j]);
+                if (!(el > (real)0)) el = (real)0;
+                sig = R_SQRT(el * K23);
+            } else {
+                sig = o->sig_i0;
+            }
+            float n0f, n1f, n2f, n3f;
+            orc_box_muller(U24(r[1]), U24(r[2]), &n0f, &n1f);
+            orc_box_muller(U24(r[3]), U24(q[0]), &n2f, &n3f);
+            (void)n3f;
+            store_push(s, c, f, sig * (real)n0f, sig * (real)n1f, sig * (real)n2f);
+        }
+    }
+    free(cdf);
+    free(eps);
+    finish_load(o);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One sweep over both species at step n, from (x_n, v*) with the node field
  * E_n: v_n = v* + K E(x_n); collision on v_n; v* <- v_n + K E(x_n);
  * x_{n+1} = x_n + v*_z dt; absorption; deposit at x_{n+1}.
- * New arrays: for each input slot in order, the particle if it stays, then
- * its same-species newborn if that stays; then the other species' births
- * (ions from ionization in electron-slot order, secondary electrons in
- * ion-slot order).                                                          */
+ * New arrays: the survivors in input-slot order, then the newborns that stay,
+ * in parent-slot order: for electrons the ionization electrons, then the
+ * secondary electrons of absorbed ions; for ions the ionization ions.       */
 int orc_sweep(orc_ctx* o) {
     const int N = o->N;
     size_t N1 = (size_t)N + 1;
-    store out[2], birth[2];
+    /* out: survivors in input order; sec: ionization electrons in parent order; birth[sp]: newborns
+     * of species sp made by the other species' sweep (ions from ionization, SEE electrons) */
+    store out[2], birth[2], sec;
     memset(out, 0, sizeof(out));
     memset(birth, 0, sizeof(birth));
+    memset(&sec, 0, sizeof(sec));
     if (store_reserve(&out[SP_E], o->s[SP_E].n * 2 + 16) || store_reserve(&out[SP_I], o->s[SP_I].n + 16) ||
-        store_reserve(&birth[SP_E], 16) || store_reserve(&birth[SP_I], 16))
+        store_reserve(&birth[SP_E], 16) || store_reserve(&birth[SP_I], 16) || store_reserve(&sec, 16))
         return -1;
     memcpy(o->Dprev_e, o->D[SP_E], sizeof(int64_t) * N1);
     memset(o->Q, 0, sizeof(int64_t) * N1);
@@ -651,7 +745,7 @@ int orc_sweep(orc_ctx* o) {
                 ce_vz = R_FMA(o->K_e, ef, ce_vz);
                 side = drift(o, c, f, ce_vz, &cn, &fn);
                 if (side < 0) {
-                    store_push(&out[SP_E], cn, fn, ce_vx, ce_vy, ce_vz);
+                    store_push(&sec, cn, fn, ce_vx, ce_vy, ce_vz);
                     deposit(o->D[SP_E], cn, fn);
                 } else {
                     o->cnt.absorbed[SP_E][side]++;
@@ -738,7 +832,10 @@ int orc_sweep(orc_ctx* o) {
         }
     }
 
-    /* append the births of the other species */
+    /* newborns after the survivors, in parent order: electrons get the ionization electrons, then
+     * the SEE electrons; ions get the ionization ions */
+    for (int64_t k = 0; k < sec.n; ++k) store_push(&out[SP_E], sec.c[k], sec.f[k], sec.vx[k], sec.vy[k], sec.vz[k]);
+    store_free(&sec);
     for (int sp = 0; sp < 2; ++sp) {
         store* b = &birth[sp];
         for (int64_t k = 0; k < b->n; ++k) store_push(&out[sp], b->c[k], b->f[k], b->vx[k], b->vy[k], b->vz[k]);

@@ -80,6 +80,14 @@ int      orc_real_bytes(void);               /* 4 or 8                       */
  * deposit, field solve at t = 0 and the half back-kick of v_z.            */
 int      orc_load(orc_ctx* o);
 
+/* Warm start: replaces both stores by particles sampled from profiles on a
+ * uniform grid of n_pts points over [0, d]: n_e, n_i (m^-3), mean electron
+ * energy (eV). Counts = integral / weight; positions by the inverse of the
+ * piecewise-constant CDF; velocities Maxwellian, electrons at kT = 2/3 <eps>(z),
+ * ions at T_i0. Then deposit, field at t = 0 and the half back-kick.        */
+int      orc_load_profiles(orc_ctx* o, int n_pts, const double* n_e, const double* n_i,
+                           const double* mean_eps);
+
 /* The parts of one time step, and the whole step. */
 int      orc_sweep(orc_ctx* o);     /* gather, Verlet, MCC, walls, compaction, deposit */
 int      orc_sort(orc_ctx* o);      /* stable counting sort of both species by cell   */

@@ -111,6 +111,8 @@ PROTOTYPES = {
     "pic_debug_philox": (C.c_int, [_i64, _vp, _vp, _vp]),
     "pic_debug_math": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
     "pic_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp]),
+    "pic_period_counts": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
+    "pic_load_profiles": (C.c_int, [_vp, _i32, _vp]),
 }
 
 _lib = None

@@ -359,6 +359,8 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.w[1] = d.weights.w_i;
         D.has_see = d.weights.gamma_see > 0.0;
         D.tile = (int)tile;
+        D.chunk = 32 * o.ppt;
+        D.warps = o.block / 32;
         fill_consts<float>(D.cf, der, d);
         fill_consts<double>(D.cd, der, d);
         D.Te = g.Te;
@@ -368,9 +370,9 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.bcap = std::max(D.cap[0], D.cap[1]) / 8 + 4096;
         const size_t rec = 4 * rsz;
         for (int sp = 0; sp < 2; ++sp) {
-            // record buffers: 2 tile records per input tile, then the births region
+            // record buffers: one chunk region per input chunk, then the newborn region
             D.max_tiles[sp] = (D.cap[sp] + tile - 1) / tile;
-            D.R0[sp] = D.max_tiles[sp] * 2 * tile;
+            D.R0[sp] = D.max_tiles[sp] * tile;
             D.rcap[sp] = D.R0[sp] + D.bcap;
             if (D.rcap[sp] > 0x7FFFFFF0ll) {
                 pic_status s_ = fail(ctx, PIC_ERR_ARG, "capacity too large for 32-bit segment offsets");
@@ -384,14 +386,19 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
                 ALLOC(D.p[b][sp], void*, rec * (size_t)(D.rcap[sp] + 16));
             }
         for (int sp = 0; sp < 2; ++sp) {
-            const size_t mt = (size_t)D.max_tiles[sp];
+            const size_t mt = (size_t)D.max_tiles[sp], mc = mt * (size_t)D.warps;
             ALLOC(D.bc[sp], int32_t*, sizeof(int32_t) * (mt * tile + 16));
             ALLOC(D.bp[sp], void*, rec * (mt * tile + 16));
-            ALLOC(D.seg_start[sp], int*, sizeof(int) * (mt + 3));
-            ALLOC(D.seg_src[sp], int*, sizeof(int) * (mt + 2));
-            ALLOC(D.first_seg[sp], int*, sizeof(int) * (mt + 2));
-            ALLOC(D.cnt_main[sp], int*, sizeof(int) * (mt + 1));
-            ALLOC(D.cnt_birth[sp], int*, sizeof(int) * (mt + 1));
+            ALLOC(D.seg_start[sp], int*, sizeof(int) * (mc + 3));
+            ALLOC(D.seg_src[sp], int*, sizeof(int) * (mc + 2));
+            ALLOC(D.first_seg[sp], int*, sizeof(int) * (mc + 2));
+            ALLOC(D.cnt_main[sp], int*, sizeof(int) * (mc + 1));
+            ALLOC(D.cnt_birth[sp], int*, sizeof(int) * (mc + 1));
+            if (sp == 0) {
+                ALLOC(D.sc, int32_t*, sizeof(int32_t) * (mt * tile + 16));
+                ALLOC(D.sp_, void*, rec * (mt * tile + 16));
+                ALLOC(D.cnt_same, int*, sizeof(int) * (mc + 1));
+            }
         }
         const size_t N1 = (size_t)d.n_cells + 1;
         ALLOC(D.E, void*, rsz * N1);
@@ -406,6 +413,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ALLOC(D.acc_Q, double*, 8 * N1);
         ALLOC(D.acc_Dprev, double*, 8 * N1);
         ALLOC(D.cnt, unsigned long long*, 8 * NCNT);
+        ALLOC(D.period_mean, double*, sizeof(double) * 2 * PERIOD_HIST);
         ctx->hd.push_back(D);
         std::memset(&ctx->cnt_at_reset[i], 0, sizeof(pic_counters));
     }
@@ -913,4 +921,111 @@ extern "C" pic_status pic_debug_math(int64_t n, const float* x, const float* y, 
     if (e == cudaSuccess) e = cudaMemcpy(cs, b + 4 * n, 4 * n, cudaMemcpyDeviceToHost);
     cudaFree(b);
     return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}
+
+extern "C" pic_status pic_period_counts(pic_ctx* ctx, int32_t d, int64_t first, int64_t n, double* out,
+                                        int64_t* periods_done) {
+    if (bad_d(ctx, d) || first < 0 || n < 0 || (n && !out)) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const int spp = ctx->dis[d].weights.steps_per_period;
+    const long long done = spp > 0 ? ctx->step / spp : 0;
+    if (periods_done) *periods_done = done;
+    if (first + n > done || done - first > PERIOD_HIST) return fail(ctx, PIC_ERR_ARG, "periods not available");
+    for (long long k = 0; k < n; ++k) {
+        const long long slot = (first + k) % PERIOD_HIST;
+        CK(cudaMemcpy(out + 2 * k, ctx->hd[d].period_mean + 2 * slot, 2 * sizeof(double), cudaMemcpyDeviceToHost),
+           "period counts");
+    }
+    return PIC_OK;
+}
+
+// Warm start (see include/pic.h): profiles[d][3][n_pts] = n_e, n_i (m^-3), mean electron energy (eV).
+extern "C" pic_status pic_load_profiles(pic_ctx* ctx, int32_t n_pts, const double* profiles) {
+    if (!ctx || n_pts < 2 || !profiles) return PIC_ERR_ARG;
+    if (ctx->step != 0) return fail(ctx, PIC_ERR_STATE, "profiles can only be loaded before the first step");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const int P = n_pts, nd = ctx->n_disc;
+    const size_t r = ctx->fp64 ? 8 : 4;
+    std::vector<unsigned char> host((size_t)nd * 3 * P * r);
+    std::vector<long long> counts((size_t)nd * 2);
+    for (int d = 0; d < nd; ++d) {
+        const double* pr = profiles + (size_t)d * 3 * P;
+        const double dz = ctx->dis[d].gap_m / (double)(P - 1);
+        for (int sp = 0; sp < 2; ++sp) {
+            const double* prof = pr + (size_t)sp * P;
+            const double w = sp == 0 ? ctx->dis[d].weights.w_e : ctx->dis[d].weights.w_i;
+            double A = 0.0;
+            for (int j = 0; j + 1 < P; ++j) {
+                const double a = 0.5 * (std::fmax(prof[j], 0.0) + std::fmax(prof[j + 1], 0.0)) * dz;
+                A += a;
+            }
+            const long long n = A > 0.0 ? (long long)std::floor(A / w + 0.5) : 0;
+            const long long cap = sp == 0 ? ctx->dis[d].weights.capacity_e : ctx->dis[d].weights.capacity_i;
+            if (n > cap) return fail(ctx, PIC_ERR_CAPACITY, "profile integral exceeds the store capacity");
+            counts[2 * d + sp] = n;
+            double run = 0.0;
+            unsigned char* out = host.data() + ((size_t)d * 3 + sp) * P * r;
+            for (int j = 0; j < P; ++j) {
+                double v;
+                if (j == 0) v = 0.0;
+                else if (j == P - 1) v = 1.0;
+                else {
+                    run += 0.5 * (std::fmax(prof[j - 1], 0.0) + std::fmax(prof[j], 0.0)) * dz;
+                    v = A > 0.0 ? run / A : 0.0;
+                }
+                if (ctx->fp64) std::memcpy(out + j * r, &v, 8);
+                else {
+                    const float fv = (float)v;
+                    std::memcpy(out + j * r, &fv, 4);
+                }
+            }
+        }
+        unsigned char* out = host.data() + ((size_t)d * 3 + 2) * P * r;
+        for (int j = 0; j < P; ++j) {
+            const double v = std::fmax(pr[2 * (size_t)P + j], 0.0);
+            if (ctx->fp64) std::memcpy(out + j * r, &v, 8);
+            else {
+                const float fv = (float)v;
+                std::memcpy(out + j * r, &fv, 4);
+            }
+        }
+    }
+    void* dtab = nullptr;
+    void* ddesc = nullptr;
+    const size_t dsz = warm_desc_bytes(ctx->fp64);
+    if (cudaMalloc(&dtab, host.size()) != cudaSuccess || cudaMalloc(&ddesc, dsz * nd) != cudaSuccess) {
+        cudaFree(dtab);
+        return fail(ctx, PIC_ERR_CUDA, "warm-start tables");
+    }
+    std::vector<unsigned char> desc(dsz * nd);
+    const double K23 = 2.0 * H_E_CHARGE / (3.0 * H_M_ELEC);
+    for (int d = 0; d < nd; ++d) {
+        unsigned char* base = (unsigned char*)dtab + (size_t)d * 3 * P * r;
+        warm_desc_fill(ctx->fp64, desc.data() + dsz * d, base, base + P * r, base + 2 * P * r, P,
+                       (double)ctx->dis[d].n_cells / (double)(P - 1), K23);
+    }
+    cudaError_t e = cudaMemcpy(dtab, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ddesc, desc.data(), desc.size(), cudaMemcpyHostToDevice);
+    for (int d = 0; d < nd && e == cudaSuccess; ++d)
+        e = cudaMemcpy(&ctx->d_ctl->count[d][0], &counts[2 * d], 16, cudaMemcpyHostToDevice);
+    for (auto& D : ctx->hd) {
+        const size_t b = 8 * ((size_t)D.N + 1);
+        if (e == cudaSuccess) e = cudaMemset(D.D[0], 0, b);
+        if (e == cudaSuccess) e = cudaMemset(D.D[1], 0, b);
+        if (e == cudaSuccess) e = cudaMemset(D.Q, 0, b);
+    }
+    const int gx = std::max(1, ctx->num_sms * 4);
+    ctx->cur = 0;
+    if (e == cudaSuccess)
+        e = launch_load_profile(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->seed, ddesc, gx, ctx->stream);
+    if (e == cudaSuccess) e = launch_set_dense(ctx->d_discs, nd, ctx->d_ctl, ctx->stream);
+    if (e == cudaSuccess) e = launch_deposit(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->max_N, gx, ctx->stream);
+    if (e == cudaSuccess) e = launch_finalize(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = launch_backkick(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, gx, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dtab);
+    cudaFree(ddesc);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "warm start");
+    ctx->deposits_zero = true;
+    return PIC_OK;
 }

@@ -58,6 +58,7 @@ struct Disc {
     int steps_per_period;
     double dx, dt, V_rf, f_rf, w[2];
     int has_see, tile;        // sweep tile (slots) of this context
+    int chunk, warps;         // compaction unit: one warp's 32 PPT slots; warps per tile
     Consts<float> cf;
     Consts<double> cd;
     const void* Te;           // n_pts rows x 4 (T): cumulative sigma*v, electrons
@@ -66,15 +67,18 @@ struct Disc {
     void* p[2][2];            // [buffer][species] {f, vx, vy, vz} records
     long long cap[2];         // capacity per species (superparticles)
     long long max_tiles[2];   // ceil(cap / tile)
-    long long R0[2];          // offset of the births region in a record buffer
-    long long rcap[2];        // records per buffer: max_tiles 2 tile + bcap
-    int* seg_start[2];        // [max_tiles + 2] segment table of the current store
-    int* seg_src[2];          // [max_tiles + 1]
-    int* first_seg[2];        // [max_tiles + 1] segment holding slot j tile
-    int* cnt_main[2];         // [max_tiles] same-species outputs of each sweep tile
-    int* cnt_birth[2];        // [max_tiles] other-species births of each sweep tile
-    int32_t* bc[2];           // births of the other species, by parent species:
-    void* bp[2];              //   tile t owns records [t tile, (t+1) tile)
+    long long R0[2];          // offset of the newborn region in a record buffer: max_tiles tile
+    long long rcap[2];        // records per buffer: R0 + bcap (chunk k's survivors at [k chunk, ...))
+    int* seg_start[2];        // [max_tiles warps + 2] segment table of the current store
+    int* seg_src[2];          // [max_tiles warps + 1]
+    int* first_seg[2];        // [max_tiles warps + 1] segment holding slot j chunk
+    int* cnt_main[2];         // [max_tiles warps] survivors of each sweep chunk
+    int* cnt_birth[2];        // [max_tiles warps] other-species newborns of each sweep chunk
+    int* cnt_same;            // [max_tiles warps] ionization electrons of each electron-sweep chunk
+    int32_t* bc[2];           // newborns of the other species, by parent species:
+    void* bp[2];              //   chunk k owns records [k chunk, (k+1) chunk)
+    int32_t* sc;              // ionization electrons of the electron sweep, same chunk regions
+    void* sp_;
     long long bcap;           // births region size in the record buffers
     void* E;                  // node field for the gather (T), N+1
     double* E64;              // node field, FP64
@@ -86,6 +90,7 @@ struct Disc {
     double* acc_Q;
     double* acc_Dprev;
     unsigned long long* cnt;  // NCNT counters
+    double* period_mean;      // [PERIOD_HIST][2] mean superparticle count of every rf period
 };
 
 // Control block; one per context, in device memory.
@@ -100,7 +105,10 @@ struct Ctl {
     int nseg[MAXD][2];        // segments per store
     long long acc_steps[MAXD];
     double E0_last[MAXD];
+    double period_acc[MAXD][2];   // sum of the counts over the steps of the current rf period
 };
+
+constexpr int PERIOD_HIST = 1 << 16;  // rf periods of mean counts kept per discharge (ring)
 
 struct alignas(32) d4 {
     double x, y, z, w;

@@ -39,6 +39,11 @@ template <typename T> struct T4;
 template <> struct T4<float> { using type = float4; using two = float2; };
 template <> struct T4<double> { using type = d4; using two = double2; };
 
+template <int V>
+struct IC {
+    static constexpr int value = V;
+};
+
 template <typename T>
 struct Part {
     int c;
@@ -56,8 +61,10 @@ struct Seg {
     const void* pin;
     int32_t* cout;
     void* pout;
-    int32_t* bc;
+    int32_t* bc;      // other-species newborns of this sweep, chunk regions
     void* bp;
+    int32_t* sc;      // same-species newborns (ionization electrons), chunk regions
+    void* sp_;
     const void* Te;
     const void* Ti;
     unsigned long long* Dg;
@@ -70,11 +77,12 @@ struct Seg {
     int nseg;
     int* cnt_main;
     int* cnt_birth;
+    int* cnt_same;
 };
 
 // Window of the segment table staged in shared memory for one tile: segments
 // k0 .. k0+nw-1 and the start of segment k0+nw.
-constexpr int SEGWIN = 32;
+constexpr int SEGWIN = 128;
 struct SegWin {
     int k0, nw;
     int start[SEGWIN + 1];
@@ -88,12 +96,9 @@ __device__ __forceinline__ void seg_window_load(SegWin& W, const int* __restrict
     if (lane == 0) {
         W.k0 = k0;
         W.nw = nw;
-        W.start[SEGWIN] = 0x7FFFFFFF;
     }
-    const int k = k0 + lane;
-    W.start[lane] = (lane <= nw && k <= nseg) ? seg_start[k] : 0x7FFFFFFF;
-    W.src[lane] = (lane < nw) ? seg_src[k] : 0;
-    if (lane == 0 && nw == SEGWIN) W.start[SEGWIN] = seg_start[k0 + SEGWIN];
+    for (int j = lane; j <= SEGWIN; j += 32) W.start[j] = j <= nw ? seg_start[k0 + j] : 0x7FFFFFFF;
+    for (int j = lane; j < SEGWIN; j += 32) W.src[j] = j < nw ? seg_src[k0 + j] : 0;
 }
 
 // Buffer offset of a slot: the last segment whose start is <= slot holds it.
@@ -196,24 +201,22 @@ __device__ __forceinline__ void warp_hist(unsigned long long* h, int key, unsign
 
 // One collision candidate, queued by its warp in shared memory: the owner
 // writes the particle (cell, offset, gathered field, v_n); the lane that
-// processes the collision writes back the new velocity and the newborns after
-// their first drift.
+// processes the collision writes back the new velocity and flags the newborns
+// it left, after their first drift, in its scratch pair.
 template <typename T>
 struct QEnt {
     uint32_t slot;
     int c;
-    uint32_t out;     // bit1 same-species newborn stays, bit2 other-species birth stays
-    int pad_;
+    uint32_t out;     // bit1: same-species newborn in scratch[0], bit2: other-species newborn in scratch[1]
     T f, ef;
     T vx, vy, vz;     // in: v_n; out: velocity after the collision
-    Part<T> p1, p2;   // newborns (same species, other species) at x_{n+1}
 };
 
 // The collision of a queued candidate (null-collision method: process
 // selection against the cumulative rate tables, then the kinematics).
 template <typename T>
-__device__ __noinline__ void collide(const Seg<T>& S, QEnt<T>& q, long long step, unsigned long long seed,
-                                     unsigned long long* sH, unsigned* sC, int& err) {
+__device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, Part<T>* born, long long step,
+                                     unsigned long long seed, unsigned long long* sH, unsigned* sC, int& err) {
     using Row4 = typename T4<T>::type;
     using Row2 = typename T4<T>::two;
     const Consts<T>& K = S.k;
@@ -299,7 +302,7 @@ __device__ __noinline__ void collide(const Seg<T>& S, QEnt<T>& q, long long step
             cvz = fma_(K.K[0], q.ef, cvz);
             int side = drift(N, K.dtdx, q.c, q.f, cvz, cn, fn, err);
             if (side < 0) {
-                q.p1 = Part<T>{cn, fn, cvx, cvy, cvz};
+                born[0] = Part<T>{cn, fn, cvx, cvy, cvz};
                 shist_add(sH, cn, cic_F(fn));
                 out |= 2u;
             } else {
@@ -308,7 +311,7 @@ __device__ __noinline__ void collide(const Seg<T>& S, QEnt<T>& q, long long step
             ivz = fma_(K.K[1], q.ef, ivz);
             side = drift(N, K.dtdx, q.c, q.f, ivz, cn, fn, err);
             if (side < 0) {
-                q.p2 = Part<T>{cn, fn, ivx, ivy, ivz};
+                born[1] = Part<T>{cn, fn, ivx, ivy, ivz};
                 hist_add(S.Dother, cn, cic_F(fn));
                 out |= 4u;
             } else {
@@ -362,7 +365,7 @@ __device__ __noinline__ void collide(const Seg<T>& S, QEnt<T>& q, long long step
 
 // Secondary electron of an ion absorbed at electrode `side` (added option).
 template <typename T>
-__device__ __noinline__ bool emit_see(const Seg<T>& S, uint32_t slot, long long step, unsigned long long seed,
+__device__ __forceinline__ bool emit_see(const Seg<T>& S, uint32_t slot, long long step, unsigned long long seed,
                                       int side, Part<T>& p, unsigned* sC) {
     const Consts<T>& K = S.k;
     const U4 w = draw(seed, slot, step, 1, 3, S.did);
@@ -379,14 +382,14 @@ __device__ __noinline__ bool emit_see(const Seg<T>& S, uint32_t slot, long long 
 }
 
 template <typename T>
-__device__ __forceinline__ void store_rec(int32_t* c, void* p, long long i, const Part<T>& q);
+__device__ __forceinline__ void store_rec(int32_t* c, void* p, unsigned i, const Part<T>& q);
 template <>
-__device__ __forceinline__ void store_rec<float>(int32_t* c, void* p, long long i, const Part<float>& q) {
+__device__ __forceinline__ void store_rec<float>(int32_t* c, void* p, unsigned i, const Part<float>& q) {
     c[i] = q.c;
     reinterpret_cast<float4*>(p)[i] = make_float4(q.f, q.vx, q.vy, q.vz);
 }
 template <>
-__device__ __forceinline__ void store_rec<double>(int32_t* c, void* p, long long i, const Part<double>& q) {
+__device__ __forceinline__ void store_rec<double>(int32_t* c, void* p, unsigned i, const Part<double>& q) {
     c[i] = q.c;
     double2* pp = reinterpret_cast<double2*>(p) + 2 * i;
     pp[0] = make_double2(q.f, q.vx);
@@ -394,15 +397,15 @@ __device__ __forceinline__ void store_rec<double>(int32_t* c, void* p, long long
 }
 
 template <typename T>
-__device__ __forceinline__ void load_rec(const void* p, long long i, T& f, T& vx, T& vy, T& vz);
+__device__ __forceinline__ void load_rec(const void* p, unsigned i, T& f, T& vx, T& vy, T& vz);
 template <>
-__device__ __forceinline__ void load_rec<float>(const void* p, long long i, float& f, float& vx, float& vy,
+__device__ __forceinline__ void load_rec<float>(const void* p, unsigned i, float& f, float& vx, float& vy,
                                                 float& vz) {
     const float4 a = __ldcs(reinterpret_cast<const float4*>(p) + i);
     f = a.x; vx = a.y; vy = a.z; vz = a.w;
 }
 template <>
-__device__ __forceinline__ void load_rec<double>(const void* p, long long i, double& f, double& vx, double& vy,
+__device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, double& f, double& vx, double& vy,
                                                  double& vz) {
     const double2* pp = reinterpret_cast<const double2*>(p) + 2 * i;
     const double2 a = __ldcs(pp), b = __ldcs(pp + 1);
@@ -410,44 +413,61 @@ __device__ __forceinline__ void load_rec<double>(const void* p, long long i, dou
 }
 
 // Dynamic shared memory of the sweep: histogram and energy moment (u64, N+1
-// each), the node field (T, N+1), then the warps' candidate queues.
+// each), the node field (T, N+1), then per warp its candidate queue (one entry
+// per slot of its chunk) and its newborn scratch (a pair per lane).
 template <typename T>
 __host__ __device__ constexpr size_t sweep_queue_offset(int max_N) {
     return (((size_t)(max_N + 1) * (16 + sizeof(T)) + 15) / 16) * 16;
 }
 template <typename T, int BLOCK, int PPT>
+__host__ __device__ constexpr size_t sweep_born_offset(int max_N) {
+    return ((sweep_queue_offset<T>(max_N) + sizeof(QEnt<T>) * (size_t)BLOCK * PPT + 15) / 16) * 16;
+}
+template <typename T, int BLOCK, int PPT>
 __host__ __device__ constexpr size_t sweep_smem(int max_N) {
-    return sweep_queue_offset<T>(max_N) + sizeof(QEnt<T>) * (BLOCK / 32) * 32 * (PPT < 2 ? PPT : 2);
+    return sweep_born_offset<T, BLOCK, PPT>(max_N) + sizeof(Part<T>) * 2 * (size_t)BLOCK;
+}
+
+// Resident threads per SM the sweep is compiled for (the register budget is 65536 / that): the
+// FP32 chunk state (7 PPT registers per lane) fits 64 registers at PPT <= 2 and 80 at PPT = 4.
+template <typename T, int BLOCK, int PPT>
+__host__ __device__ constexpr int sweep_min_blocks() {
+    return (sizeof(T) == 4 ? (PPT <= 2 ? 1024 : PPT == 4 ? 768 : 512) : 256) / BLOCK > 0
+               ? (sizeof(T) == 4 ? (PPT <= 2 ? 1024 : PPT == 4 ? 768 : 512) : 256) / BLOCK
+               : 1;
 }
 
 // ---------------------------------------------------------------------------
-// The sweep. Persistent CTAs take tiles of TILE = BLOCK x PPT slots of every
-// store (discharge, species) in increasing order from a global dispenser.
-// Tile t of a store reads its slots through the store's segment table and
-// writes its outputs, in slot order, into its own region of the output buffer:
-// same-species outputs at [2 TILE t, ...), other-species births at [TILE t, ...)
-// of the birth buffer; it records both counts. No tile waits for another.
+// The sweep. Persistent CTAs take the tiles of TILE = BLOCK x PPT slots of all
+// stores (discharge, species) in a static grid-stride order; warp w of a tile
+// owns the chunk of CHUNK = 32 PPT consecutive slots at w CHUNK and works on it
+// alone, with no barrier: it loads its particles straight into registers
+// through the store's segment table, pushes them (gather, kick, energy moment,
+// candidate test), runs one collision pass over the chunk's candidates, then
+// kicks, drifts, deposits and writes the survivors in slot order to the
+// chunk's own output region [CHUNK cs, ...), cs the chunk index. Newborns go
+// in parent-slot order to the chunk's regions of the newborn buffers (same
+// species: ionization electrons; other species: ionization ions, or SEE
+// electrons of the ion sweep), and the chunk records the three counts. The
+// CTA synchronises only where its tiles move to another store (histogram
+// flush).
 template <typename T, int BLOCK, int PPT>
-__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
+__global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     k_sweep(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl, int in_buf, unsigned long long seed,
             int max_N) {
-    constexpr int TILE = BLOCK * PPT;
+    using R = typename Rec<T>::type;
     constexpr int NW = BLOCK / 32;
+    constexpr int CHUNK = 32 * PPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem_raw);
     unsigned long long* s_Q = s_hist + (max_N + 1);
     T* s_E = reinterpret_cast<T*>(s_Q + (max_N + 1));
     QEnt<T>* s_q = reinterpret_cast<QEnt<T>*>(smem_raw + sweep_queue_offset<T>(max_N));
+    Part<T>* s_born = reinterpret_cast<Part<T>*>(smem_raw + sweep_born_offset<T, BLOCK, PPT>(max_N));
 
     __shared__ long long s_segstart[2 * MAXD + 1];
     __shared__ Seg<T> S;
-    __shared__ SegWin W;
-    __shared__ unsigned int s_tile;
     __shared__ long long s_step;
-    constexpr int BATCH = PPT < 2 ? PPT : 2;   // iterations whose candidates share one queue pass
-    constexpr int QCAP = 32 * BATCH;           // queue entries per warp
-    __shared__ uint32_t s_wsum[BATCH][NW];
-    __shared__ uint32_t s_ktot[BATCH];
     __shared__ unsigned s_cnt[NCNT];
     __shared__ int s_err;
 
@@ -457,7 +477,7 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
         for (int s = 0; s < 2 * n_disc; ++s) {
             s_segstart[s] = acc;
             const long long n = ctl->count[s >> 1][s & 1];
-            acc += (n + TILE - 1) / TILE;
+            acc += (n + BLOCK * PPT - 1) / (BLOCK * PPT);
         }
         s_segstart[2 * n_disc] = acc;
         s_step = ctl->step;
@@ -483,20 +503,203 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
         __syncthreads();
     };
 
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&ctl->tile_ctr, 1u);
-        __syncthreads();
-        const long long g = s_tile;
-        if (g >= total_tiles) break;
+    QEnt<T>* Q = s_q + warp * CHUNK;
+    Part<T>* born = s_born + 2 * (warp * 32 + lane);
+    const unsigned lt = (1u << lane) - 1u;
+
+    // One warp's chunk of the store of species SP: load, push, collide, write (see above).
+    auto chunk = [&](unsigned cs, unsigned cbase, auto spc) {
+        constexpr int SP = decltype(spc)::value;
+        const unsigned n = (unsigned)S.n;
+        unsigned offA = cbase, offB = cbase, offS = cbase;  // output cursors of the chunk's regions
+        if (cbase < n) {
+            const int N = S.N;
+            // ---- load: slot s lives at seg_src[k] + (s - seg_start[k]), k the last segment with
+            // seg_start[k] <= s; the chunk's first 32 segments sit in registers (lane j: k0 + j)
+            const int nseg = S.nseg;
+            const int* __restrict__ seg_start = S.seg_start;
+            const int* __restrict__ seg_src = S.seg_src;
+            const bool dense = nseg <= 1;
+            int k0 = 0, w_start = 0, w_src = 0;
+            if (!dense) {
+                k0 = __ldg(&S.first_seg[cs]);
+                w_start = __ldg(&seg_start[min(k0 + lane, nseg)]);
+                w_src = __ldg(&seg_src[min(k0 + lane, nseg - 1)]);
+            }
+            auto start_of = [&](int k) -> unsigned {  // k uniform across the warp
+                const int v = __shfl_sync(FULL, w_start, (k - k0) & 31);
+                return (unsigned)(k - k0 < 32 ? v : __ldg(&seg_start[k]));
+            };
+            const int32_t* __restrict__ cin = S.cin;
+            const void* pin = S.pin;
+            int cc[PPT];
+            T fq[PPT], vxq[PPT], vyq[PPT], vzq[PPT];
+            int ks = k0;  // segment holding the first slot of the current 32
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const unsigned s0 = cbase + 32 * k, slot = s0 + lane;
+                cc[k] = -1;
+                fq[k] = vxq[k] = vyq[k] = vzq[k] = (T)0;
+                if (s0 < n) {
+                    unsigned off = slot;
+                    if (!dense) {
+                        while (ks + 1 < nseg && start_of(ks + 1) <= s0) ++ks;
+                        int my = ks;
+                        for (int nx = ks + 1; nx < nseg; ++nx) {
+                            const unsigned b = start_of(nx);
+                            if (b >= s0 + 32) break;
+                            if (b <= slot) my = nx;
+                        }
+                        const int dk = my - k0;
+                        int src = __shfl_sync(FULL, w_src, dk & 31), st = __shfl_sync(FULL, w_start, dk & 31);
+                        if (dk >= 32) {
+                            src = __ldg(&seg_src[my]);
+                            st = __ldg(&seg_start[my]);
+                        }
+                        off = (unsigned)src + (slot - (unsigned)st);
+                    }
+                    if (slot < n) {
+                        cc[k] = __ldcs(cin + off);
+                        load_rec<T>(pin, off, fq[k], vxq[k], vyq[k], vzq[k]);
+                    }
+                }
+            }
+            // candidate words: slots 4q..4q+3 take the four words of one Philox call (call 4,
+            // counter word 0 = q); lane l computes group q = (cbase + 32 k) / 4 + j for k = i / 8,
+            // j = i % 8, i = l + 32 m, and iteration k takes its word by shuffle
+            constexpr int NG = (8 * PPT + 31) / 32;
+            const uint32_t did = S.did, thr = S.thr;
+            U4 cw[NG];
+#pragma unroll
+            for (int m = 0; m < NG; ++m) {
+                const int i = lane + 32 * m;
+                const unsigned q = (cbase + 32u * (unsigned)(i >> 3)) / 4 + (unsigned)(i & 7);
+                cw[m] = draw(seed, q, step, SP, 4, did);
+            }
+            const T Ksp = S.k.K[SP];
+            // ---- phase A: gather, first half kick, energy moment, candidate test
+            T efq[PPT];
+            int qiq[PPT];
+            int qn = 0;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (cc[k] >= 0 && !((unsigned)cc[k] < (unsigned)N)) {
+                    err |= ERR_NONFINITE;  // corrupt cell index: dropped and reported
+                    cc[k] = -1;
+                }
+                const bool valid = cc[k] >= 0;
+                efq[k] = (T)0;
+                unsigned long long qv = 0;
+                if (valid) {
+                    const int c = cc[k];
+                    const T E0 = s_E[c], E1 = s_E[c + 1];
+                    efq[k] = fma_(fq[k], sub_(E1, E0), E0);
+                    vzq[k] = fma_(Ksp, efq[k], vzq[k]);  // v_n
+                    if (SP == 0) {  // energy moment at (x_n, v_n), 2^-12 eV, clamped at 2^26
+                        const T e2 = fma_(vxq[k], vxq[k], fma_(vyq[k], vyq[k], mul_(vzq[k], vzq[k])));
+                        T eq = mul_(e2, S.k.kappa_E);
+                        if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
+                        const unsigned long long Et = rint_u32(eq);
+                        const unsigned long long Eh = rint_u32(mul_(eq, fq[k]));
+                        qv = (Et - Eh) | (Eh << 32);
+                    }
+                }
+                if (SP == 0) warp_hist<true>(s_Q, cc[k], qv, lane);
+                const int src_lane = (8 * k + (lane >> 2)) & 31;
+                const U4& g4 = cw[(8 * k) >> 5];
+                const uint32_t w0 = __shfl_sync(FULL, g4.x, src_lane), w1 = __shfl_sync(FULL, g4.y, src_lane);
+                const uint32_t w2 = __shfl_sync(FULL, g4.z, src_lane), w3 = __shfl_sync(FULL, g4.w, src_lane);
+                const int wi = lane & 3;
+                const uint32_t cword = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
+                const bool cand = valid && cword < thr;
+                const unsigned cm = __ballot_sync(FULL, cand);
+                if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + SP], (unsigned)__popc(cm));
+                qiq[k] = cand ? qn + __popc(cm & lt) : -1;
+                if (cand) {
+                    QEnt<T>& e = Q[qiq[k]];
+                    e.slot = cbase + 32 * k + lane;
+                    e.c = cc[k];
+                    e.out = 0;
+                    e.f = fq[k];
+                    e.ef = efq[k];
+                    e.vx = vxq[k];
+                    e.vy = vyq[k];
+                    e.vz = vzq[k];
+                }
+                qn += __popc(cm);
+            }
+            // ---- phase B: the chunk's candidates, 32 at a time; newborns in queue (= slot) order
+            __syncwarp();
+            for (int r0 = 0; r0 < qn; r0 += 32) {
+                const int q = r0 + lane;
+                if (q < qn) collide<T>(S, Q[q], born, step, seed, s_hist, s_cnt, err);
+                __syncwarp();
+                if (SP == 0) {
+                    const uint32_t o = q < qn ? Q[q].out : 0u;
+                    const unsigned m1 = __ballot_sync(FULL, (o & 2u) != 0), m2 = __ballot_sync(FULL, (o & 4u) != 0);
+                    if (o & 2u) store_rec<T>(S.sc, S.sp_, offS + __popc(m1 & lt), born[0]);
+                    if (o & 4u) store_rec<T>(S.bc, S.bp, offB + __popc(m2 & lt), born[1]);
+                    offS += __popc(m1);
+                    offB += __popc(m2);
+                    __syncwarp();
+                }
+            }
+            // ---- phase C: second half kick, drift, walls, deposit, survivors in slot order
+            const T dtdx = S.k.dtdx;
+            int32_t* __restrict__ cout = S.cout;
+            void* pout = S.pout;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                bool alive = false, see = false;
+                Part<T> P0{}, Pse{};
+                if (cc[k] >= 0) {
+                    T vx = vxq[k], vy = vyq[k], vz = vzq[k];
+                    if (qiq[k] >= 0) {
+                        const QEnt<T>& e = Q[qiq[k]];
+                        vx = e.vx;
+                        vy = e.vy;
+                        vz = e.vz;
+                    }
+                    vz = fma_(Ksp, efq[k], vz);
+                    int cn;
+                    T fn;
+                    const int side = drift(N, dtdx, cc[k], fq[k], vz, cn, fn, err);
+                    if (side < 0) {
+                        P0 = Part<T>{cn, fn, vx, vy, vz};
+                        alive = true;
+                    } else {
+                        atomicAdd(&s_cnt[CNT_ABS + 2 * SP + side], 1u);
+                        if (SP == 1 && S.has_see)
+                            see = emit_see<T>(S, cbase + 32 * k + lane, step, seed, side, Pse, s_cnt);
+                    }
+                }
+                warp_hist<false>(s_hist, alive ? P0.c : -1, alive ? (1ull << 40) + cic_F(P0.f) : 0ull, lane);
+                const unsigned mA = __ballot_sync(FULL, alive);
+                if (alive) store_rec<T>(cout, pout, offA + __popc(mA & lt), P0);
+                offA += __popc(mA);
+                if (SP == 1) {
+                    const unsigned mB = __ballot_sync(FULL, see);
+                    if (see) store_rec<T>(S.bc, S.bp, offB + __popc(mB & lt), Pse);
+                    offB += __popc(mB);
+                }
+            }
+        }
+        if (lane == 0) {
+            S.cnt_main[cs] = (int)(offA - cbase);
+            S.cnt_birth[cs] = (int)(offB - cbase);
+            if (SP == 0) S.cnt_same[cs] = (int)(offS - cbase);
+        }
+    };
+
+    for (long long g = blockIdx.x; g < total_tiles; g += gridDim.x) {
         int seg = 0;
         {
-            int lo = 0, hi = 2 * n_disc - 1;  // largest store with segstart <= g
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_segstart[mid] <= g) lo = mid;
+            int hi = 2 * n_disc - 1;  // largest store with segstart <= g
+            while (seg < hi) {
+                const int mid = (seg + hi + 1) >> 1;
+                if (s_segstart[mid] <= g) seg = mid;
                 else hi = mid - 1;
             }
-            seg = lo;
         }
         if (seg != cur_seg) {
             if (cur_seg >= 0) flush();
@@ -515,14 +718,14 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
                 S.n = ctl->count[d][sp];
                 S.cap = D.cap[sp];
                 S.bcap = D.bcap;
-                S.tile0 = s_segstart[seg];
-                S.ntiles = s_segstart[seg + 1] - s_segstart[seg];
                 S.cin = D.c[in_buf][sp];
                 S.pin = D.p[in_buf][sp];
                 S.cout = D.c[1 - in_buf][sp];
                 S.pout = D.p[1 - in_buf][sp];
                 S.bc = D.bc[sp];
                 S.bp = D.bp[sp];
+                S.sc = D.sc;
+                S.sp_ = D.sp_;
                 S.Te = D.Te;
                 S.Ti = D.Ti;
                 S.Dg = D.D[sp];
@@ -535,6 +738,7 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
                 S.nseg = ctl->nseg[d][sp];
                 S.cnt_main = D.cnt_main[sp];
                 S.cnt_birth = D.cnt_birth[sp];
+                S.cnt_same = D.cnt_same;
             }
             if (tid < NCNT) s_cnt[tid] = 0;
             __syncthreads();
@@ -551,185 +755,12 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
             __syncthreads();
         }
 
-        const long long ts = g - S.tile0;
-        const long long base = ts * TILE;
-        if (warp == 0)
-            seg_window_load(W, S.seg_start, S.seg_src, S.nseg, S.nseg <= 1 ? 0 : S.first_seg[ts], lane);
-        __syncthreads();
-        int cin[PPT];
-        T fin[PPT], vxin[PPT], vyin[PPT], vzin[PPT];
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const long long slot = base + (long long)k * BLOCK + tid;
-            cin[k] = -1;
-            if (slot < S.n) {
-                const long long off = seg_offset(W, S.seg_start, S.seg_src, S.nseg, slot);
-                const int cc = __ldcs(S.cin + off);
-                load_rec<T>(S.pin, off, fin[k], vxin[k], vyin[k], vzin[k]);
-                if ((unsigned)cc < (unsigned)S.N) cin[k] = cc;
-                else err |= ERR_NONFINITE;  // corrupt cell index: dropped and reported
-            }
-        }
-        // Candidate words: slots 4q..4q+3 take the four words of one Philox call (call 4,
-        // counter word 0 = q). Lane l of warp w computes group q = (base + k BLOCK + 32 w) / 4 + j
-        // for k = i / 8, j = i % 8, i = l + 32 m; iteration k takes its word by shuffle.
-        constexpr int NG = (8 * PPT + 31) / 32;
-        U4 cw[NG];
-#pragma unroll
-        for (int m = 0; m < NG; ++m) {
-            const int i = lane + 32 * m;
-            const long long q = (base + (long long)(i >> 3) * BLOCK + 32 * warp) / 4 + (i & 7);
-            cw[m] = draw(seed, (uint32_t)q, step, S.sp, 4, S.did);
-        }
-        QEnt<T>* Q = s_q + warp * QCAP;
-        const T Ksp = S.k.K[S.sp];
-        long long offA = ts * (2 * TILE), offB = ts * TILE;
-#pragma unroll
-        for (int b = 0; b < PPT; b += BATCH) {
-            // phase A: gather, first half kick, energy moment, candidate test; candidates queued
-            T ef[BATCH];
-            uint32_t fl[BATCH];
-            int qi[BATCH];
-            int qn = 0;
-#pragma unroll
-            for (int kk = 0; kk < BATCH; ++kk) {
-                const int k = b + kk;
-                const int src_lane = (8 * k + (lane >> 2)) & 31;
-                const U4& g4 = cw[(8 * k) >> 5];
-                const uint32_t w0 = __shfl_sync(FULL, g4.x, src_lane), w1 = __shfl_sync(FULL, g4.y, src_lane);
-                const uint32_t w2 = __shfl_sync(FULL, g4.z, src_lane), w3 = __shfl_sync(FULL, g4.w, src_lane);
-                const int wi = lane & 3;
-                const uint32_t cword = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
-                const bool valid = cin[k] >= 0;
-                unsigned long long qv = 0;
-                ef[kk] = 0;
-                if (valid) {
-                    const int c = cin[k];
-                    const T E0 = s_E[c], E1 = s_E[c + 1];
-                    ef[kk] = fma_(fin[k], sub_(E1, E0), E0);
-                    vzin[k] = fma_(Ksp, ef[kk], vzin[k]);  // v_n
-                    if (S.sp == 0) {  // energy moment at (x_n, v_n), 2^-12 eV, clamped at 2^26
-                        const T e2 = fma_(vxin[k], vxin[k], fma_(vyin[k], vyin[k], mul_(vzin[k], vzin[k])));
-                        T eq = mul_(e2, S.k.kappa_E);
-                        if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
-                        const unsigned long long Et = rint_u32(eq);
-                        const unsigned long long Eh = rint_u32(mul_(eq, fin[k]));
-                        qv = (Et - Eh) | (Eh << 32);
-                    }
-                }
-                if (S.sp == 0) warp_hist<true>(s_Q, cin[k], qv, lane);
-                const bool cand = valid && cword < S.thr;
-                const unsigned cm = __ballot_sync(FULL, cand);
-                if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + S.sp], (unsigned)__popc(cm));
-                qi[kk] = qn + __popc(cm & ((1u << lane) - 1u));
-                if (cand) {
-                    QEnt<T>& e = Q[qi[kk]];
-                    e.slot = (uint32_t)(base + (long long)k * BLOCK + tid);
-                    e.c = cin[k];
-                    e.f = fin[k];
-                    e.ef = ef[kk];
-                    e.vx = vxin[k];
-                    e.vy = vyin[k];
-                    e.vz = vzin[k];
-                }
-                qn += __popc(cm);
-                fl[kk] = cand ? 8u : 0u;
-            }
-            __syncwarp();
-            // phase B: the warp works through its queue, 32 candidates at a time
-            for (int q = lane; q < qn; q += 32) collide<T>(S, Q[q], step, seed, s_hist, s_cnt, err);
-            __syncwarp();
-            // phase C: second half kick, drift, walls, deposit
-            Part<T> P0[BATCH], Pse[BATCH];
-#pragma unroll
-            for (int kk = 0; kk < BATCH; ++kk) {
-                const int k = b + kk;
-                bool alive = false;
-                if (cin[k] >= 0) {
-                    T vx = vxin[k], vy = vyin[k], vz = vzin[k];
-                    if (fl[kk] & 8u) {
-                        const QEnt<T>& e = Q[qi[kk]];
-                        vx = e.vx;
-                        vy = e.vy;
-                        vz = e.vz;
-                        fl[kk] |= e.out;
-                    }
-                    vz = fma_(Ksp, ef[kk], vz);
-                    int cn;
-                    T fn;
-                    const int side = drift(S.N, S.k.dtdx, cin[k], fin[k], vz, cn, fn, err);
-                    if (side < 0) {
-                        P0[kk] = Part<T>{cn, fn, vx, vy, vz};
-                        alive = true;
-                        fl[kk] |= 1u;
-                    } else {
-                        atomicAdd(&s_cnt[CNT_ABS + 2 * S.sp + side], 1u);
-                        if (S.sp == 1 && S.has_see &&
-                            emit_see<T>(S, (uint32_t)(base + (long long)k * BLOCK + tid), step, seed, side, Pse[kk],
-                                        s_cnt))
-                            fl[kk] |= 4u;
-                    }
-                }
-                warp_hist<false>(s_hist, alive ? P0[kk].c : -1, alive ? (1ull << 40) + cic_F(P0[kk].f) : 0ull,
-                                 lane);
-            }
-            // block scan of (same-species outputs | births << 16) per k of the batch, in slot order
-            uint32_t v[BATCH], incl[BATCH];
-#pragma unroll
-            for (int kk = 0; kk < BATCH; ++kk) {
-                v[kk] = (fl[kk] & 1u) + ((fl[kk] >> 1) & 1u) + (((fl[kk] >> 2) & 1u) << 16);
-                incl[kk] = v[kk];
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                for (int kk = 0; kk < BATCH; ++kk) {
-                    const uint32_t t = __shfl_up_sync(FULL, incl[kk], o);
-                    if (lane >= o) incl[kk] += t;
-                }
-            }
-            if (lane == 31) {
-#pragma unroll
-                for (int kk = 0; kk < BATCH; ++kk) s_wsum[kk][warp] = incl[kk];
-            }
-            __syncthreads();
-            if (warp == 0) {
-#pragma unroll
-                for (int kk = 0; kk < BATCH; ++kk) {
-                    const uint32_t own = lane < NW ? s_wsum[kk][lane] : 0u;
-                    uint32_t x = own;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t t = __shfl_up_sync(FULL, x, o);
-                        if (lane >= o) x += t;
-                    }
-                    if (lane < NW) s_wsum[kk][lane] = x - own;
-                    if (lane == NW - 1) s_ktot[kk] = x;
-                }
-            }
-            __syncthreads();
-            // phase D: write the batch's outputs into the tile's regions, in slot order
-#pragma unroll
-            for (int kk = 0; kk < BATCH; ++kk) {
-                const uint32_t ex = incl[kk] - v[kk] + s_wsum[kk][warp];
-                long long ia = offA + (ex & 0xFFFFu);
-                const long long ib = offB + (ex >> 16);
-                if (fl[kk] & 1u) {
-                    store_rec<T>(S.cout, S.pout, ia, P0[kk]);
-                    ++ia;
-                }
-                if (fl[kk] & 2u) store_rec<T>(S.cout, S.pout, ia, Q[qi[kk]].p1);
-                if (fl[kk] & 4u) store_rec<T>(S.bc, S.bp, ib, S.sp == 0 ? Q[qi[kk]].p2 : Pse[kk]);
-                offA += s_ktot[kk] & 0xFFFFu;
-                offB += s_ktot[kk] >> 16;
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            S.cnt_main[ts] = (int)(offA - ts * (2 * TILE));
-            S.cnt_birth[ts] = (int)(offB - ts * TILE);
-        }
-        __syncthreads();
+        // chunk index in the store and its first slot (slots and record offsets fit in 31 bits:
+        // the host caps every record buffer below 2^31)
+        const unsigned cs = (unsigned)(g - s_segstart[seg]) * NW + warp;
+        const unsigned cbase = cs * CHUNK;
+        if (S.sp == 0) chunk(cs, cbase, IC<0>{});
+        else chunk(cs, cbase, IC<1>{});
     }
     if (cur_seg >= 0) flush();
     if (err) atomicOr(&s_err, err);
@@ -740,7 +771,6 @@ __global__ void __launch_bounds__(BLOCK, (sizeof(T) == 4 ? 512 : 256) / BLOCK)
         const unsigned prev = atomicAdd(&ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             for (int i = 0; i < 2 * n_disc; ++i) ctl->count_in[i >> 1][i & 1] = ctl->count[i >> 1][i & 1];
-            ctl->tile_ctr = 0;
             ctl->done = 0;
             __threadfence();
         }
@@ -851,45 +881,55 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
         // tiles' regions (slot order), then one segment of the births of sp that the other
         // species' tiles produced, compacted here into the births region.
         using R = typename Rec<T>::type;
-        const int TILE = D.tile;
-        if (tid == 0) {
-            for (int sp = 0; sp < 2; ++sp) s_n[sp][0] = (ctl->count_in[d][sp] + TILE - 1) / TILE;  // input tiles
+        const int TILE = D.tile, CHUNK = D.chunk;
+        if (tid == 0) {  // input chunks: every warp chunk of every tile of the last sweep
+            for (int sp = 0; sp < 2; ++sp) s_n[sp][0] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
         }
         __syncthreads();
         {
             const int sp = role - 1;
-            const int par = 1 - sp;
-            const long long tiles = s_n[sp][0], ptiles = s_n[par][0];
+            const long long chunks = s_n[sp][0];
             int* st = D.seg_start[sp];
             int* sr = D.seg_src[sp];
-            const long long main_total = block_chunk_scan<BLOCK>(D.cnt_main[sp], tiles, s_lscan,
+            const long long main_total = block_chunk_scan<BLOCK>(D.cnt_main[sp], chunks, s_lscan,
                 [&](long long t, long long ex, int c) {
                     st[t] = (int)ex;
-                    sr[t] = (int)(t * 2 * TILE);
+                    sr[t] = (int)(t * CHUNK);
                 });
+            // newborns, appended after the survivors in parent-slot order: for electrons the
+            // ionization electrons, then the SEE electrons of the ion sweep; for ions the
+            // ionization ions
             int32_t* cdst = D.c[out_buf][sp];
             R* pdst = reinterpret_cast<R*>(D.p[out_buf][sp]);
-            const int32_t* csrc = D.bc[par];
-            const R* psrc = reinterpret_cast<const R*>(D.bp[par]);
             const long long R0 = D.R0[sp], bcap = D.bcap;
-            const long long nb = block_chunk_scan<BLOCK>(D.cnt_birth[par], ptiles, s_lscan,
-                [&](long long t, long long ex, int c) {
-                    for (int k = 0; k < c; ++k) {
-                        if (ex + k < bcap) {
-                            cdst[R0 + ex + k] = csrc[t * TILE + k];
-                            pdst[R0 + ex + k] = psrc[t * TILE + k];
-                        } else {
-                            s_err = ERR_CAPACITY;
+            long long nb = 0;
+            for (int src = 0; src < (sp == 0 ? 2 : 1); ++src) {
+                const bool same = sp == 0 && src == 0;
+                const int par = same ? 0 : 1 - sp;  // species whose sweep made them
+                const int32_t* csrc = same ? D.sc : D.bc[par];
+                const R* psrc = reinterpret_cast<const R*>(same ? D.sp_ : D.bp[par]);
+                const int* cnt = same ? D.cnt_same : D.cnt_birth[par];
+                const long long base = nb;
+                nb += block_chunk_scan<BLOCK>(cnt, s_n[par][0], s_lscan,
+                    [&](long long t, long long ex, int c) {
+                        for (int k = 0; k < c; ++k) {
+                            const long long o = base + ex + k;
+                            if (o < bcap) {
+                                cdst[R0 + o] = csrc[t * CHUNK + k];
+                                pdst[R0 + o] = psrc[t * CHUNK + k];
+                            } else {
+                                s_err = ERR_CAPACITY;
+                            }
                         }
-                    }
-                });
+                    });
+            }
             const long long nbk = nb < bcap ? nb : bcap;
-            const int nseg = (int)tiles + (nbk > 0 ? 1 : 0);
+            const int nseg = (int)chunks + (nbk > 0 ? 1 : 0);
             long long n_new = main_total + nbk;
             if (tid == 0) {
                 if (nbk > 0) {
-                    st[tiles] = (int)main_total;
-                    sr[tiles] = (int)R0;
+                    st[chunks] = (int)main_total;
+                    sr[chunks] = (int)R0;
                 }
                 st[nseg] = (int)n_new;
                 if (n_new > D.cap[sp]) {
@@ -898,15 +938,24 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
                 }
                 ctl->count[d][sp] = n_new;
                 ctl->nseg[d][sp] = nseg;
+                if (mode & 2) {  // per-period mean counts (steady-state criterion)
+                    const long long n_step = ctl->step;  // this step is n; the counts belong to n+1
+                    ctl->period_acc[d][sp] += (double)n_new;
+                    if (D.steps_per_period > 0 && (n_step + 1) % D.steps_per_period == 0) {
+                        const long long per = (n_step + 1) / D.steps_per_period - 1;
+                        D.period_mean[(per % PERIOD_HIST) * 2 + sp] = ctl->period_acc[d][sp] / D.steps_per_period;
+                        ctl->period_acc[d][sp] = 0.0;
+                    }
+                }
             }
             __syncthreads();
-            // first segment of every tile of the next sweep: the segment holding slot j TILE
-            const long long jmax = D.max_tiles[sp];
+            // first segment of every chunk of the next sweep: the segment holding slot j CHUNK
+            const long long jmax = (long long)D.max_tiles[sp] * D.warps;
             for (int k = tid; k < nseg; k += BLOCK) {
                 const long long s0 = st[k], s1 = st[k + 1];
                 if (s1 > s0) {
-                    const long long j1 = (s1 + TILE - 1) / TILE;
-                    for (long long j = (s0 + TILE - 1) / TILE; j < j1 && j <= jmax; ++j) D.first_seg[sp][j] = k;
+                    const long long j1 = (s1 + CHUNK - 1) / CHUNK;
+                    for (long long j = (s0 + CHUNK - 1) / CHUNK; j < j1 && j <= jmax; ++j) D.first_seg[sp][j] = k;
                 }
             }
             __syncthreads();
@@ -1037,6 +1086,65 @@ __global__ void k_load(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, in
     }
 }
 
+// Warm start: particles sampled from profiles on a uniform grid of P points
+// (calls 0xF2, 0xF3 at step 0): position by inverse of the piecewise-constant
+// CDF, electrons Maxwellian at kT = 2/3 <eps>(z), ions at T_i0.
+template <typename T>
+struct WarmDev {
+    const T* cdf[2];  // per species, P entries, cdf[0] = 0, cdf[P-1] = 1
+    const T* eps;     // P entries, eV
+    int P, pad_;
+    T scale;          // N / (P - 1)
+    T K23;            // 2 e / (3 m_e)
+};
+
+template <typename T>
+__global__ void k_load_profile(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int buf,
+                               unsigned long long seed, const WarmDev<T>* __restrict__ warm) {
+    const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
+    const Disc& D = discs[d];
+    const WarmDev<T>& W = warm[d];
+    const long long n = ctl->count[d][sp];
+    const int N = D.N, P = W.P;
+    const T* cdf = W.cdf[sp];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const U4 r = draw(seed, (uint32_t)k, 0, sp, 0xF2, D.discharge_id);
+        const U4 q = draw(seed, (uint32_t)k, 0, sp, 0xF3, D.discharge_id);
+        const T u = (T)u01(r.x);
+        int lo = 0, hi = P - 2;  // largest j in [0, P-2] with cdf[j] <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cdf[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const int j = lo;
+        const T den = sub_(cdf[j + 1], cdf[j]);
+        T t = den > (T)0 ? div_(sub_(u, cdf[j]), den) : (T)0;
+        if (t >= (T)1) t = one_minus_ulp<T>();
+        const T x = mul_(add_((T)j, t), W.scale);
+        int c = (int)x;
+        T f;
+        if (c >= N) {
+            c = N - 1;
+            f = one_minus_ulp<T>();
+        } else {
+            f = sub_(x, (T)c);
+        }
+        T sg;
+        if (sp == 0) {
+            T el = fma_(t, sub_(W.eps[j + 1], W.eps[j]), W.eps[j]);
+            if (!(el > (T)0)) el = (T)0;
+            sg = sqrt_(mul_(el, W.K23));
+        } else {
+            sg = consts_of<T>(D).sig0[1];
+        }
+        float n0, n1, n2, n3;
+        box_muller(u01(r.y), u01(r.z), n0, n1);
+        box_muller(u01(r.w), u01(q.x), n2, n3);
+        store_rec<T>(D.c[buf][sp], D.p[buf][sp], k, Part<T>{c, f, mul_(sg, (T)n0), mul_(sg, (T)n1), mul_(sg, (T)n2)});
+    }
+}
+
 // CIC deposit of whole stores (used after a load or a state upload).
 template <typename T>
 __global__ void k_deposit(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl, int buf, int max_N) {
@@ -1124,11 +1232,11 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restric
     const int32_t* cc = D.c[buf][sp];
     unsigned* H = hist + hoff[seg];
     const int lane = threadIdx.x & 31;
-    const int per_sweep_tile = SORT_TILE / D.tile;
+    const int per_chunk = SORT_TILE / D.chunk;
     for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = threadIdx.x; j < N; j += SORT_BLOCK) s_c[j] = 0;
         if (threadIdx.x < 32)
-            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_sweep_tile],
+            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_chunk],
                             lane);
         __syncthreads();
         for (int i = threadIdx.x; i < SORT_TILE; i += SORT_BLOCK) {
@@ -1257,11 +1365,11 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     unsigned* Wc = s_w + warp * max_N;
-    const int per_sweep_tile = SORT_TILE / D.tile;
+    const int per_chunk = SORT_TILE / D.chunk;
     for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = tid; j < SORT_NW * max_N; j += SORT_BLOCK) s_w[j] = 0;
         if (warp == 0)
-            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_sweep_tile],
+            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_chunk],
                             lane);
         __syncthreads();
         const long long wbase = t * SORT_TILE + (long long)warp * (SORT_R * 32);
@@ -1443,6 +1551,39 @@ cudaError_t launch_load(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int b
     if (fp64) k_load<double><<<g, 256, 0, st>>>(discs, ctl, buf, seed);
     else k_load<float><<<g, 256, 0, st>>>(discs, ctl, buf, seed);
     return cudaGetLastError();
+}
+
+cudaError_t launch_load_profile(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
+                                const void* warm, int grid_x, cudaStream_t st) {
+    dim3 g(grid_x, 2 * n_disc);
+    if (fp64) k_load_profile<double><<<g, 256, 0, st>>>(discs, ctl, buf, seed, (const WarmDev<double>*)warm);
+    else k_load_profile<float><<<g, 256, 0, st>>>(discs, ctl, buf, seed, (const WarmDev<float>*)warm);
+    return cudaGetLastError();
+}
+
+size_t warm_desc_bytes(int fp64) { return fp64 ? sizeof(WarmDev<double>) : sizeof(WarmDev<float>); }
+
+void warm_desc_fill(int fp64, void* out, const void* cdf_e, const void* cdf_i, const void* eps, int P, double scale,
+                    double K23) {
+    if (fp64) {
+        WarmDev<double> w{};
+        w.cdf[0] = (const double*)cdf_e;
+        w.cdf[1] = (const double*)cdf_i;
+        w.eps = (const double*)eps;
+        w.P = P;
+        w.scale = scale;
+        w.K23 = K23;
+        *(WarmDev<double>*)out = w;
+    } else {
+        WarmDev<float> w{};
+        w.cdf[0] = (const float*)cdf_e;
+        w.cdf[1] = (const float*)cdf_i;
+        w.eps = (const float*)eps;
+        w.P = P;
+        w.scale = (float)scale;
+        w.K23 = (float)K23;
+        *(WarmDev<float>*)out = w;
+    }
 }
 
 cudaError_t launch_deposit(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int buf, int max_N, int grid_x,

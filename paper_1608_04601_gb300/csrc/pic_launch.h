@@ -26,6 +26,11 @@ cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, 
 cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int src, int dst, unsigned* hist,
                         const long long* hoff, unsigned* tot, int max_N, int grid_x, cudaStream_t st);
 long long sort_tile();
+cudaError_t launch_load_profile(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
+                                const void* warm, int grid_x, cudaStream_t st);
+size_t warm_desc_bytes(int fp64);
+void warm_desc_fill(int fp64, void* out, const void* cdf_e, const void* cdf_i, const void* eps, int P, double scale,
+                    double K23);
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);

@@ -211,6 +211,25 @@ class Simulation:
     def reset_moments(self):
         self._ck(self.L.pic_reset_moments(self.h))
 
+    def load_profiles(self, profiles):
+        """Warm start from profiles (n_discharges, 3, n_pts): n_e, n_i (m^-3), mean electron energy (eV)."""
+        a = np.ascontiguousarray(profiles, np.float64)
+        if a.ndim == 2:
+            a = a[None]
+        assert a.shape[0] == len(self.N) and a.shape[1] == 3
+        self._ck(self.L.pic_load_profiles(self.h, a.shape[2], _ptr(a)))
+
+    def period_counts(self, d: int = 0, first: int = 0, n=None) -> np.ndarray:
+        """(periods, 2) mean superparticle counts per completed rf period (electrons, ions)."""
+        done = C.c_int64()
+        self._ck(self.L.pic_period_counts(self.h, d, 0, 0, None, C.byref(done)))
+        if n is None:
+            n = done.value - first
+        out = np.zeros((max(n, 0), 2))
+        if n > 0:
+            self._ck(self.L.pic_period_counts(self.h, d, first, n, _ptr(out), C.byref(done)))
+        return out
+
     def sweep_timing(self, enable: bool = True):
         ms = C.c_double()
         n = C.c_int64()

@@ -363,3 +363,44 @@ def test_full_steps_track_oracle(P, prec):
         na, nb = sim.count(0, sp), ref.count(sp)
         assert abs(na - nb) <= 6 * math.sqrt(max(abs(4000 - nb), 100)) + 0.03 * nb, (sp, na, nb)
     sim.close()
+
+
+# ----------------------------------------------------------------------------- warm start
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_warm_load_matches_oracle(P, prec):
+    """Warm start from profiles: counts, sampled positions and velocities, initial field and the
+    half back-kick agree with the oracle's loader drawing the same Philox streams."""
+    gas = X.he_like(eps_max_eV=200.0, de_eV=1e-2)
+    gap = 0.025
+    d = I.discharge(n_cells=128, n_e0=20000, n_i0=20000, V_rf_V=150.0, n_init_m3=1e15, gap_m=gap)
+    Pn = 57  # about 30000 electrons and 35600 ions at the weight 1.25e9
+    z = np.linspace(0.0, gap, Pn)
+    ne = 3e15 * np.sin(np.pi * z / gap) ** 2
+    ni = 3.2e15 * np.sin(np.pi * z / gap) ** 1.5
+    eps = 1.0 + 5.0 * (2 * z / gap - 1) ** 2
+    sim = P.Simulation(gas, d, precision=prec, load=False)
+    sim.load_profiles(np.stack([ne, ni, eps]))
+    ref = O.Oracle(gas, d, _prec(prec), load=False)
+    ref.load_profiles(ne, ni, eps)
+    for sp in (0, 1):
+        a, b = sim.get_state(0, sp), ref.get_state(sp)
+        assert a["c"].size == b["c"].size > 1000
+        assert_state_equal(a, b, what=f"warm load sp{sp}")
+        for k in ("c", "f", "vx", "vy"):
+            assert np.array_equal(a[k], b[k])
+    E, E64, phi = sim.get_field(0)
+    assert np.max(np.abs(E64 - ref.get_field64())) <= 1e-12 * np.max(np.abs(ref.get_field64()))
+    sim.step(3)
+    ref.step(3)
+    for sp in (0, 1):
+        assert_state_equal(sim.get_state(0, sp), ref.get_state(sp), what=f"warm steps sp{sp}")
+    sim.close()
+    with pytest.raises(RuntimeError):
+        s2 = P.Simulation(gas, d, precision=prec)
+        try:
+            s2.step(1)
+            s2.load_profiles(np.stack([ne, ni, eps]))
+        finally:
+            s2.close()

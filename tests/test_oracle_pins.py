@@ -666,3 +666,78 @@ def test_f32_build_runs_and_matches_physics_build_statistically():
     m64, m32 = o64.moments(), o32.moments()
     rel = np.linalg.norm(m64["n_i"] - m32["n_i"]) / np.linalg.norm(m64["n_i"])
     assert rel < 0.05
+
+
+def test_steady_state_criterion():
+    """Block-mean steady-state criterion: a count that relaxes exponentially to a plateau is steady
+    once 50-period means 50 periods apart differ by < 1e-3; pure noise of 1e-2 per period is
+    averaged down by the blocks."""
+    from paper_1608_04601_gb300.steady import steady_period
+    k = np.arange(2000)
+    m = 1e5 * (1 + 0.5 * np.exp(-k / 100.0))
+    ks = steady_period(np.stack([m, m], 1))
+    # |mean_a - mean_b| / mean_a ~ 0.5 e^{-k/100} (e^{0.5} - 1) * (100/50) (1 - e^{-0.5}) < 1e-3
+    exact = next(kk for kk in range(100, 2000)
+                 if abs(np.mean(m[kk - 50:kk]) - np.mean(m[kk - 100:kk - 50])) / np.mean(m[kk - 50:kk]) < 1e-3)
+    assert ks == exact
+    rng = np.random.default_rng(0)
+    flat = 1e5 * (1 + 1e-3 * rng.standard_normal((400, 2)))
+    assert steady_period(flat) == 100
+    assert steady_period(np.stack([m, m * 0 + 1e5], 1)[:150]) is None
+
+
+def _tent_profiles(P, gap, n0e, n0i):
+    """Tent electron density, flat ion density and a linear mean energy on P points over [0, gap]:
+    piecewise linear, so the trapezoid integrals of the loader are exact."""
+    z = np.linspace(0.0, gap, P)
+    ne = n0e * np.minimum(z, gap - z) / (gap / 2)
+    ni = np.full(P, n0i)
+    eps = 2.0 + 4.0 * z / gap
+    return z, np.stack([ne, ni, eps])
+
+
+def test_warm_load_follows_profiles():
+    """Warm start from density and mean-energy profiles (the paper's proposal of initial values
+    closer to the periodic state, section 'Numerical parameters and initial values'): the count is
+    the profile integral over the weight, positions follow the density, electron velocities are
+    Maxwellian with kT = 2/3 of the local mean energy, ion velocities Maxwellian at T_gas."""
+    P, gap, N = 33, 0.025, 64
+    d = I.discharge(n_cells=N, n_e0=1, n_i0=1, V_rf_V=0.0, n_init_m3=1e14, gap_m=gap)
+    o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=False)
+    z, prof = _tent_profiles(P, gap, 4e15, 1.5e15)
+    o.load_profiles(*prof)
+    ne_int, ni_int = 4e15 * gap / 2, 1.5e15 * gap  # exact integrals of the tent and the flat profile
+    assert o.count(0) == math.floor(ne_int / d.w_e + 0.5)
+    assert o.count(1) == math.floor(ni_int / d.w_i + 0.5)
+    for sp in (0, 1):
+        st = o.get_state(sp)
+        x = (st["c"] + st["f"]) / N * gap
+        n = x.size
+        # fraction below each profile point = the exact cumulative integral there
+        frac = np.array([np.mean(x < zj) for zj in z[1:-1]])
+        u = z[1:-1] / gap
+        cdf = np.where(u <= 0.5, 2 * u ** 2, 1 - 2 * (1 - u) ** 2) if sp == 0 else u
+        assert np.all(np.abs(frac - cdf) <= 5 * np.sqrt(cdf * (1 - cdf) / n) + 1e-12)
+        if sp == 0:
+            sig = np.sqrt(I.E_CH * (2.0 + 4.0 * x / gap) * 2.0 / (3.0 * I.M_E))
+        else:
+            sig = np.full(n, math.sqrt(I.K_B * d.T_gas_K / (4.002602 * I.AMU)))
+        for k in ("vx", "vy"):
+            assert stats.kstest(st[k] / sig, "norm").pvalue > 1e-4
+    # the field is solved at t = 0 from the loaded charge: non-zero, since n_e != n_i
+    assert np.max(np.abs(o.get_field())) > 0
+
+
+def test_warm_load_clips_negative_density_and_loads_empty_species():
+    """A zero ion profile loads no ions; negative profile values count as zero."""
+    P, gap = 9, 0.025
+    d = I.discharge(n_cells=32, n_e0=1, n_i0=1, V_rf_V=0.0, n_init_m3=1e14, gap_m=gap)
+    o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=False)
+    z = np.linspace(0, gap, P)
+    ne = np.where(z < gap / 2, 2e15, -1e15)  # negative half clipped to zero
+    o.load_profiles(ne, np.zeros(P), np.full(P, 3.0))
+    assert o.count(1) == 0
+    A = sum(0.5 * (max(ne[j], 0) + max(ne[j + 1], 0)) * (gap / (P - 1)) for j in range(P - 1))
+    assert o.count(0) == math.floor(A / d.w_e + 0.5)
+    st = o.get_state(0)
+    assert np.all((st["c"] + st["f"]) / 32 * gap <= z[P // 2 + 1])
