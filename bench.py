@@ -68,39 +68,68 @@ def recorded_traffic(prec: str):
 
 
 class Clocks:
+    """nvidia-smi samples (every 20 ms) of SM clock, power and throttle reasons. Each sample is
+    stamped on arrival; summary() keeps those that arrived inside the marked timed window (widened
+    by one sampling interval on each side)."""
+
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.samples = []
+        self.t0 = self.t1 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
 
+    def _reader(self):
+        for ln in self.proc.stdout:
+            self.samples.append((time.time(), ln.strip()))
+
     def __enter__(self):
+        import threading
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._reader, daemon=True).start()
+            t_end = time.time() + 5.0
+            while not self.samples and time.time() < t_end:  # sampler running before the window opens
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, start: bool):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.05)
             self.proc.terminate()
             try:
                 self.proc.wait(5)
             except Exception:
                 self.proc.kill()
-            self.f.close()
+            try:
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
+                with open(self.path, "w") as f:
+                    for t, ln in self.samples:
+                        f.write(f"{t:.3f}, {ln}\n")
+            except OSError:
+                pass
 
     def summary(self):
-        if not self.proc or not os.path.exists(self.path):
+        if not self.proc or self.t0 is None or self.t1 is None:
             return None
         sm, mx, reasons = [], [], set()
-        for ln in open(self.path):
+        for t, ln in self.samples:
+            if not (self.t0 - 0.025 <= t <= self.t1 + 0.025):
+                continue
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -116,7 +145,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window_s": round(self.t1 - self.t0, 3)}
 
 
 def reduce_over_ranks(total_ms: float, ps: float, world: int, device: str):
@@ -156,6 +185,7 @@ def run_gpu(args, rank: int, world: int):
         sim.sweep_timing(True)
         torch.cuda.synchronize()
         with Clocks(dev) as clk:
+            clk.mark(True)
             for k in range(steps):
                 counts.append(sim.count(0, 0) + sim.count(0, 1))
                 flush.fill_(float(k))
@@ -163,6 +193,7 @@ def run_gpu(args, rank: int, world: int):
                 sim.step(1)
                 ev[k][1].record(stream)
             torch.cuda.synchronize()
+            clk.mark(False)
         sim.sync()
         sweep_ms, launches = sim.sweep_timing(False)
         step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -170,10 +201,11 @@ def run_gpu(args, rank: int, world: int):
         ps = float(sum(counts))
         out = {"ps": ps, "total_ms": total_ms, "sweep_ms": sweep_ms, "sweep_launches": launches,
                "clocks": clk.summary(), "counts": (counts[0], counts[-1])}
-        # kernels launched per step: sweep + finalize, and the 4 sort kernels when a sort is due
+        # kernels launched per step: sweep, finalize (field, store totals) and the segment-table pass;
+        # when a sort is due its count, row-scan, cell-scan and scatter kernels and the dense reset
         step0 = sim.step_index - steps
         sorts = sum(1 for n in range(step0 + 1, step0 + steps + 1) if sort_every > 0 and n % sort_every == 0)
-        out["gpu_launches"] = 2 * steps + 4 * sorts
+        out["gpu_launches"] = 3 * steps + 5 * sorts
         sim.close()
         return out
 
@@ -246,6 +278,13 @@ def run_gpu(args, rank: int, world: int):
                 "one_at_a_time": {"value": ps_s / (t_s * 1e-3), "ms_per_step": t_s},
                 "particles": int(ps_b / steps)}
 
+    tuned = None
+    if args.autotune:
+        # small search of the launch shape and the sort period on this workload (whole steps, L2 flushed)
+        from paper_1608_04601_gb300 import autotune
+        tuned = autotune.autotune([gas], [(d, 0)], "fp32", tiles=[(256, 2), (256, 4), (128, 4)], ctas=[0],
+                                  sorts=[4, 8], use_cache=False)
+        args.block, args.ppt, args.sort_every = tuned["block"], tuned["ppt"], tuned["sort_every"]
     sort_every = args.sort_every
     main = measure("fp32", args.steps, args.warmup, sort_every)
     fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
@@ -275,7 +314,8 @@ def run_gpu(args, rank: int, world: int):
            "config": {"workload": d0.name, "cells": d0.n_cells, "particles_per_species": d0.n_e0,
                       "steps_per_period": d0.steps_per_period, "sort_every": sort_every,
                       "block": args.block, "ppt": args.ppt, "parallelism": f"replicas{world}" if world > 1 else "1gpu",
-                      "l2": "flushed (256 MB write) before every timed step"},
+                      "l2": "flushed (256 MB write) before every timed step",
+                      "autotuned": tuned},
            "roofline": roofline,
            "fp64_path": {"value": fp64["ps"] / (fp64["total_ms"] * 1e-3), "unit": UNIT,
                          "ms_per_step": fp64["total_ms"] / max(1, max(4, args.steps // 2)),
@@ -310,7 +350,7 @@ def run_cpu_baseline(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--sort-every", type=int, default=4)
@@ -319,6 +359,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use --block/--ppt/--sort-every as given instead of searching")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -19,6 +19,8 @@ using namespace pic;
 #define H_K_BOLTZ 1.380649e-23
 #define H_TWO32 4294967296.0
 #define H_T_SEE_EV 2.0
+#define H_EPS0 8.8541878128e-12
+#define H_PI 3.14159265358979323846
 
 struct GasDev {
     int n_pts, n_exc;
@@ -49,6 +51,7 @@ struct pic_ctx {
     long long step = 0;
     bool deposits_zero = true;
     int sweep_grid = 0, num_sms = 0;
+    int max_slices = 0;  // slices of sweep chunks of the largest store
     std::string err;
     pic_counters cnt_at_reset[MAXD];
     bool timing = false;
@@ -357,10 +360,37 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.f_rf = d.f_rf_Hz;
         D.w[0] = d.weights.w_e;
         D.w[1] = d.weights.w_i;
+        for (int sp = 0; sp < 2; ++sp) {
+            D.pc_r[sp] = H_E_CHARGE * D.w[sp] * der.dx / (H_TWO32 * H_EPS0);
+            D.pc_w[sp] = H_E_CHARGE * D.w[sp] / (H_TWO32 * 0.5 * der.dx);
+        }
+        D.inv_dx = 1.0 / der.dx;
+        D.m_inv_2dx = -1.0 / (2.0 * der.dx);
+        D.hdx_eps = der.dx / (2.0 * H_EPS0);
+        D.inv_N = 1.0 / (double)d.n_cells;
+        D.V0tab = nullptr;
+        {
+            // one rf period of V(t) when dt divides it (f dt steps_per_period = 1 to 1e-12)
+            const int spp = d.weights.steps_per_period;
+            if (spp > 0 && std::fabs(d.f_rf_Hz * d.dt_s * spp - 1.0) <= 1e-12) {
+                std::vector<double> v((size_t)spp);
+                for (int k = 0; k < spp; ++k)
+                    v[(size_t)k] = d.V_rf_V * std::sin(2.0 * H_PI * d.f_rf_Hz * ((double)k * d.dt_s));
+                double* dv = nullptr;
+                ALLOC(dv, double*, sizeof(double) * (size_t)spp);
+                if (cudaMemcpy(dv, v.data(), sizeof(double) * (size_t)spp, cudaMemcpyHostToDevice) != cudaSuccess) {
+                    pic_status s_ = fail(ctx, PIC_ERR_CUDA, "voltage table");
+                    pic_destroy(ctx);
+                    return s_;
+                }
+                D.V0tab = dv;
+            }
+        }
         D.has_see = d.weights.gamma_see > 0.0;
         D.tile = (int)tile;
         D.chunk = 32 * o.ppt;
         D.warps = o.block / 32;
+        D.rec_words = ctx->fp64 ? 2 : 1;
         fill_consts<float>(D.cf, der, d);
         fill_consts<double>(D.cd, der, d);
         D.Te = g.Te;
@@ -394,6 +424,15 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
             ALLOC(D.first_seg[sp], int*, sizeof(int) * (mc + 2));
             ALLOC(D.cnt_main[sp], int*, sizeof(int) * (mc + 1));
             ALLOC(D.cnt_birth[sp], int*, sizeof(int) * (mc + 1));
+            const size_t ns = (mc + SLICE - 1) / SLICE + 1;
+            ctx->max_slices = std::max(ctx->max_slices, (int)ns);
+            ALLOC(D.slice_tot[sp], unsigned*, sizeof(unsigned) * 3 * ns);
+            ALLOC(D.slice_pre[sp], unsigned*, sizeof(unsigned) * 3 * ns);
+            if (cudaMemset(D.slice_tot[sp], 0, sizeof(unsigned) * 3 * ns) != cudaSuccess) {
+                pic_status s_ = fail(ctx, PIC_ERR_CUDA, "slice sums");
+                pic_destroy(ctx);
+                return s_;
+            }
             if (sp == 0) {
                 ALLOC(D.sc, int32_t*, sizeof(int32_t) * (mt * tile + 16));
                 ALLOC(D.sp_, void*, rec * (mt * tile + 16));
@@ -408,10 +447,10 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ALLOC(D.D[1], unsigned long long*, 8 * N1);
         ALLOC(D.Q, unsigned long long*, 8 * N1);
         ALLOC(D.Dprev, unsigned long long*, 8 * N1);
-        ALLOC(D.acc_D[0], double*, 8 * N1);
-        ALLOC(D.acc_D[1], double*, 8 * N1);
-        ALLOC(D.acc_Q, double*, 8 * N1);
-        ALLOC(D.acc_Dprev, double*, 8 * N1);
+        ALLOC(D.acc_D[0], unsigned __int128*, 16 * N1);
+        ALLOC(D.acc_D[1], unsigned __int128*, 16 * N1);
+        ALLOC(D.acc_Q, unsigned __int128*, 16 * N1);
+        ALLOC(D.acc_Dprev, unsigned __int128*, 16 * N1);
         ALLOC(D.cnt, unsigned long long*, 8 * NCNT);
         ALLOC(D.period_mean, double*, sizeof(double) * 2 * PERIOD_HIST);
         ctx->hd.push_back(D);
@@ -448,7 +487,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ce = launch_load(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, seed, gx, ctx->stream);
         if (ce == cudaSuccess) ce = launch_deposit(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, ctx->max_N, gx,
                                                    ctx->stream);
-        if (ce == cudaSuccess) ce = launch_finalize(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, 4, ctx->stream);
+        if (ce == cudaSuccess) ce = launch_finalize(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, 4, 0, ctx->stream);
         if (ce == cudaSuccess) ce = launch_backkick(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, gx, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
         if (ce != cudaSuccess) {
@@ -523,7 +562,7 @@ static pic_status enqueue_sweep(pic_ctx* ctx) {
 
 static pic_status enqueue_finalize(pic_ctx* ctx, int mode) {
     CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, mode & 1 ? 1 - ctx->cur : ctx->cur, mode,
-                       ctx->stream),
+                       ctx->max_slices, ctx->stream),
        "finalize launch");
     if (mode & 1) ctx->cur = 1 - ctx->cur;
     if (mode & 2) ctx->step += 1;
@@ -617,7 +656,8 @@ extern "C" pic_status pic_sweep(pic_ctx* ctx) {
     pic_status s = enqueue_sweep(ctx);
     if (s != PIC_OK) return s;
     // births appended and counts updated; no solve, no step advance
-    CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, 1 - ctx->cur, 1 | 8, ctx->stream),
+    CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, 1 - ctx->cur, 1 | 8, ctx->max_slices,
+                       ctx->stream),
        "append launch");
     ctx->cur = 1 - ctx->cur;
     return PIC_OK;
@@ -825,11 +865,18 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
     const Disc& D = ctx->hd[d];
     const int N = D.N;
     const size_t N1 = (size_t)N + 1;
+    std::vector<unsigned __int128> iD0(N1), iD1(N1), iQ(N1), iP(N1);
+    CK(cudaMemcpy(iD0.data(), D.acc_D[0], 16 * N1, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(iD1.data(), D.acc_D[1], 16 * N1, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(iQ.data(), D.acc_Q, 16 * N1, cudaMemcpyDeviceToHost), "moments");
+    CK(cudaMemcpy(iP.data(), D.acc_Dprev, 16 * N1, cudaMemcpyDeviceToHost), "moments");
     std::vector<double> aD0(N1), aD1(N1), aQ(N1), aP(N1);
-    CK(cudaMemcpy(aD0.data(), D.acc_D[0], 8 * N1, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(aD1.data(), D.acc_D[1], 8 * N1, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(aQ.data(), D.acc_Q, 8 * N1, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(aP.data(), D.acc_Dprev, 8 * N1, cudaMemcpyDeviceToHost), "moments");
+    for (size_t j = 0; j < N1; ++j) {
+        aD0[j] = (double)iD0[j];
+        aD1[j] = (double)iD1[j];
+        aQ[j] = (double)iQ[j];
+        aP[j] = (double)iP[j];
+    }
     long long steps = 0, cnt[2] = {0, 0};
     double E0 = 0;
     CK(cudaMemcpy(&steps, &ctx->d_ctl->acc_steps[d], 8, cudaMemcpyDeviceToHost), "moments");
@@ -862,7 +909,7 @@ extern "C" pic_status pic_reset_moments(pic_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     for (int d = 0; d < ctx->n_disc; ++d) {
         const Disc& D = ctx->hd[d];
-        const size_t b = 8 * ((size_t)D.N + 1);
+        const size_t b = 16 * ((size_t)D.N + 1);
         CK(cudaMemset(D.acc_D[0], 0, b), "reset");
         CK(cudaMemset(D.acc_D[1], 0, b), "reset");
         CK(cudaMemset(D.acc_Q, 0, b), "reset");
@@ -1020,7 +1067,7 @@ extern "C" pic_status pic_load_profiles(pic_ctx* ctx, int32_t n_pts, const doubl
         e = launch_load_profile(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->seed, ddesc, gx, ctx->stream);
     if (e == cudaSuccess) e = launch_set_dense(ctx->d_discs, nd, ctx->d_ctl, ctx->stream);
     if (e == cudaSuccess) e = launch_deposit(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->max_N, gx, ctx->stream);
-    if (e == cudaSuccess) e = launch_finalize(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = launch_finalize(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, 4, 0, ctx->stream);
     if (e == cudaSuccess) e = launch_backkick(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, gx, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(dtab);

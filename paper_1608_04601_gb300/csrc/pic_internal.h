@@ -8,6 +8,7 @@ namespace pic {
 
 constexpr int MAXD = 64;      // discharges per context
 constexpr int MAXN = 4096;    // cells per discharge
+constexpr int SLICE = 4096;   // sweep chunks per slice of the segment-table pass
 constexpr int NCNT = 16;      // event counters per discharge
 
 // Event counter slots (u64 each), per discharge.
@@ -57,8 +58,14 @@ struct Disc {
     uint32_t discharge_id;
     int steps_per_period;
     double dx, dt, V_rf, f_rf, w[2];
+    // Poisson constants (host-computed, so the FP64 solve needs no device division):
+    // r_j = pc_r[1] D_i,j - pc_r[0] D_e,j = rho_j dx^2 / eps0 inside; wall charge density
+    // rho = pc_w[1] D_i - pc_w[0] D_e (half-cell volume); 1/dx, -1/(2 dx), dx/(2 eps0), 1/N
+    double pc_r[2], pc_w[2], inv_dx, m_inv_2dx, hdx_eps, inv_N;
+    const double* V0tab;      // V_rf sin(2 pi f k dt), k < steps_per_period, or null (then sin on device)
     int has_see, tile;        // sweep tile (slots) of this context
     int chunk, warps;         // compaction unit: one warp's 32 PPT slots; warps per tile
+    int rec_words;            // particle record size in 16-byte words (1: FP32, 2: FP64)
     Consts<float> cf;
     Consts<double> cd;
     const void* Te;           // n_pts rows x 4 (T): cumulative sigma*v, electrons
@@ -79,6 +86,11 @@ struct Disc {
     void* bp[2];              //   chunk k owns records [k chunk, (k+1) chunk)
     int32_t* sc;              // ionization electrons of the electron sweep, same chunk regions
     void* sp_;
+    // per slice of SLICE sweep chunks of species sp, [k][3]: 0 survivors, 1 other-species
+    // newborns, 2 same-species newborns. slice_tot: sums (the sweep adds, the segment pass
+    // clears); slice_pre: output offsets of the slice's first chunk (finalize)
+    unsigned* slice_tot[2];
+    unsigned* slice_pre[2];
     long long bcap;           // births region size in the record buffers
     void* E;                  // node field for the gather (T), N+1
     double* E64;              // node field, FP64
@@ -86,9 +98,9 @@ struct Disc {
     unsigned long long* D[2]; // CIC deposits at x_{n+1}, 2^32 per particle
     unsigned long long* Q;    // electron energy moment at x_n, 2^-12 eV
     unsigned long long* Dprev;// electron deposit at x_n
-    double* acc_D[2];
-    double* acc_Q;
-    double* acc_Dprev;
+    unsigned __int128* acc_D[2];    // exact sums over the accumulated steps of D, Q, D at x_n
+    unsigned __int128* acc_Q;
+    unsigned __int128* acc_Dprev;
     unsigned long long* cnt;  // NCNT counters
     double* period_mean;      // [PERIOD_HIST][2] mean superparticle count of every rf period
 };

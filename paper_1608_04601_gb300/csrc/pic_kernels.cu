@@ -78,53 +78,59 @@ struct Seg {
     int* cnt_main;
     int* cnt_birth;
     int* cnt_same;
+    unsigned* slice_tot;
 };
 
-// Window of the segment table staged in shared memory for one tile: segments
-// k0 .. k0+nw-1 and the start of segment k0+nw.
-constexpr int SEGWIN = 128;
-struct SegWin {
-    int k0, nw;
-    int start[SEGWIN + 1];
-    int src[SEGWIN];
-};
+// Slot -> record offset through a store's segment table for a warp that walks
+// groups of 32 consecutive slots upwards (lane l holds slot s0 + l): slot s
+// lives at seg_src[k] + (s - seg_start[k]), k the last segment with
+// seg_start[k] <= s. The 32 segments from the first one of the walk sit in
+// registers (lane j holds segment k0 + j); later ones are read from memory.
+struct SegCursor {
+    const int* start;
+    const int* src;
+    int nseg, k0, ws, wr, ks;
 
-// Loaded by one warp: the window starting at segment k0.
-__device__ __forceinline__ void seg_window_load(SegWin& W, const int* __restrict__ seg_start,
-                                                const int* __restrict__ seg_src, int nseg, int k0, int lane) {
-    const int nw = min(SEGWIN, nseg - k0);
-    if (lane == 0) {
-        W.k0 = k0;
-        W.nw = nw;
-    }
-    for (int j = lane; j <= SEGWIN; j += 32) W.start[j] = j <= nw ? seg_start[k0 + j] : 0x7FFFFFFF;
-    for (int j = lane; j < SEGWIN; j += 32) W.src[j] = j < nw ? seg_src[k0 + j] : 0;
-}
-
-// Buffer offset of a slot: the last segment whose start is <= slot holds it.
-__device__ __forceinline__ long long seg_offset(const SegWin& W, const int* __restrict__ seg_start,
-                                                const int* __restrict__ seg_src, int nseg, long long slot) {
-    if (slot < (long long)W.start[1]) return (long long)W.src[0] + (slot - W.start[0]);  // first segment
-    if (slot < (long long)W.start[W.nw]) {
-        int lo = 0, hi = W.nw - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((long long)W.start[mid] <= slot) lo = mid;
-            else hi = mid - 1;
+    // first_slot < count: first slot of the walk; first_seg[j] = segment holding slot j chunk
+    __device__ __forceinline__ void init(const int* seg_start, const int* seg_src, const int* first_seg, int nseg_,
+                                         unsigned first_slot, int chunk, int lane) {
+        start = seg_start;
+        src = seg_src;
+        nseg = nseg_;
+        k0 = 0;
+        ws = 0;
+        wr = 0;
+        if (nseg > 1) {
+            k0 = __ldg(&first_seg[first_slot / (unsigned)chunk]);
+            ws = __ldg(&start[min(k0 + lane, nseg)]);
+            wr = __ldg(&src[min(k0 + lane, nseg - 1)]);
         }
-        return (long long)W.src[lo] + (slot - W.start[lo]);
+        ks = k0;
     }
-    int lo = W.k0 + W.nw, hi = nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((long long)seg_start[mid] <= slot) lo = mid;
-        else hi = mid - 1;
+    __device__ __forceinline__ unsigned start_of(int k) const {  // k uniform across the warp
+        const int v = __shfl_sync(0xFFFFFFFFu, ws, (k - k0) & 31);
+        return (unsigned)(k - k0 < 32 ? v : __ldg(&start[k]));
     }
-    return (long long)seg_src[lo] + (slot - seg_start[lo]);
-}
+    // Called by the whole warp with s0 uniform, s0 below the count and at or above the last s0.
+    __device__ __forceinline__ unsigned offset(unsigned s0, unsigned slot) {
+        if (nseg <= 1) return slot;
+        while (ks + 1 < nseg && start_of(ks + 1) <= s0) ++ks;
+        int my = ks;
+        for (int nx = ks + 1; nx < nseg; ++nx) {
+            const unsigned b = start_of(nx);
+            if (b >= s0 + 32) break;
+            if (b <= slot) my = nx;
+        }
+        const int dk = my - k0;
+        int sr = __shfl_sync(0xFFFFFFFFu, wr, dk & 31), st = __shfl_sync(0xFFFFFFFFu, ws, dk & 31);
+        if (dk >= 32) {
+            sr = __ldg(&src[my]);
+            st = __ldg(&start[my]);
+        }
+        return (unsigned)sr + (slot - (unsigned)st);
+    }
+};
 
-// Drift x_{n+1} = x_n + v_z dt in cell units. Returns -1 (inside) with the new
-// (cell, offset), or the electrode reached (0: z = 0, 1: z = d).
 template <typename T>
 __device__ __forceinline__ int drift(int N, T dtdx, int c, T f, T vz, int& cn, T& fn, int& err) {
     const T s = fma_(vz, dtdx, f);
@@ -514,50 +520,20 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         unsigned offA = cbase, offB = cbase, offS = cbase;  // output cursors of the chunk's regions
         if (cbase < n) {
             const int N = S.N;
-            // ---- load: slot s lives at seg_src[k] + (s - seg_start[k]), k the last segment with
-            // seg_start[k] <= s; the chunk's first 32 segments sit in registers (lane j: k0 + j)
-            const int nseg = S.nseg;
-            const int* __restrict__ seg_start = S.seg_start;
-            const int* __restrict__ seg_src = S.seg_src;
-            const bool dense = nseg <= 1;
-            int k0 = 0, w_start = 0, w_src = 0;
-            if (!dense) {
-                k0 = __ldg(&S.first_seg[cs]);
-                w_start = __ldg(&seg_start[min(k0 + lane, nseg)]);
-                w_src = __ldg(&seg_src[min(k0 + lane, nseg - 1)]);
-            }
-            auto start_of = [&](int k) -> unsigned {  // k uniform across the warp
-                const int v = __shfl_sync(FULL, w_start, (k - k0) & 31);
-                return (unsigned)(k - k0 < 32 ? v : __ldg(&seg_start[k]));
-            };
+            // ---- load, through the store's segment table
+            SegCursor cur;
+            cur.init(S.seg_start, S.seg_src, S.first_seg, S.nseg, cbase, CHUNK, lane);
             const int32_t* __restrict__ cin = S.cin;
             const void* pin = S.pin;
             int cc[PPT];
             T fq[PPT], vxq[PPT], vyq[PPT], vzq[PPT];
-            int ks = k0;  // segment holding the first slot of the current 32
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const unsigned s0 = cbase + 32 * k, slot = s0 + lane;
                 cc[k] = -1;
                 fq[k] = vxq[k] = vyq[k] = vzq[k] = (T)0;
                 if (s0 < n) {
-                    unsigned off = slot;
-                    if (!dense) {
-                        while (ks + 1 < nseg && start_of(ks + 1) <= s0) ++ks;
-                        int my = ks;
-                        for (int nx = ks + 1; nx < nseg; ++nx) {
-                            const unsigned b = start_of(nx);
-                            if (b >= s0 + 32) break;
-                            if (b <= slot) my = nx;
-                        }
-                        const int dk = my - k0;
-                        int src = __shfl_sync(FULL, w_src, dk & 31), st = __shfl_sync(FULL, w_start, dk & 31);
-                        if (dk >= 32) {
-                            src = __ldg(&seg_src[my]);
-                            st = __ldg(&seg_start[my]);
-                        }
-                        off = (unsigned)src + (slot - (unsigned)st);
-                    }
+                    const unsigned off = cur.offset(s0, slot);
                     if (slot < n) {
                         cc[k] = __ldcs(cin + off);
                         load_rec<T>(pin, off, fq[k], vxq[k], vyq[k], vzq[k]);
@@ -685,9 +661,14 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             }
         }
         if (lane == 0) {
-            S.cnt_main[cs] = (int)(offA - cbase);
-            S.cnt_birth[cs] = (int)(offB - cbase);
-            if (SP == 0) S.cnt_same[cs] = (int)(offS - cbase);
+            const unsigned a = offA - cbase, b = offB - cbase, c = offS - cbase;
+            S.cnt_main[cs] = (int)a;
+            S.cnt_birth[cs] = (int)b;
+            if (SP == 0) S.cnt_same[cs] = (int)c;
+            unsigned* sl = S.slice_tot + 3 * (cs / SLICE);
+            if (a) atomicAdd(&sl[0], a);
+            if (b) atomicAdd(&sl[1], b);
+            if (SP == 0 && c) atomicAdd(&sl[2], c);
         }
     };
 
@@ -739,6 +720,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 S.cnt_main = D.cnt_main[sp];
                 S.cnt_birth = D.cnt_birth[sp];
                 S.cnt_same = D.cnt_same;
+                S.slice_tot = D.slice_tot[sp];
             }
             if (tid < NCNT) s_cnt[tid] = 0;
             __syncthreads();
@@ -778,83 +760,70 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
 }
 
 // ---------------------------------------------------------------------------
-// Block-wide inclusive scan of doubles held as `per` consecutive elements per
-// thread (fixed association order, hence deterministic).
-template <int BLOCK>
-__device__ void block_scan_inclusive(double* a, int n, double* s_warp) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = BLOCK / 32;
-    const int per = (n + BLOCK - 1) / BLOCK;
-    const int lo = tid * per, hi = min(n, lo + per);
-    double run = 0.0;
-    for (int i = lo; i < hi; ++i) {
-        run = __dadd_rn(run, a[i]);
-        a[i] = run;
+// Integer prefix segment of the Poisson sums for both species: r = sum of
+// deposits, s = sum of the running r, L = elements. Segment A followed by B:
+// (r_A + r_B, s_A + L_B r_A + s_B, L_A + L_B); exact, so any order gives the same.
+struct ISeg {
+    long long r[2];
+    __int128 s[2];
+    int L;
+};
+__device__ __forceinline__ ISeg iseg_join(const ISeg& a, const ISeg& b) {
+    ISeg c;
+    for (int sp = 0; sp < 2; ++sp) {
+        c.r[sp] = a.r[sp] + b.r[sp];
+        c.s[sp] = a.s[sp] + (__int128)b.L * a.r[sp] + b.s[sp];
     }
-    double x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double t = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x = __dadd_rn(x, t);
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const double own = lane < NW ? s_warp[lane] : 0.0;
-        double y = own;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double t = __shfl_up_sync(FULL, y, o);
-            if (lane >= o) y = __dadd_rn(y, t);
-        }
-        if (lane < NW) s_warp[lane] = __dsub_rn(y, own);
-    }
-    __syncthreads();
-    const double add = __dadd_rn(__dsub_rn(x, run), s_warp[warp]);
-    for (int i = lo; i < hi; ++i) a[i] = __dadd_rn(a[i], add);
-    __syncthreads();
+    c.L = a.L + b.L;
+    return c;
 }
-
-// Exclusive scan of n int counts (global memory) by a whole block: every thread
-// takes a contiguous chunk; visit(t, prefix, count) is called for every entry in
-// order within the chunk. Returns the total (to every thread).
-template <int BLOCK, typename F>
-__device__ long long block_chunk_scan(const int* __restrict__ cnt, long long n, long long* s_w, F&& visit) {
+__device__ __forceinline__ ISeg iseg_shfl_up(const ISeg& x, int o) {
+    ISeg y;
+    for (int sp = 0; sp < 2; ++sp) {
+        y.r[sp] = __shfl_up_sync(FULL, x.r[sp], o);
+        const unsigned long long lo = __shfl_up_sync(FULL, (unsigned long long)x.s[sp], o);
+        const long long hi = __shfl_up_sync(FULL, (long long)(x.s[sp] >> 64), o);
+        y.s[sp] = ((__int128)hi << 64) | (__int128)lo;
+    }
+    y.L = __shfl_up_sync(FULL, x.L, o);
+    return y;
+}
+// Exclusive block scan of one ISeg per thread (s_w: 32 entries).
+template <int BLOCK>
+__device__ ISeg block_exclusive_iseg(const ISeg& own, ISeg* s_w) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = BLOCK / 32;
-    const long long per = (n + BLOCK - 1) / BLOCK;
-    const long long lo = tid * per, hi = min(n, lo + per);
-    long long run = 0;
-    for (long long t = lo; t < hi; ++t) run += cnt[t];
-    long long x = run;
+    ISeg x = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
+        const ISeg y = iseg_shfl_up(x, o);
+        if (lane >= o) x = iseg_join(y, x);
     }
+    ISeg e = iseg_shfl_up(x, 1);
+    if (lane == 0) e = ISeg{};
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        const long long own = lane < NW ? s_w[lane] : 0;
-        long long y = own;
+        ISeg w = lane < NW ? s_w[lane] : ISeg{};
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long z = __shfl_up_sync(FULL, y, o);
-            if (lane >= o) y += z;
+            const ISeg y = iseg_shfl_up(w, o);
+            if (lane >= o) w = iseg_join(y, w);
         }
-        if (lane < NW) s_w[lane] = y - own;
-        if (lane == NW - 1) s_w[32] = y;
+        ISeg p = iseg_shfl_up(w, 1);
+        if (lane == 0) p = ISeg{};
+        if (lane < NW) s_w[lane] = p;
     }
     __syncthreads();
-    long long ex = s_w[warp] + x - run;
-    for (long long t = lo; t < hi; ++t) {
-        const int c = cnt[t];
-        visit(t, ex, c);
-        ex += c;
-    }
-    const long long total = s_w[32];
+    const ISeg r = iseg_join(s_w[warp], e);
     __syncthreads();
-    return total;
+    return r;
+}
+// Nearest double of a 128-bit integer below 2^115 in magnitude (two roundings at most).
+__device__ __forceinline__ double i128_to_double(__int128 x) {
+    const long long hi = (long long)(x >> 64);
+    const unsigned long long lo = (unsigned long long)x;
+    return __fma_rn((double)hi, 0x1p64, __ull2double_rn(lo));
 }
 
 // mode bits: 1 append births and update counts; 2 accumulate moments and
@@ -865,71 +834,58 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
                                                    int out_buf, int mode) {
     constexpr int BLOCK = 1024;
     extern __shared__ __align__(16) double s_f[];
-    __shared__ double s_warp[32];
-    __shared__ long long s_n[2][3];
-    __shared__ long long s_lscan[33];
+    __shared__ ISeg s_iseg[32];
     __shared__ int s_err;
-    const int d = blockIdx.x, tid = threadIdx.x, role = blockIdx.y;
+    const int d = blockIdx.x, tid = threadIdx.x, role = blockIdx.y, lane = tid & 31, warp = tid >> 5;
     const Disc& D = discs[d];
     const int N = D.N;
     if (tid == 0) s_err = 0;
     __syncthreads();
 
-    // role 1, 2: the new segment table and births of store role-1; role 0: the field
-    if ((mode & 1) && role > 0) {
-        // New segment tables from the sweep's per-tile counts: store sp's segments are its own
-        // tiles' regions (slot order), then one segment of the births of sp that the other
-        // species' tiles produced, compacted here into the births region.
-        using R = typename Rec<T>::type;
+    // role 1: store totals and the output offsets of every slice of sweep chunks (the per-chunk
+    // segment entries and the newborn copies follow in k_seg_apply); role 0: the field
+    if ((mode & 1) && role == 1 && warp == 0) {
         const int TILE = D.tile, CHUNK = D.chunk;
-        if (tid == 0) {  // input chunks: every warp chunk of every tile of the last sweep
-            for (int sp = 0; sp < 2; ++sp) s_n[sp][0] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
+        long long chunks[2], slices[2];
+        for (int sp = 0; sp < 2; ++sp) {
+            chunks[sp] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
+            slices[sp] = (chunks[sp] + SLICE - 1) / SLICE;
         }
-        __syncthreads();
-        {
-            const int sp = role - 1;
-            const long long chunks = s_n[sp][0];
-            int* st = D.seg_start[sp];
-            int* sr = D.seg_src[sp];
-            const long long main_total = block_chunk_scan<BLOCK>(D.cnt_main[sp], chunks, s_lscan,
-                [&](long long t, long long ex, int c) {
-                    st[t] = (int)ex;
-                    sr[t] = (int)(t * CHUNK);
-                });
-            // newborns, appended after the survivors in parent-slot order: for electrons the
-            // ionization electrons, then the SEE electrons of the ion sweep; for ions the
-            // ionization ions
-            int32_t* cdst = D.c[out_buf][sp];
-            R* pdst = reinterpret_cast<R*>(D.p[out_buf][sp]);
-            const long long R0 = D.R0[sp], bcap = D.bcap;
-            long long nb = 0;
-            for (int src = 0; src < (sp == 0 ? 2 : 1); ++src) {
-                const bool same = sp == 0 && src == 0;
-                const int par = same ? 0 : 1 - sp;  // species whose sweep made them
-                const int32_t* csrc = same ? D.sc : D.bc[par];
-                const R* psrc = reinterpret_cast<const R*>(same ? D.sp_ : D.bp[par]);
-                const int* cnt = same ? D.cnt_same : D.cnt_birth[par];
-                const long long base = nb;
-                nb += block_chunk_scan<BLOCK>(cnt, s_n[par][0], s_lscan,
-                    [&](long long t, long long ex, int c) {
-                        for (int k = 0; k < c; ++k) {
-                            const long long o = base + ex + k;
-                            if (o < bcap) {
-                                cdst[R0 + o] = csrc[t * CHUNK + k];
-                                pdst[R0 + o] = psrc[t * CHUNK + k];
-                            } else {
-                                s_err = ERR_CAPACITY;
-                            }
-                        }
-                    });
+        // exclusive warp scan of slice sums (column q of sweep sp) into slice_pre, plus base
+        auto scan = [&](int sp, int q, long long base) -> long long {
+            long long carry = base;
+            for (long long k0 = 0; k0 < slices[sp]; k0 += 32) {
+                const long long k = k0 + lane;
+                const long long v = k < slices[sp] ? (long long)D.slice_tot[sp][3 * k + q] : 0;
+                long long x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (k < slices[sp]) D.slice_pre[sp][3 * k + q] = (unsigned)(carry + x - v);
+                carry += __shfl_sync(FULL, x, 31);
             }
+            return carry - base;
+        };
+        const long long main0 = scan(0, 0, 0), main1 = scan(1, 0, 0);
+        const long long same0 = scan(0, 2, 0);           // ionization electrons, first in store 0's newborns
+        const long long see = scan(1, 1, same0);          // SEE electrons, after them
+        const long long ions = scan(0, 1, 0);             // ionization ions, store 1's newborns
+        for (int sp = 0; sp < 2; ++sp) {
+            const long long main_total = sp == 0 ? main0 : main1;
+            const long long nb = sp == 0 ? same0 + see : ions;
+            const long long bcap = D.bcap;
             const long long nbk = nb < bcap ? nb : bcap;
-            const int nseg = (int)chunks + (nbk > 0 ? 1 : 0);
+            const long long ch = chunks[sp];
+            const int nseg = (int)ch + (nbk > 0 ? 1 : 0);
             long long n_new = main_total + nbk;
-            if (tid == 0) {
+            int* st = D.seg_start[sp];
+            if (lane == 0) {
+                if (nb > bcap) s_err = ERR_CAPACITY;
                 if (nbk > 0) {
-                    st[chunks] = (int)main_total;
-                    sr[chunks] = (int)R0;
+                    st[ch] = (int)main_total;
+                    D.seg_src[sp][ch] = (int)D.R0[sp];
                 }
                 st[nseg] = (int)n_new;
                 if (n_new > D.cap[sp]) {
@@ -948,17 +904,11 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
                     }
                 }
             }
-            __syncthreads();
-            // first segment of every chunk of the next sweep: the segment holding slot j CHUNK
+            n_new = __shfl_sync(FULL, n_new, 0);
+            // the newborn segment's share of first_seg
             const long long jmax = (long long)D.max_tiles[sp] * D.warps;
-            for (int k = tid; k < nseg; k += BLOCK) {
-                const long long s0 = st[k], s1 = st[k + 1];
-                if (s1 > s0) {
-                    const long long j1 = (s1 + CHUNK - 1) / CHUNK;
-                    for (long long j = (s0 + CHUNK - 1) / CHUNK; j < j1 && j <= jmax; ++j) D.first_seg[sp][j] = k;
-                }
-            }
-            __syncthreads();
+            for (long long j = (main_total + CHUNK - 1) / CHUNK + lane; j * CHUNK < n_new && j <= jmax; j += 32)
+                D.first_seg[sp][j] = (int)ch;
         }
     }
 
@@ -979,59 +929,75 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
 
     // Poisson, Eq. (poisson): phi_{j-1} - 2 phi_j + phi_{j+1} = -r_j, r_j = rho_j dx^2 / eps0,
     // phi_0 = V_rf sin(2 pi f t), phi_N = 0. With R_j = sum_{k<=j} r_k and S_j = sum_{i<j} R_i:
-    // phi_j = phi_0 + j g_1 - S_j, g_1 = (phi_N - phi_0 + S_N) / N.
-    double* a = s_f;               // N+1
-    double* rho = s_f + (MAXN + 1);
-    const double dx = D.dx;
+    // phi_j = phi_0 + j g_1 - S_j, g_1 = (phi_N - phi_0 + S_N) / N. FP64 latency is long on this
+    // part, so the dependent chain is kept short: one scan of (R, S) pairs, no division.
+    double* Rr = s_f + (MAXN + 1);      // R_j
+    double* Sx = s_f + 2 * (MAXN + 1);  // S_{j+1}
     const long long step = ctl->step;
-    const double t = (mode & 4) ? (double)step * D.dt : (double)(step + 1) * D.dt;
-    const double V0 = D.V_rf * sin(2.0 * PI_D * D.f_rf * t);
-    for (int j = tid; j <= N; j += BLOCK) {
-        const double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
-        rho[j] = E_CHARGE * (D.w[1] * (double)D.D[1][j] - D.w[0] * (double)D.D[0][j]) / (TWO32_D * Vj);
-        a[j] = (j >= 1 && j <= N - 1) ? rho[j] * dx * dx / EPS0 : 0.0;
-    }
-    __syncthreads();
-    block_scan_inclusive<BLOCK>(a, N, s_warp);  // a[j] = R_j, j = 0..N-1
-    double* Rr = rho + (MAXN + 1);              // keep R for the field (third shared array)
-    for (int j = tid; j < N; j += BLOCK) Rr[j] = a[j];
-    __syncthreads();
-    // exclusive scan of R into S: S_j = sum_{i<j} R_i, j = 0..N
-    double* Sx = a;  // reuse: shift by one
+    const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
+    const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
+                              : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
+    // R and S are linear in the deposits: R_j = c_i IR_i,j - c_e IR_e,j and S_{j+1} = c_i IS_i,j -
+    // c_e IS_e,j with the exact integer sums IR_s,j = sum_{1<=k<=j} D_s,k (64 bits: a store holds
+    // below 2^30 particles of 2^32 each) and IS_s,j = sum_{i<=j} IR_s,i (128 bits). The scans are
+    // integer; FP64 (slow on this part) is used once per node.
     {
-        // a[j] holds R_j (j < N); build S in place: S_0 = 0, S_{j+1} = S_j + R_j
-        block_scan_inclusive<BLOCK>(a, N, s_warp);  // a[j] = sum_{i<=j} R_i = S_{j+1}
+        const int per = (N + BLOCK - 1) / BLOCK;
+        const int lo = min(N, tid * per), hi = min(N, lo + per);
+        long long dv[2][4];
+        ISeg own{};
+        for (int i = 0; i < 4; ++i)
+            if (i < hi - lo) {
+                const int j = lo + i;
+                for (int sp = 0; sp < 2; ++sp) {
+                    dv[sp][i] = j >= 1 ? (long long)D.D[sp][j] : 0;
+                    own.r[sp] += dv[sp][i];
+                    own.s[sp] += own.r[sp];
+                }
+            }
+        own.L = hi - lo;
+        const ISeg pre = block_exclusive_iseg<BLOCK>(own, s_iseg);
+        ISeg run = pre;
+        for (int i = 0; i < 4; ++i)
+            if (i < hi - lo) {
+                const int j = lo + i;
+                for (int sp = 0; sp < 2; ++sp) {
+                    run.r[sp] += dv[sp][i];
+                    run.s[sp] += run.r[sp];
+                }
+                Rr[j] = __fma_rn(D.pc_r[1], (double)run.r[1], -D.pc_r[0] * (double)run.r[0]);
+                Sx[j] = __fma_rn(D.pc_r[1], i128_to_double(run.s[1]), -D.pc_r[0] * i128_to_double(run.s[0]));
+            }
+        __syncthreads();
     }
-    __syncthreads();
     const double SN = N > 0 ? Sx[N - 1] : 0.0;
-    const double g1 = (0.0 - V0 + SN) / (double)N;
+    const double g1 = (SN - V0) * D.inv_N;
     // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
     // (the central difference of phi, without the cancellation of large phi values), and Gauss's
     // law over the half cells at the electrodes.
     double* phi = D.phi;
     for (int j = tid; j <= N; j += BLOCK) {
-        const double Sj = j == 0 ? 0.0 : Sx[j - 1];
-        double ph = V0 + (double)j * g1 - Sj;
+        double ph = V0 + (double)j * g1 - (j == 0 ? 0.0 : Sx[j - 1]);
         if (j == N) ph = 0.0;
         if (j == 0) ph = V0;
         phi[j] = ph;
-    }
-    __syncthreads();
-    for (int j = tid; j <= N; j += BLOCK) {
         double E;
-        if (j == 0) E = -g1 / dx - rho[0] * dx / (2.0 * EPS0);
-        else if (j == N) E = -(g1 - Rr[N - 1]) / dx + rho[N] * dx / (2.0 * EPS0);
-        else E = -((g1 - Rr[j - 1]) + (g1 - Rr[j])) / (2.0 * dx);
+        if (j == 0 || j == N) {
+            const double rw = __fma_rn(D.pc_w[1], (double)D.D[1][j], -D.pc_w[0] * (double)D.D[0][j]);
+            E = j == 0 ? -g1 * D.inv_dx - rw * D.hdx_eps : -(g1 - Rr[N - 1]) * D.inv_dx + rw * D.hdx_eps;
+        } else {
+            E = ((g1 - Rr[j - 1]) + (g1 - Rr[j])) * D.m_inv_2dx;
+        }
         D.E64[j] = E;
         reinterpret_cast<T*>(D.E)[j] = (T)E;
         if (j == 0) ctl->E0_last[d] = E;
     }
     if (mode & 2) {
         for (int j = tid; j <= N; j += BLOCK) {
-            D.acc_D[0][j] += (double)D.D[0][j];
-            D.acc_D[1][j] += (double)D.D[1][j];
-            D.acc_Q[j] += (double)D.Q[j];
-            D.acc_Dprev[j] += (double)D.Dprev[j];
+            D.acc_D[0][j] += D.D[0][j];
+            D.acc_D[1][j] += D.D[1][j];
+            D.acc_Q[j] += D.Q[j];
+            D.acc_Dprev[j] += D.Dprev[j];
         }
         if (tid == 0) ctl->acc_steps[d] += 1;
     }
@@ -1054,6 +1020,112 @@ __global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ disc
             }
         }
     }
+}
+
+// Segment entries of one slice of SLICE chunks of sweep sp (after k_finalize):
+// seg_start/seg_src of its chunks and first_seg of the slots they hold, the copy
+// of their newborns into the newborn regions, and the slice sums cleared for
+// the next sweep.
+__global__ void __launch_bounds__(1024) k_seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
+                                                    int out_buf) {
+    constexpr int BLOCK = 1024, K = SLICE / BLOCK, NW = BLOCK / 32;
+    __shared__ int s_w[3][NW];
+    const int st_ = blockIdx.y, d = st_ >> 1, sp = st_ & 1;
+    const Disc& D = discs[d];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int TILE = D.tile, CHUNK = D.chunk;
+    const long long chunks = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
+    const long long t0 = (long long)blockIdx.x * SLICE;
+    if (t0 >= chunks) return;
+    const long long tb = t0 + (long long)tid * K;
+    int cm[K], cb[K], cs[K];
+    int rm = 0, rb = 0, rs = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const bool in = tb + i < chunks;
+        cm[i] = in ? D.cnt_main[sp][tb + i] : 0;
+        cb[i] = in ? D.cnt_birth[sp][tb + i] : 0;
+        cs[i] = (in && sp == 0) ? D.cnt_same[tb + i] : 0;
+        rm += cm[i];
+        rb += cb[i];
+        rs += cs[i];
+    }
+    int xm = rm, xb = rb, xs = rs;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ym = __shfl_up_sync(FULL, xm, o), yb = __shfl_up_sync(FULL, xb, o), ys = __shfl_up_sync(FULL, xs, o);
+        if (lane >= o) {
+            xm += ym;
+            xb += yb;
+            xs += ys;
+        }
+    }
+    if (lane == 31) {
+        s_w[0][warp] = xm;
+        s_w[1][warp] = xb;
+        s_w[2][warp] = xs;
+    }
+    __syncthreads();
+    if (warp < 3) {
+        const int v = s_w[warp][lane];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        s_w[warp][lane] = x - v;
+    }
+    __syncthreads();
+    const unsigned* pre = D.slice_pre[sp] + 3 * blockIdx.x;
+    long long em = (long long)pre[0] + s_w[0][warp] + xm - rm;
+    long long eb = (long long)pre[1] + s_w[1][warp] + xb - rb;
+    long long es = (long long)pre[2] + s_w[2][warp] + xs - rs;
+    using R = float4;
+    int* st = D.seg_start[sp];
+    int* sr = D.seg_src[sp];
+    int* fs = D.first_seg[sp];
+    const long long jmax = (long long)D.max_tiles[sp] * D.warps;
+    const int q = 1 - sp;  // store of the other-species newborns
+    const long long bcap = D.bcap;
+    const int rw = D.rec_words;  // record size in 16-byte words
+    int err = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const long long t = tb + i;
+        if (t < chunks) {
+            st[t] = (int)em;
+            sr[t] = (int)(t * CHUNK);
+            for (long long j = (em + CHUNK - 1) / CHUNK; j * CHUNK < em + cm[i] && j <= jmax; ++j) fs[j] = (int)t;
+            for (int k = 0; k < cb[i]; ++k) {
+                const long long o = eb + k;
+                if (o < bcap) {
+                    D.c[out_buf][q][D.R0[q] + o] = D.bc[sp][t * CHUNK + k];
+                    const R* src = reinterpret_cast<const R*>(D.bp[sp]) + (t * CHUNK + k) * rw;
+                    R* dst = reinterpret_cast<R*>(D.p[out_buf][q]) + (D.R0[q] + o) * rw;
+                    for (int w = 0; w < rw; ++w) dst[w] = src[w];
+                } else {
+                    err = ERR_CAPACITY;
+                }
+            }
+            for (int k = 0; k < cs[i]; ++k) {
+                const long long o = es + k;
+                if (o < bcap) {
+                    D.c[out_buf][0][D.R0[0] + o] = D.sc[t * CHUNK + k];
+                    const R* src = reinterpret_cast<const R*>(D.sp_) + (t * CHUNK + k) * rw;
+                    R* dst = reinterpret_cast<R*>(D.p[out_buf][0]) + (D.R0[0] + o) * rw;
+                    for (int w = 0; w < rw; ++w) dst[w] = src[w];
+                } else {
+                    err = ERR_CAPACITY;
+                }
+            }
+        }
+        em += cm[i];
+        eb += cb[i];
+        es += cs[i];
+    }
+    if (err) atomicOr(&ctl->error, err);
+    if (tid < 3) D.slice_tot[sp][3 * blockIdx.x + tid] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1215,87 +1287,86 @@ __global__ void k_tables(int n_pts, int n_proc, double de, double M, const doubl
 // Stable counting sort by cell. Tiles of SORT_TILE particles; inside a tile
 // warp w owns a contiguous run of SORT_R x 32 particles in input order.
 constexpr int SORT_BLOCK = 256, SORT_NW = SORT_BLOCK / 32, SORT_R = 16, SORT_TILE = SORT_BLOCK * SORT_R;
+constexpr int SORT_WARP = 32 * SORT_R;  // consecutive slots of one warp in a sort tile
 
-// Per tile: count of each cell -> hist[seg][c * T_s + t]. Input read through
-// the store's segment table.
+// Stable counting sort of every store by cell, in three passes over tiles of
+// SORT_TILE slots (warp w of tile t owns slots t SORT_TILE + w SORT_WARP ...):
+// per-tile cell counts (hist[seg][t N + c]); per cell an exclusive scan over the
+// tiles plus the cell starts; the scatter, where each warp places its slots in
+// order (rank among equal cells by match_any). Input through the store's
+// segment table, output dense.
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                            int buf, unsigned* __restrict__ hist,
                                                            const long long* __restrict__ hoff) {
     extern __shared__ __align__(16) unsigned s_c[];
-    __shared__ SegWin W;
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
-    const long long n = ctl->count[d][sp];
+    const unsigned n = (unsigned)ctl->count[d][sp];
     const int nseg = ctl->nseg[d][sp];
-    const long long Ts = (n + SORT_TILE - 1) / SORT_TILE;
-    const int32_t* cc = D.c[buf][sp];
+    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
+    const int32_t* __restrict__ cc = D.c[buf][sp];
     unsigned* H = hist + hoff[seg];
-    const int lane = threadIdx.x & 31;
-    const int per_chunk = SORT_TILE / D.chunk;
-    for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (unsigned t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = threadIdx.x; j < N; j += SORT_BLOCK) s_c[j] = 0;
-        if (threadIdx.x < 32)
-            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_chunk],
-                            lane);
         __syncthreads();
-        for (int i = threadIdx.x; i < SORT_TILE; i += SORT_BLOCK) {
-            const long long k = t * SORT_TILE + i;
-            const int key = k < n ? cc[seg_offset(W, D.seg_start[sp], D.seg_src[sp], nseg, k)] : N;
-            const unsigned peers = __match_any_sync(FULL, key);
-            if ((unsigned)key < (unsigned)N && lane == __ffs(peers) - 1) atomicAdd(&s_c[key], (unsigned)__popc(peers));
+        const unsigned wbase = t * SORT_TILE + warp * SORT_WARP;
+        if (wbase < n) {
+            SegCursor cur;
+            cur.init(D.seg_start[sp], D.seg_src[sp], D.first_seg[sp], nseg, wbase, D.chunk, lane);
+            int key[SORT_R];
+#pragma unroll
+            for (int r = 0; r < SORT_R; ++r) {  // all loads first
+                const unsigned s0 = wbase + 32 * r, slot = s0 + lane;
+                key[r] = N;
+                if (s0 < n) {
+                    const unsigned off = cur.offset(s0, slot);
+                    if (slot < n) key[r] = __ldcs(cc + off);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < SORT_R; ++r) {
+                const unsigned peers = __match_any_sync(FULL, key[r]);
+                if ((unsigned)key[r] < (unsigned)N && lane == __ffs(peers) - 1)
+                    atomicAdd(&s_c[key[r]], (unsigned)__popc(peers));
+            }
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < N; j += SORT_BLOCK) H[(long long)j * Ts + t] = s_c[j];
+        for (int j = threadIdx.x; j < N; j += SORT_BLOCK) H[(size_t)t * N + j] = s_c[j];
         __syncthreads();
     }
 }
 
-// Per (store, cell) row: exclusive scan over the tiles in place; row total out.
+// Per (store, group of 32 cells): exclusive scan over the tiles in place (lane = cell, each warp
+// a contiguous range of tiles, so rows are read 128 bytes at a time); row totals out.
 __global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                     unsigned* __restrict__ hist, const long long* __restrict__ hoff,
                                                     unsigned* __restrict__ tot) {
+    __shared__ unsigned s_sum[32][33];
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const int N = discs[d].N;
-    const int c = blockIdx.x;
-    if (c >= N) return;
-    const long long n = ctl->count[d][sp];
-    const long long Ts = (n + SORT_TILE - 1) / SORT_TILE;
-    unsigned* row = hist + hoff[seg] + (long long)c * Ts;
-    __shared__ unsigned s_w[32];
-    __shared__ unsigned s_carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= N) return;
+    const unsigned n = (unsigned)ctl->count[d][sp];
+    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
+    unsigned* H = hist + hoff[seg];
+    const unsigned per = (Ts + 31) / 32, t0 = min(Ts, warp * per), t1 = min(Ts, t0 + per);
+    unsigned sum = 0;
+    if (c < N)
+        for (unsigned t = t0; t < t1; ++t) sum += H[(size_t)t * N + c];
+    s_sum[warp][lane] = sum;
     __syncthreads();
-    for (long long b0 = 0; b0 < Ts; b0 += 1024) {
-        const long long i = b0 + tid;
-        const unsigned own = i < Ts ? row[i] : 0u;
-        unsigned x = own;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned t = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += t;
+    unsigned pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_sum[w][lane];
+    if (warp == 31 && c < N) tot[(long long)seg * MAXN + c] = pre + sum;
+    if (c < N)
+        for (unsigned t = t0; t < t1; ++t) {
+            const unsigned v = H[(size_t)t * N + c];
+            H[(size_t)t * N + c] = pre;
+            pre += v;
         }
-        if (lane == 31) s_w[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            const unsigned w = s_w[lane];
-            unsigned y = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned t = __shfl_up_sync(FULL, y, o);
-                if (lane >= o) y += t;
-            }
-            s_w[lane] = y - w;
-        }
-        __syncthreads();
-        const unsigned carry = s_carry;
-        if (i < Ts) row[i] = carry + s_w[warp] + x - own;
-        __syncthreads();
-        if (tid == 1023) s_carry = carry + s_w[warp] + x;
-        __syncthreads();
-    }
-    if (tid == 0) tot[(long long)seg * MAXN + c] = s_carry;
 }
 
 // Per store: exclusive scan of the row totals -> first slot of every cell.
@@ -1338,9 +1409,6 @@ __global__ void __launch_bounds__(1024) k_sort_cells(const Disc* __restrict__ di
     }
 }
 
-// Scatter: per-warp counts, prefix over warps, then each warp places its run
-// in order (rank among equal cells by match_any). Input through the segment
-// table; output dense.
 template <typename T>
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restrict__ discs,
                                                              const Ctl* __restrict__ ctl, int src, int dst,
@@ -1348,41 +1416,57 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
                                                              const long long* __restrict__ hoff,
                                                              const unsigned* __restrict__ tot, int max_N) {
     extern __shared__ __align__(16) unsigned s_w[];  // [SORT_NW][max_N]
-    __shared__ SegWin W;
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
-    const long long n = ctl->count[d][sp];
+    const unsigned n = (unsigned)ctl->count[d][sp];
     const int nseg = ctl->nseg[d][sp];
-    const long long Ts = (n + SORT_TILE - 1) / SORT_TILE;
-    const int32_t* cs = D.c[src][sp];
-    int32_t* cd = D.c[dst][sp];
+    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
+    const int32_t* __restrict__ cs = D.c[src][sp];
+    int32_t* __restrict__ cd = D.c[dst][sp];
     using R = typename Rec<T>::type;
-    const R* ps = reinterpret_cast<const R*>(D.p[src][sp]);
-    R* pd = reinterpret_cast<R*>(D.p[dst][sp]);
+    const R* __restrict__ ps = reinterpret_cast<const R*>(D.p[src][sp]);
+    R* __restrict__ pd = reinterpret_cast<R*>(D.p[dst][sp]);
     const unsigned* H = hist + hoff[seg];
     const unsigned* cstart = tot + (long long)seg * MAXN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     unsigned* Wc = s_w + warp * max_N;
-    const int per_chunk = SORT_TILE / D.chunk;
-    for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
+    for (unsigned t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = tid; j < SORT_NW * max_N; j += SORT_BLOCK) s_w[j] = 0;
-        if (warp == 0)
-            seg_window_load(W, D.seg_start[sp], D.seg_src[sp], nseg, nseg <= 1 ? 0 : D.first_seg[sp][t * per_chunk],
-                            lane);
         __syncthreads();
-        const long long wbase = t * SORT_TILE + (long long)warp * (SORT_R * 32);
-        for (int r = 0; r < SORT_R; ++r) {
-            const long long k = wbase + r * 32 + lane;
-            const int key = k < n ? cs[seg_offset(W, D.seg_start[sp], D.seg_src[sp], nseg, k)] : N;
+        const unsigned wbase = t * SORT_TILE + warp * SORT_WARP;
+        uint32_t kr[SORT_R];  // cell | rank among the warp's equal cells so far << 16
+        unsigned off[SORT_R];
+        SegCursor cur;
+        if (wbase < n) cur.init(D.seg_start[sp], D.seg_src[sp], D.first_seg[sp], nseg, wbase, D.chunk, lane);
+#pragma unroll
+        for (int r = 0; r < SORT_R; ++r) {  // all cell loads first
+            const unsigned s0 = wbase + 32 * r, slot = s0 + lane;
+            int key = N;
+            off[r] = 0;
+            if (s0 < n) {
+                off[r] = cur.offset(s0, slot);
+                if (slot < n) key = __ldcs(cs + off[r]);
+            }
+            kr[r] = (uint32_t)key;
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_R; ++r) {  // rank of each slot among the warp's equal cells
+            const int key = (int)kr[r];
             const unsigned peers = __match_any_sync(FULL, key);
-            if ((unsigned)key < (unsigned)N && lane == __ffs(peers) - 1) Wc[key] += __popc(peers);
+            if ((unsigned)key < (unsigned)N) {
+                const unsigned b = Wc[key];
+                kr[r] |= (b + __popc(peers & lt)) << 16;
+                __syncwarp(peers);
+                if (lane == __ffs(peers) - 1) Wc[key] = b + __popc(peers);
+            }
             __syncwarp();
         }
         __syncthreads();
+        // per cell: its first output slot for each warp of the tile
         for (int j = tid; j < N; j += SORT_BLOCK) {
-            unsigned run = 0;
+            unsigned run = cstart[j] + H[(size_t)t * N + j];
 #pragma unroll
             for (int w = 0; w < SORT_NW; ++w) {
                 const unsigned v = s_w[w * max_N + j];
@@ -1391,26 +1475,16 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
             }
         }
         __syncthreads();
+#pragma unroll
         for (int r = 0; r < SORT_R; ++r) {
-            const long long k = wbase + r * 32 + lane;
-            long long off = 0;
-            int key = N;
-            if (k < n) {
-                off = seg_offset(W, D.seg_start[sp], D.seg_src[sp], nseg, k);
-                key = cs[off];
-            }
-            const unsigned peers = __match_any_sync(FULL, key);
-            const unsigned b = (unsigned)key < (unsigned)N ? Wc[key] : 0u;
-            __syncwarp();
-            if ((unsigned)key < (unsigned)N) {
-                const long long o = (long long)cstart[key] + H[(long long)key * Ts + t] + b + __popc(peers & lt);
+            const int k = (int)(kr[r] & 0xFFFFu);
+            if ((unsigned)k < (unsigned)N) {
+                const unsigned o = Wc[k] + (kr[r] >> 16);
                 if (o < n) {
-                    cd[o] = key;
-                    pd[o] = ps[off];
+                    cd[o] = k;
+                    pd[o] = ps[off[r]];
                 }
-                if (lane == __ffs(peers) - 1) Wc[key] = b + __popc(peers);
             }
-            __syncwarp();
         }
         __syncthreads();
     }
@@ -1532,7 +1606,7 @@ int sweep_occupancy(int fp64, int block, int ppt, int max_N) {
     return fp64 ? occ_p<double>(block, ppt, max_N) : occ_p<float>(block, ppt, max_N);
 }
 
-cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode,
+cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, int max_slices,
                             cudaStream_t st) {
     const size_t smem = sizeof(double) * 3 * (MAXN + 1);
     if (fp64) {
@@ -1542,6 +1616,9 @@ cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, i
         smem_attr(k_finalize<float>, smem);
         k_finalize<float><<<dim3(n_disc, 3), 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !(mode & 1)) return e;
+    k_seg_apply<<<dim3(max_slices > 0 ? max_slices : 1, 2 * n_disc), 1024, 0, st>>>(discs, ctl, out_buf);
     return cudaGetLastError();
 }
 
@@ -1617,7 +1694,7 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
     k_sort_count<<<g, SORT_BLOCK, sizeof(unsigned) * max_N, st>>>(discs, ctl, src, hist, hoff);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sort_rows<<<dim3(max_N, 2 * n_disc), 1024, 0, st>>>(discs, ctl, hist, hoff, tot);
+    k_sort_rows<<<dim3((max_N + 31) / 32, 2 * n_disc), 1024, 0, st>>>(discs, ctl, hist, hoff, tot);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sort_cells<<<2 * n_disc, 1024, 0, st>>>(discs, tot);
