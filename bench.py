@@ -54,15 +54,15 @@ def sweep_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(prec: str):
+def recorded_traffic(prec: str, kernel: str):
     """DRAM bytes per particle-step of the sweep from the committed ncu summary, if it was taken on
-    the current kernel source."""
+    the current kernel source and the same launch shape."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
     e = j.get(prec)
-    if not e or e.get("source_hash") != sweep_source_hash():
+    if not e or e.get("source_hash") != sweep_source_hash() or e.get("kernel") != kernel:
         return None
     return e
 
@@ -300,7 +300,7 @@ def run_gpu(args, rank: int, world: int):
     bytes_per_launch = BYTES_PER_PS["fp32"] * launch_ps
     avg_sweep_s = main["sweep_ms"] * 1e-3 / max(1, main["sweep_launches"])
     achieved = bytes_per_launch / avg_sweep_s / 1e9
-    tr = recorded_traffic("fp32")
+    tr = recorded_traffic("fp32", "k_sweep<float,%d,%d>" % (args.block, args.ppt))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tr["dram_bytes_per_particle"] * launch_ps) if tr else None,
                 "kernel": "k_sweep<float,%d,%d>" % (args.block, args.ppt),
