@@ -113,6 +113,19 @@ PROTOTYPES = {
     "pic_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp]),
     "pic_period_counts": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
     "pic_load_profiles": (C.c_int, [_vp, _i32, _vp]),
+    # include/mlp.h
+    "mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _vp, _i32, _u64, _vp]),
+    "mlp_param_count": (_i64, [_vp]),
+    "mlp_set_params": (C.c_int, [_vp, _vp]),
+    "mlp_get_params": (C.c_int, [_vp, _vp]),
+    "mlp_forward": (C.c_int, [_vp, _i32, _vp, _vp]),
+    "mlp_loss_grad": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "mlp_get_grads": (C.c_int, [_vp, _vp]),
+    "mlp_adam": (C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "mlp_train_step": (C.c_int, [_vp, _i32, _vp, _vp, C.c_float, _vp]),
+    "mlp_sync": (C.c_int, [_vp]),
+    "mlp_destroy": (None, [_vp]),
+    "mlp_last_error": (C.c_char_p, [_vp]),
 }
 
 _lib = None

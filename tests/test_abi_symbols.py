@@ -9,15 +9,19 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "pic.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", txt)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b((?:pic|mlp)_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = _declared()
     for must in ("pic_create", "pic_batch_create", "pic_step", "pic_moments", "pic_destroy", "pic_sweep",
-                 "pic_solve", "pic_sort", "pic_sync"):
+                 "pic_solve", "pic_sort", "pic_sync", "mlp_create", "mlp_forward", "mlp_loss_grad", "mlp_adam"):
         assert must in names
 
 
