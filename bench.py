@@ -290,6 +290,11 @@ def run_gpu(args, rank: int, world: int):
     fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
     e2e = measure_e2e("fp32", max(3, min(10, args.steps)), sort_every)
     batch = measure_batch(max(4, args.steps // 2), 3, sort_every) if not args.no_batch else None
+    warm = None
+    if args.warm_start and world == 1:
+        # rf periods to the steady state from the homogeneous start vs from the network's profiles
+        from paper_1608_04601_gb300 import warmstart
+        warm = warmstart.experiment(n_train=args.ws_train, n_test=args.ws_test)
 
     # aggregate over ranks: the job took as long as its slowest rank, and did every rank's work
     total_ms, ps = reduce_over_ranks(main["total_ms"], main["ps"], world, "cuda")
@@ -324,6 +329,8 @@ def run_gpu(args, rank: int, world: int):
            "e2e": e2e, "clocks": main["clocks"], "gpu_launches": main["gpu_launches"]}
     if batch:
         res["batch_c4"] = batch
+    if warm:
+        res["warm_start"] = warm
     return res
 
 
@@ -359,6 +366,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
+                    help="skip the warm-start experiment (training runs, network training, cold vs warm runs)")
+    ap.add_argument("--ws-train", type=int, default=64, help="training discharges of the warm-start experiment")
+    ap.add_argument("--ws-test", type=int, default=8, help="held-out discharges of the warm-start experiment")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use --block/--ppt/--sort-every as given instead of searching")
     args = ap.parse_args()
