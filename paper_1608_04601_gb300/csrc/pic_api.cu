@@ -52,6 +52,8 @@ struct pic_ctx {
     bool deposits_zero = true;
     int sweep_grid = 0, num_sms = 0;
     int max_slices = 0;  // slices of sweep chunks of the largest store
+    void* stage = nullptr;  // device staging of state transfers
+    size_t stage_bytes = 0;
     std::string err;
     pic_counters cnt_at_reset[MAXD];
     bool timing = false;
@@ -188,6 +190,7 @@ extern "C" void pic_destroy(pic_ctx* ctx) {
         cudaEventDestroy(e.second);
     }
     for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -696,6 +699,20 @@ extern "C" pic_status pic_get_count(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     return PIC_OK;
 }
 
+// Device staging for state transfers (cells, then four real arrays), grown on demand.
+static pic_status staging(pic_ctx* ctx, long long n) {
+    const size_t r = ctx->fp64 ? 8 : 4;
+    const size_t need = (((size_t)n * 4 + 15) / 16) * 16 + (size_t)n * 4 * r + 64;  // cells, reals, error word
+    if (ctx->stage_bytes >= need) return PIC_OK;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    CK(cudaMalloc(&ctx->stage, need), "staging");
+    ctx->stage_bytes = need;
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t cap, int32_t* c, void* f,
                                     void* vx, void* vy, void* vz, int64_t* n_out) {
     int64_t n = 0;
@@ -703,33 +720,21 @@ extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     if (s != PIC_OK) return s;
     if (n_out) *n_out = n;
     if (n > cap) return fail(ctx, PIC_ERR_ARG, "host buffer too small");
-    const Disc& D = ctx->hd[d];
-    int nseg = 0;
-    CK(cudaMemcpy(&nseg, &ctx->d_ctl->nseg[d][sp], sizeof(int), cudaMemcpyDeviceToHost), "segments");
-    std::vector<int> st(nseg + 1), sr(nseg > 0 ? nseg : 1);
-    if (nseg > 0) {
-        CK(cudaMemcpy(st.data(), D.seg_start[sp], sizeof(int) * (nseg + 1), cudaMemcpyDeviceToHost), "segments");
-        CK(cudaMemcpy(sr.data(), D.seg_src[sp], sizeof(int) * nseg, cudaMemcpyDeviceToHost), "segments");
-    }
-    long long span = 0;  // buffer records that hold the store
-    for (int k = 0; k < nseg; ++k)
-        if (st[k + 1] > st[k]) span = std::max(span, (long long)sr[k] + (st[k + 1] - st[k]));
+    if (n == 0) return PIC_OK;
+    s = staging(ctx, n);
+    if (s != PIC_OK) return s;
     const size_t r = ctx->fp64 ? 8 : 4;
-    std::vector<int32_t> cb((size_t)span + 1);
-    std::vector<unsigned char> buf(4 * r * ((size_t)span + 1));
-    if (span) {
-        CK(cudaMemcpy(cb.data(), D.c[ctx->cur][sp], sizeof(int32_t) * span, cudaMemcpyDeviceToHost), "state c");
-        CK(cudaMemcpy(buf.data(), D.p[ctx->cur][sp], 4 * r * span, cudaMemcpyDeviceToHost), "state p");
-    }
+    int32_t* sc = static_cast<int32_t*>(ctx->stage);
+    unsigned char* sv = static_cast<unsigned char*>(ctx->stage) + (((size_t)n * 4 + 15) / 16) * 16;
+    const int grid = std::max(1, std::min(ctx->num_sms * 8, (int)((n + 255) / 256)));
+    CK(launch_unpack_state(ctx->fp64, ctx->d_discs, ctx->d_ctl, d, sp, ctx->cur, n, sc, sv, grid, ctx->stream),
+       "state gather");
+    if (c) CK(cudaMemcpyAsync(c, sc, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream), "state c");
     void* outs[4] = {f, vx, vy, vz};
-    for (int k = 0; k < nseg; ++k) {
-        for (long long i = st[k]; i < st[k + 1] && i < n; ++i) {
-            const long long o = sr[k] + (i - st[k]);
-            if (c) c[i] = cb[o];
-            for (int q = 0; q < 4; ++q)
-                if (outs[q]) std::memcpy((unsigned char*)outs[q] + r * i, buf.data() + r * (4 * o + q), r);
-        }
-    }
+    for (int q = 0; q < 4; ++q)
+        if (outs[q]) CK(cudaMemcpyAsync(outs[q], sv + (size_t)q * n * r, r * (size_t)n, cudaMemcpyDeviceToHost,
+                                        ctx->stream), "state p");
+    CK(cudaStreamSynchronize(ctx->stream), "state copy");
     return PIC_OK;
 }
 
@@ -738,25 +743,34 @@ extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     if (bad_d(ctx, d) || (sp & ~1) || n < 0 || (n && (!c || !f || !vx || !vy || !vz))) return PIC_ERR_ARG;
     const Disc& D = ctx->hd[d];
     if (n > D.cap[sp]) return fail(ctx, PIC_ERR_CAPACITY, "state larger than capacity");
-    for (int64_t i = 0; i < n; ++i)
-        if (c[i] < 0 || c[i] >= D.N) return fail(ctx, PIC_ERR_ARG, "cell index out of range");
-    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     const size_t r = ctx->fp64 ? 8 : 4;
-    std::vector<unsigned char> buf(4 * r * (size_t)n);
-    const void* ins[4] = {f, vx, vy, vz};
-    for (int k = 0; k < 4; ++k)
-        for (int64_t i = 0; i < n; ++i) std::memcpy(buf.data() + r * (4 * i + k), (const unsigned char*)ins[k] + r * i, r);
+    pic_status s = staging(ctx, n > 0 ? n : 1);
+    if (s != PIC_OK) return s;
+    int32_t* sc = static_cast<int32_t*>(ctx->stage);
+    unsigned char* sv = static_cast<unsigned char*>(ctx->stage) + (((size_t)n * 4 + 15) / 16) * 16;
+    unsigned* bad = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ctx->stage) + ctx->stage_bytes - 64);
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), ctx->stream), "state check");
     if (n) {
-        CK(cudaMemcpy(D.c[ctx->cur][sp], c, sizeof(int32_t) * n, cudaMemcpyHostToDevice), "state c");
-        CK(cudaMemcpy(D.p[ctx->cur][sp], buf.data(), 4 * r * n, cudaMemcpyHostToDevice), "state p");
+        CK(cudaMemcpyAsync(sc, c, 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream), "state c");
+        const void* ins[4] = {f, vx, vy, vz};
+        for (int q = 0; q < 4; ++q)
+            CK(cudaMemcpyAsync(sv + (size_t)q * n * r, ins[q], r * (size_t)n, cudaMemcpyHostToDevice, ctx->stream),
+               "state p");
+        const int grid = std::max(1, std::min(ctx->num_sms * 8, (int)((n + 255) / 256)));
+        CK(launch_pack_state(ctx->fp64, ctx->d_discs, d, sp, ctx->cur, n, sc, sv, bad, grid, ctx->stream),
+           "state pack");
     }
-    long long v = n;
+    unsigned nbad = 0;
+    CK(cudaMemcpyAsync(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream), "state check");
+    CK(cudaStreamSynchronize(ctx->stream), "state copy");
+    long long v = nbad ? 0 : n;  // a rejected upload leaves an empty store
     CK(cudaMemcpy(&ctx->d_ctl->count[d][sp], &v, 8, cudaMemcpyHostToDevice), "count");
-    const int seg[2] = {0, (int)n}, zero = 0, one = 1;
+    const int seg[2] = {0, (int)v}, zero = 0, one = 1;
     CK(cudaMemcpy(D.seg_start[sp], seg, sizeof(seg), cudaMemcpyHostToDevice), "segments");
     CK(cudaMemcpy(D.seg_src[sp], &zero, sizeof(int), cudaMemcpyHostToDevice), "segments");
     CK(cudaMemcpy(D.first_seg[sp], &zero, sizeof(int), cudaMemcpyHostToDevice), "segments");
     CK(cudaMemcpy(&ctx->d_ctl->nseg[d][sp], &one, sizeof(int), cudaMemcpyHostToDevice), "segments");
+    if (nbad) return fail(ctx, PIC_ERR_ARG, "cell index out of range");
     return PIC_OK;
 }
 

@@ -1490,6 +1490,47 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
     }
 }
 
+// State upload: SoA staging (cells, then f, vx, vy, vz arrays of n reals) ->
+// the store's records; cells outside [0, N) are counted in *bad.
+template <typename T>
+__global__ void k_pack_state(const Disc* __restrict__ discs, int d, int sp, int buf, long long n,
+                             const int32_t* __restrict__ c, const T* __restrict__ sv, unsigned* __restrict__ bad) {
+    const Disc& D = discs[d];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = c[i];
+        if ((unsigned)ci >= (unsigned)D.N) atomicAdd(bad, 1u);
+        store_rec<T>(D.c[buf][sp], D.p[buf][sp], (unsigned)i,
+                     Part<T>{ci, sv[i], sv[n + i], sv[2 * n + i], sv[3 * n + i]});
+    }
+}
+
+// State download: the store, read through its segment table (binary search per
+// slot), -> SoA staging.
+template <typename T>
+__global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl, int d, int sp, int buf,
+                               long long n, int32_t* __restrict__ c, T* __restrict__ sv) {
+    const Disc& D = discs[d];
+    const int nseg = ctl->nseg[d][sp];
+    const int* st = D.seg_start[sp];
+    const int* sr = D.seg_src[sp];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nseg - 1;  // last segment with start <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((long long)st[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const unsigned o = (unsigned)sr[lo] + (unsigned)(i - st[lo]);
+        T f, vx, vy, vz;
+        load_rec<T>(D.p[buf][sp], o, f, vx, vy, vz);
+        c[i] = D.c[buf][sp][o];
+        sv[i] = f;
+        sv[n + i] = vx;
+        sv[2 * n + i] = vy;
+        sv[3 * n + i] = vz;
+    }
+}
+
 // Every store becomes one dense segment [0, count) (after a load, an upload or a sort).
 __global__ void k_set_dense(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl) {
     const int i = threadIdx.x;
@@ -1708,6 +1749,20 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
         smem_attr(k_sort_scatter<float>, smem);
         k_sort_scatter<float><<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, dst, hist, hoff, tot, max_N);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
+                              const void* sv, unsigned* bad, int grid, cudaStream_t st) {
+    if (fp64) k_pack_state<double><<<grid, 256, 0, st>>>(discs, d, sp, buf, n, c, (const double*)sv, bad);
+    else k_pack_state<float><<<grid, 256, 0, st>>>(discs, d, sp, buf, n, c, (const float*)sv, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long n,
+                                int32_t* c, void* sv, int grid, cudaStream_t st) {
+    if (fp64) k_unpack_state<double><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (double*)sv);
+    else k_unpack_state<float><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (float*)sv);
     return cudaGetLastError();
 }
 

@@ -139,13 +139,21 @@ class Simulation:
         self._ck(self.L.pic_get_count(self.h, d, species, C.byref(v)))
         return v.value
 
-    def get_state(self, d: int, species: int) -> dict:
+    def get_state(self, d: int, species: int, out: dict = None) -> dict:
+        """The store of (d, species) as host arrays; `out` may hold preallocated arrays (keys c, f,
+        vx, vy, vz, e.g. in pinned memory) of at least the store's size, which are then filled."""
         n = self.count(d, species)
-        c = np.zeros(max(n, 1), np.int32)
-        arrs = [np.zeros(max(n, 1), self.dtype) for _ in range(4)]
+        if out is not None:
+            c = out["c"]
+            arrs = [out[k] for k in ("f", "vx", "vy", "vz")]
+            assert c.dtype == np.int32 and all(a.dtype == self.dtype for a in arrs)
+            cap = min(c.size, *[a.size for a in arrs])
+        else:
+            c = np.zeros(max(n, 1), np.int32)
+            arrs = [np.zeros(max(n, 1), self.dtype) for _ in range(4)]
+            cap = max(n, 1)
         got = C.c_int64()
-        self._ck(self.L.pic_get_state(self.h, d, species, max(n, 1), _ptr(c), *[_ptr(a) for a in arrs],
-                                      C.byref(got)))
+        self._ck(self.L.pic_get_state(self.h, d, species, cap, _ptr(c), *[_ptr(a) for a in arrs], C.byref(got)))
         n = got.value
         return {"c": c[:n], "f": arrs[0][:n], "vx": arrs[1][:n], "vy": arrs[2][:n], "vz": arrs[3][:n]}
 

@@ -404,3 +404,27 @@ def test_warm_load_matches_oracle(P, prec):
             s2.load_profiles(np.stack([ne, ni, eps]))
         finally:
             s2.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_state_upload_round_trip_and_rejects_bad_cells(P, prec):
+    """pic_set_state / pic_get_state move the exact values (device-side interleave and gather);
+    a cell outside [0, N) is reported and leaves the store empty."""
+    rng = np.random.default_rng(21)
+    d = I.discharge(n_cells=64, n_e0=10, n_i0=10)
+    gas = X.he_like(eps_max_eV=200.0, de_eV=1e-2)
+    sim = P.Simulation(gas, d, precision=prec, load=False, capacity=[(5000, 5000)])
+    dt = np.float32 if prec == "fp32" else np.float64
+    st = I.maxwell_state(rng, 3001, 64, 1e5, dt)
+    sim.set_state(0, 0, st)
+    back = sim.get_state(0, 0)
+    for k in ("c", "f", "vx", "vy", "vz"):
+        assert np.array_equal(back[k], st[k])
+    bad = dict(st)
+    bad["c"] = st["c"].copy()
+    bad["c"][1234] = 64
+    with pytest.raises(RuntimeError):
+        sim.set_state(0, 1, bad)
+    assert sim.count(0, 1) == 0
+    sim.close()
