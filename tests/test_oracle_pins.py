@@ -432,7 +432,7 @@ def test_ionization_shares_remaining_energy_equally():
     assert out["c"].size == 2 * n
     e0 = 0.5 * I.M_E * (st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2) / I.E_CH
     e = 0.5 * I.M_E * (out["vx"] ** 2 + out["vy"] ** 2 + out["vz"] ** 2) / I.E_CH
-    e1, e2 = e[0::2], e[1::2]     # parent, then its secondary
+    e1, e2 = e[:n], e[n:]         # survivors in input order, then the secondaries in parent order
     assert np.max(np.abs(e1 + e2 - (e0 - eiz))) < 1e-11 * np.max(e0)
     assert np.max(np.abs(e1 - e2)) < 1e-11 * np.max(e0)
     ions = o.get_state(1)
