@@ -195,7 +195,7 @@ extern "C" void pic_destroy(pic_ctx* ctx) {
     delete ctx;
 }
 
-static pic_status enqueue_sweep(pic_ctx* ctx);
+static pic_status enqueue_sweep(pic_ctx* ctx, int full_step);
 static pic_status enqueue_finalize(pic_ctx* ctx, int mode);
 static pic_status enqueue_sort(pic_ctx* ctx);
 
@@ -490,7 +490,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ce = launch_load(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, seed, gx, ctx->stream);
         if (ce == cudaSuccess) ce = launch_deposit(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, ctx->max_N, gx,
                                                    ctx->stream);
-        if (ce == cudaSuccess) ce = launch_finalize(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, 4, 0, ctx->stream);
+        if (ce == cudaSuccess) ce = launch_finalize(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, 4, 0, ctx->max_N, ctx->stream);
         if (ce == cudaSuccess) ce = launch_backkick(ctx->fp64, ctx->d_discs, n_dis, ctx->d_ctl, 0, gx, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
         if (ce != cudaSuccess) {
@@ -525,7 +525,7 @@ extern "C" pic_status pic_create(pic_ctx** out, const pic_gas* gas, double gap_m
 }
 
 // ---------------------------------------------------------------------------
-static pic_status enqueue_sweep(pic_ctx* ctx) {
+static pic_status enqueue_sweep(pic_ctx* ctx, int full_step) {
     if (!ctx->deposits_zero) {
         for (auto& D : ctx->hd) {
             const size_t b = 8 * ((size_t)D.N + 1);
@@ -559,13 +559,14 @@ static pic_status enqueue_sweep(pic_ctx* ctx) {
     }
     CK(launch_sweep(L), "sweep launch");
     if (evp) cudaEventRecord(evp->second, ctx->stream);
+    CK(launch_totals(ctx->d_discs, ctx->n_disc, ctx->d_ctl, full_step, ctx->stream), "totals launch");
     ctx->deposits_zero = false;
     return PIC_OK;
 }
 
 static pic_status enqueue_finalize(pic_ctx* ctx, int mode) {
     CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, mode & 1 ? 1 - ctx->cur : ctx->cur, mode,
-                       ctx->max_slices, ctx->stream),
+                       ctx->max_slices, ctx->max_N, ctx->stream),
        "finalize launch");
     if (mode & 1) ctx->cur = 1 - ctx->cur;
     if (mode & 2) ctx->step += 1;
@@ -586,7 +587,7 @@ static pic_status enqueue_sort(pic_ctx* ctx) {
 // Sweep + births + solve: the sweep reads buffer cur and writes 1-cur; the
 // finalize appends births into 1-cur; cur flips.
 static pic_status enqueue_step(pic_ctx* ctx) {
-    pic_status s = enqueue_sweep(ctx);
+    pic_status s = enqueue_sweep(ctx, 1);
     if (s != PIC_OK) return s;
     s = enqueue_finalize(ctx, 3);
     if (s != PIC_OK) return s;
@@ -656,11 +657,11 @@ extern "C" pic_status pic_step(pic_ctx* ctx, int64_t n_steps) {
 
 extern "C" pic_status pic_sweep(pic_ctx* ctx) {
     if (!ctx) return PIC_ERR_ARG;
-    pic_status s = enqueue_sweep(ctx);
+    pic_status s = enqueue_sweep(ctx, 0);
     if (s != PIC_OK) return s;
     // births appended and counts updated; no solve, no step advance
     CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, 1 - ctx->cur, 1 | 8, ctx->max_slices,
-                       ctx->stream),
+                       ctx->max_N, ctx->stream),
        "append launch");
     ctx->cur = 1 - ctx->cur;
     return PIC_OK;
@@ -1081,7 +1082,7 @@ extern "C" pic_status pic_load_profiles(pic_ctx* ctx, int32_t n_pts, const doubl
         e = launch_load_profile(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->seed, ddesc, gx, ctx->stream);
     if (e == cudaSuccess) e = launch_set_dense(ctx->d_discs, nd, ctx->d_ctl, ctx->stream);
     if (e == cudaSuccess) e = launch_deposit(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->max_N, gx, ctx->stream);
-    if (e == cudaSuccess) e = launch_finalize(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, 4, 0, ctx->stream);
+    if (e == cudaSuccess) e = launch_finalize(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, 4, 0, ctx->max_N, ctx->stream);
     if (e == cudaSuccess) e = launch_backkick(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, gx, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(dtab);

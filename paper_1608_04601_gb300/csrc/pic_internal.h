@@ -114,6 +114,7 @@ struct Ctl {
     int error;                // ERR_* bits
     long long count[MAXD][2]; // superparticles per store
     long long count_in[MAXD][2]; // the counts the last sweep read (its tiles)
+    long long see_base[MAXD];    // offset of the SEE electrons among store 0's newborns (after the ionization electrons)
     int nseg[MAXD][2];        // segments per store
     long long acc_steps[MAXD];
     double E0_last[MAXD];

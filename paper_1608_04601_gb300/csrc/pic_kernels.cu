@@ -1,21 +1,22 @@
 // pic_kernels.cu -- CUDA kernels (sm_103a) of the 1d3v PIC/MCC time step of
 // arXiv:1608.04601, section "PIC/MCC simulation procedure".
 //
-// One time step is two launches (and the sort every K steps):
-//   k_sweep     persistent; every CTA takes tiles of particles in increasing
-//               order from a global dispenser. Per particle: CIC gather of E_n
-//               (node field held in shared memory), half kick, null-collision
-//               MCC on Philox streams, half kick, drift, wall test. A block
-//               scan orders each tile's outputs (particles in slot order, each
-//               followed by its same-species newborn), written into the tile's
-//               own region of the output buffer; no tile waits for another.
-//               CIC deposit into a shared-memory int64 histogram, flushed
-//               with global atomics.
-//   k_finalize  one CTA per discharge: the new segment tables (an exclusive
-//               scan of the per-tile output counts), births of the other
-//               species compacted behind them, Poisson (Eq. poisson, rf
-//               Dirichlet boundary) in FP64 by two block scans, node field,
-//               cycle-average accumulators.
+// One time step is three launches (and the sort every K steps):
+//   k_sweep     persistent; tiles of BLOCK x PPT slots of all stores in a
+//               static grid-stride order; each warp owns a chunk of 32 PPT
+//               slots and loads, pushes (CIC gather of E_n from shared
+//               memory, half kick, null-collision MCC on Philox streams, half
+//               kick, drift, walls), collides and writes its survivors in slot
+//               order into the chunk's own output region, newborns into the
+//               chunk's newborn regions, with no barrier inside a tile. CIC
+//               deposits go to warp-aggregated shared-memory int64 histograms,
+//               flushed with global atomics. Chunk counts are summed per slice.
+//   k_totals    one warp per discharge: slice sums -> output offsets, new store
+//               counts.
+//   k_post      per slice of chunks: the segment table entries and the newborn
+//               copies; per discharge, concurrently: Poisson (Eq. poisson, rf
+//               Dirichlet boundary) from exact integer prefix sums of the
+//               deposits, node field, cycle-average accumulators.
 //   sort        every K steps: stable counting sort of each store by cell
 //               into a dense store.
 #include "pic_internal.h"
@@ -418,6 +419,98 @@ __device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, doub
     f = a.x; vx = a.y; vy = b.x; vz = b.y;
 }
 
+// Store totals after a sweep, for discharge d, by one warp (k_totals): the
+// output offsets of every slice of sweep chunks (slice_pre),
+// the new counts and segment counts, the newborn segment and its first_seg
+// entries; on a full step also the per-period mean counts. The per-chunk
+// segment entries and the newborn copies follow in k_post.
+__device__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, bool full_step, int& err) {
+    const int TILE = D.tile, CHUNK = D.chunk;
+    long long chunks[2], slices[2];
+    for (int sp = 0; sp < 2; ++sp) {
+        chunks[sp] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
+        slices[sp] = (chunks[sp] + SLICE - 1) / SLICE;
+    }
+    // exclusive warp scans of the five slice-sum columns (survivors of both sweeps, ionization
+    // electrons and ions of the electron sweep, SEE electrons of the ion sweep) into slice_pre,
+    // 32 slices a round, all loads of a round issued first. The SEE electrons' offsets are
+    // relative: k_post adds see_base, the count of ionization electrons that precede them.
+    long long main0 = 0, main1 = 0, same0 = 0, see = 0, ions = 0;
+    const long long rounds = (max(slices[0], slices[1]) + 31) / 32;
+    for (long long r = 0; r < rounds; ++r) {
+        const long long k = r * 32 + lane;
+        const bool e = k < slices[0], i = k < slices[1];
+        long long v[5] = {e ? (long long)__ldcg(&D.slice_tot[0][3 * k + 0]) : 0,
+                          i ? (long long)__ldcg(&D.slice_tot[1][3 * k + 0]) : 0,
+                          e ? (long long)__ldcg(&D.slice_tot[0][3 * k + 2]) : 0,
+                          i ? (long long)__ldcg(&D.slice_tot[1][3 * k + 1]) : 0,
+                          e ? (long long)__ldcg(&D.slice_tot[0][3 * k + 1]) : 0};
+        long long x[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            x[q] = v[q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(FULL, x[q], o);
+                if (lane >= o) x[q] += y;
+            }
+        }
+        if (e) {
+            D.slice_pre[0][3 * k + 0] = (unsigned)(main0 + x[0] - v[0]);
+            D.slice_pre[0][3 * k + 2] = (unsigned)(same0 + x[2] - v[2]);
+            D.slice_pre[0][3 * k + 1] = (unsigned)(ions + x[4] - v[4]);
+        }
+        if (i) {
+            D.slice_pre[1][3 * k + 0] = (unsigned)(main1 + x[1] - v[1]);
+            D.slice_pre[1][3 * k + 1] = (unsigned)(see + x[3] - v[3]);
+        }
+        main0 += __shfl_sync(FULL, x[0], 31);
+        main1 += __shfl_sync(FULL, x[1], 31);
+        same0 += __shfl_sync(FULL, x[2], 31);
+        see += __shfl_sync(FULL, x[3], 31);
+        ions += __shfl_sync(FULL, x[4], 31);
+    }
+    if (lane == 0) ctl->see_base[d] = same0;
+    for (int sp = 0; sp < 2; ++sp) {
+        const long long main_total = sp == 0 ? main0 : main1;
+        const long long nb = sp == 0 ? same0 + see : ions;
+        const long long bcap = D.bcap;
+        const long long nbk = nb < bcap ? nb : bcap;
+        const long long ch = chunks[sp];
+        const int nseg = (int)ch + (nbk > 0 ? 1 : 0);
+        long long n_new = main_total + nbk;
+        int* st = D.seg_start[sp];
+        if (lane == 0) {
+            if (nb > bcap) err |= ERR_CAPACITY;
+            if (nbk > 0) {
+                st[ch] = (int)main_total;
+                D.seg_src[sp][ch] = (int)D.R0[sp];
+            }
+            st[nseg] = (int)n_new;
+            if (n_new > D.cap[sp]) {
+                err |= ERR_CAPACITY;
+                n_new = D.cap[sp];
+            }
+            ctl->count[d][sp] = n_new;
+            ctl->nseg[d][sp] = nseg;
+            if (full_step) {  // per-period mean counts (steady-state criterion)
+                const long long n_step = ctl->step;  // this step is n; the counts belong to n+1
+                ctl->period_acc[d][sp] += (double)n_new;
+                if (D.steps_per_period > 0 && (n_step + 1) % D.steps_per_period == 0) {
+                    const long long per = (n_step + 1) / D.steps_per_period - 1;
+                    D.period_mean[(per % PERIOD_HIST) * 2 + sp] = ctl->period_acc[d][sp] / D.steps_per_period;
+                    ctl->period_acc[d][sp] = 0.0;
+                }
+            }
+        }
+        n_new = __shfl_sync(FULL, n_new, 0);
+        // the newborn segment's share of first_seg
+        const long long jmax = (long long)D.max_tiles[sp] * D.warps;
+        for (long long j = (main_total + CHUNK - 1) / CHUNK + lane; j * CHUNK < n_new && j <= jmax; j += 32)
+            D.first_seg[sp][j] = (int)ch;
+    }
+}
+
 // Dynamic shared memory of the sweep: histogram and energy moment (u64, N+1
 // each), the node field (T, N+1), then per warp its candidate queue (one entry
 // per slot of its chunk) and its newborn scratch (a pair per lane).
@@ -759,6 +852,14 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     }
 }
 
+// Store totals of every discharge after a sweep, one warp per discharge.
+__global__ void k_totals(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl, int full_step) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int err = 0;
+    for (int d = warp; d < n_disc; d += nw) store_totals(discs[d], d, ctl, lane, full_step != 0, err);
+    if (err) atomicOr(&ctl->error, err);
+}
+
 // ---------------------------------------------------------------------------
 // Integer prefix segment of the Poisson sums for both species: r = sum of
 // deposits, s = sum of the running r, L = elements. Segment A followed by B:
@@ -826,213 +927,21 @@ __device__ __forceinline__ double i128_to_double(__int128 x) {
     return __fma_rn((double)hi, 0x1p64, __ull2double_rn(lo));
 }
 
-// mode bits: 1 append births and update counts; 2 accumulate moments and
-// advance the step; 4 initial solve at t = n dt (load); 8 births only (no
-// solve, deposits kept).
-template <typename T>
-__global__ void __launch_bounds__(1024) k_finalize(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
-                                                   int out_buf, int mode) {
-    constexpr int BLOCK = 1024;
-    extern __shared__ __align__(16) double s_f[];
-    __shared__ ISeg s_iseg[32];
-    __shared__ int s_err;
-    const int d = blockIdx.x, tid = threadIdx.x, role = blockIdx.y, lane = tid & 31, warp = tid >> 5;
-    const Disc& D = discs[d];
-    const int N = D.N;
-    if (tid == 0) s_err = 0;
-    __syncthreads();
-
-    // role 1: store totals and the output offsets of every slice of sweep chunks (the per-chunk
-    // segment entries and the newborn copies follow in k_seg_apply); role 0: the field
-    if ((mode & 1) && role == 1 && warp == 0) {
-        const int TILE = D.tile, CHUNK = D.chunk;
-        long long chunks[2], slices[2];
-        for (int sp = 0; sp < 2; ++sp) {
-            chunks[sp] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
-            slices[sp] = (chunks[sp] + SLICE - 1) / SLICE;
-        }
-        // exclusive warp scan of slice sums (column q of sweep sp) into slice_pre, plus base
-        auto scan = [&](int sp, int q, long long base) -> long long {
-            long long carry = base;
-            for (long long k0 = 0; k0 < slices[sp]; k0 += 32) {
-                const long long k = k0 + lane;
-                const long long v = k < slices[sp] ? (long long)D.slice_tot[sp][3 * k + q] : 0;
-                long long x = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const long long y = __shfl_up_sync(FULL, x, o);
-                    if (lane >= o) x += y;
-                }
-                if (k < slices[sp]) D.slice_pre[sp][3 * k + q] = (unsigned)(carry + x - v);
-                carry += __shfl_sync(FULL, x, 31);
-            }
-            return carry - base;
-        };
-        const long long main0 = scan(0, 0, 0), main1 = scan(1, 0, 0);
-        const long long same0 = scan(0, 2, 0);           // ionization electrons, first in store 0's newborns
-        const long long see = scan(1, 1, same0);          // SEE electrons, after them
-        const long long ions = scan(0, 1, 0);             // ionization ions, store 1's newborns
-        for (int sp = 0; sp < 2; ++sp) {
-            const long long main_total = sp == 0 ? main0 : main1;
-            const long long nb = sp == 0 ? same0 + see : ions;
-            const long long bcap = D.bcap;
-            const long long nbk = nb < bcap ? nb : bcap;
-            const long long ch = chunks[sp];
-            const int nseg = (int)ch + (nbk > 0 ? 1 : 0);
-            long long n_new = main_total + nbk;
-            int* st = D.seg_start[sp];
-            if (lane == 0) {
-                if (nb > bcap) s_err = ERR_CAPACITY;
-                if (nbk > 0) {
-                    st[ch] = (int)main_total;
-                    D.seg_src[sp][ch] = (int)D.R0[sp];
-                }
-                st[nseg] = (int)n_new;
-                if (n_new > D.cap[sp]) {
-                    s_err = ERR_CAPACITY;
-                    n_new = D.cap[sp];
-                }
-                ctl->count[d][sp] = n_new;
-                ctl->nseg[d][sp] = nseg;
-                if (mode & 2) {  // per-period mean counts (steady-state criterion)
-                    const long long n_step = ctl->step;  // this step is n; the counts belong to n+1
-                    ctl->period_acc[d][sp] += (double)n_new;
-                    if (D.steps_per_period > 0 && (n_step + 1) % D.steps_per_period == 0) {
-                        const long long per = (n_step + 1) / D.steps_per_period - 1;
-                        D.period_mean[(per % PERIOD_HIST) * 2 + sp] = ctl->period_acc[d][sp] / D.steps_per_period;
-                        ctl->period_acc[d][sp] = 0.0;
-                    }
-                }
-            }
-            n_new = __shfl_sync(FULL, n_new, 0);
-            // the newborn segment's share of first_seg
-            const long long jmax = (long long)D.max_tiles[sp] * D.warps;
-            for (long long j = (main_total + CHUNK - 1) / CHUNK + lane; j * CHUNK < n_new && j <= jmax; j += 32)
-                D.first_seg[sp][j] = (int)ch;
-        }
-    }
-
-    if (role > 0 || (mode & 8)) {
-        __syncthreads();
-        if (tid == 0 && s_err) atomicOr(&ctl->error, s_err);
-        if (tid == 0 && (mode & 2)) {
-            __threadfence();
-            const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
-            if (prev == gridDim.x * gridDim.y - 1) {
-                ctl->fin_done = 0;
-                ctl->step = ctl->step + 1;
-                __threadfence();
-            }
-        }
-        return;
-    }
-
-    // Poisson, Eq. (poisson): phi_{j-1} - 2 phi_j + phi_{j+1} = -r_j, r_j = rho_j dx^2 / eps0,
-    // phi_0 = V_rf sin(2 pi f t), phi_N = 0. With R_j = sum_{k<=j} r_k and S_j = sum_{i<j} R_i:
-    // phi_j = phi_0 + j g_1 - S_j, g_1 = (phi_N - phi_0 + S_N) / N. FP64 latency is long on this
-    // part, so the dependent chain is kept short: one scan of (R, S) pairs, no division.
-    double* Rr = s_f + (MAXN + 1);      // R_j
-    double* Sx = s_f + 2 * (MAXN + 1);  // S_{j+1}
-    const long long step = ctl->step;
-    const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
-    const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
-                              : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
-    // R and S are linear in the deposits: R_j = c_i IR_i,j - c_e IR_e,j and S_{j+1} = c_i IS_i,j -
-    // c_e IS_e,j with the exact integer sums IR_s,j = sum_{1<=k<=j} D_s,k (64 bits: a store holds
-    // below 2^30 particles of 2^32 each) and IS_s,j = sum_{i<=j} IR_s,i (128 bits). The scans are
-    // integer; FP64 (slow on this part) is used once per node.
-    {
-        const int per = (N + BLOCK - 1) / BLOCK;
-        const int lo = min(N, tid * per), hi = min(N, lo + per);
-        long long dv[2][4];
-        ISeg own{};
-        for (int i = 0; i < 4; ++i)
-            if (i < hi - lo) {
-                const int j = lo + i;
-                for (int sp = 0; sp < 2; ++sp) {
-                    dv[sp][i] = j >= 1 ? (long long)D.D[sp][j] : 0;
-                    own.r[sp] += dv[sp][i];
-                    own.s[sp] += own.r[sp];
-                }
-            }
-        own.L = hi - lo;
-        const ISeg pre = block_exclusive_iseg<BLOCK>(own, s_iseg);
-        ISeg run = pre;
-        for (int i = 0; i < 4; ++i)
-            if (i < hi - lo) {
-                const int j = lo + i;
-                for (int sp = 0; sp < 2; ++sp) {
-                    run.r[sp] += dv[sp][i];
-                    run.s[sp] += run.r[sp];
-                }
-                Rr[j] = __fma_rn(D.pc_r[1], (double)run.r[1], -D.pc_r[0] * (double)run.r[0]);
-                Sx[j] = __fma_rn(D.pc_r[1], i128_to_double(run.s[1]), -D.pc_r[0] * i128_to_double(run.s[0]));
-            }
-        __syncthreads();
-    }
-    const double SN = N > 0 ? Sx[N - 1] : 0.0;
-    const double g1 = (SN - V0) * D.inv_N;
-    // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
-    // (the central difference of phi, without the cancellation of large phi values), and Gauss's
-    // law over the half cells at the electrodes.
-    double* phi = D.phi;
-    for (int j = tid; j <= N; j += BLOCK) {
-        double ph = V0 + (double)j * g1 - (j == 0 ? 0.0 : Sx[j - 1]);
-        if (j == N) ph = 0.0;
-        if (j == 0) ph = V0;
-        phi[j] = ph;
-        double E;
-        if (j == 0 || j == N) {
-            const double rw = __fma_rn(D.pc_w[1], (double)D.D[1][j], -D.pc_w[0] * (double)D.D[0][j]);
-            E = j == 0 ? -g1 * D.inv_dx - rw * D.hdx_eps : -(g1 - Rr[N - 1]) * D.inv_dx + rw * D.hdx_eps;
-        } else {
-            E = ((g1 - Rr[j - 1]) + (g1 - Rr[j])) * D.m_inv_2dx;
-        }
-        D.E64[j] = E;
-        reinterpret_cast<T*>(D.E)[j] = (T)E;
-        if (j == 0) ctl->E0_last[d] = E;
-    }
-    if (mode & 2) {
-        for (int j = tid; j <= N; j += BLOCK) {
-            D.acc_D[0][j] += D.D[0][j];
-            D.acc_D[1][j] += D.D[1][j];
-            D.acc_Q[j] += D.Q[j];
-            D.acc_Dprev[j] += D.Dprev[j];
-        }
-        if (tid == 0) ctl->acc_steps[d] += 1;
-    }
-    for (int j = tid; j <= N; j += BLOCK) {
-        D.Dprev[j] = D.D[0][j];
-        D.D[0][j] = 0;
-        D.D[1][j] = 0;
-        D.Q[j] = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (s_err) atomicOr(&ctl->error, s_err);
-        if (mode & 2) {
-            __threadfence();
-            const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
-            if (prev == gridDim.x * gridDim.y - 1) {
-                ctl->fin_done = 0;
-                ctl->step = step + 1;
-                __threadfence();
-            }
-        }
-    }
-}
-
-// Segment entries of one slice of SLICE chunks of sweep sp (after k_finalize):
-// seg_start/seg_src of its chunks and first_seg of the slots they hold, the copy
-// of their newborns into the newborn regions, and the slice sums cleared for
-// the next sweep.
-__global__ void __launch_bounds__(1024) k_seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
-                                                    int out_buf) {
-    constexpr int BLOCK = 1024, K = SLICE / BLOCK, NW = BLOCK / 32;
+// After a sweep (mode bit 1) and for every solve, one grid (x = slice or the
+// field role, y = store): CTAs x < nsl write the segment entries of slice x of
+// store y (seg_start/seg_src of its chunks, first_seg of the slots they hold),
+// copy its newborns into the newborn regions and clear the slice sums; CTAs
+// x = nsl, y even solve the field of discharge y / 2 and accumulate the moments.
+// mode bits: 1 segments after a sweep; 2 accumulate moments and advance the
+// step; 4 initial solve at t = n dt (load); 8 segments only (no solve,
+// deposits kept). The last CTA to finish advances the step (mode bit 2).
+template <int BLOCK>
+__device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int out_buf, int tid, int lane,
+                          int warp) {
+    constexpr int K = SLICE / BLOCK, NW = BLOCK / 32;
     __shared__ int s_w[3][NW];
-    const int st_ = blockIdx.y, d = st_ >> 1, sp = st_ & 1;
+    const int d = blockIdx.y >> 1, sp = blockIdx.y & 1;
     const Disc& D = discs[d];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int TILE = D.tile, CHUNK = D.chunk;
     const long long chunks = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
     const long long t0 = (long long)blockIdx.x * SLICE;
@@ -1079,7 +988,8 @@ __global__ void __launch_bounds__(1024) k_seg_apply(const Disc* __restrict__ dis
     __syncthreads();
     const unsigned* pre = D.slice_pre[sp] + 3 * blockIdx.x;
     long long em = (long long)pre[0] + s_w[0][warp] + xm - rm;
-    long long eb = (long long)pre[1] + s_w[1][warp] + xb - rb;
+    // other-species newborns: the ion sweep's SEE electrons follow all ionization electrons
+    long long eb = (long long)pre[1] + s_w[1][warp] + xb - rb + (sp == 1 ? ctl->see_base[d] : 0);
     long long es = (long long)pre[2] + s_w[2][warp] + xs - rs;
     using R = float4;
     int* st = D.seg_start[sp];
@@ -1126,6 +1036,118 @@ __global__ void __launch_bounds__(1024) k_seg_apply(const Disc* __restrict__ dis
     }
     if (err) atomicOr(&ctl->error, err);
     if (tid < 3) D.slice_tot[sp][3 * blockIdx.x + tid] = 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_post(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
+                                               int out_buf, int mode, int nsl, int max_N) {
+    constexpr int BLOCK = 1024;
+    extern __shared__ __align__(16) double s_f[];
+    __shared__ ISeg s_iseg[32];
+    __shared__ int s_err;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_err = 0;
+    __syncthreads();
+    if ((int)blockIdx.x < nsl) {
+        seg_apply<BLOCK>(discs, ctl, out_buf, tid, lane, warp);
+    } else if (!(mode & 8) && (blockIdx.y & 1) == 0) {
+        const int d = blockIdx.y >> 1;
+        const Disc& D = discs[d];
+        const int N = D.N;
+        // Poisson, Eq. (poisson): phi_{j-1} - 2 phi_j + phi_{j+1} = -r_j, r_j = rho_j dx^2 / eps0,
+        // phi_0 = V_rf sin(2 pi f t), phi_N = 0. With R_j = sum_{k<=j} r_k and S_j = sum_{i<j} R_i:
+        // phi_j = phi_0 + j g_1 - S_j, g_1 = (phi_N - phi_0 + S_N) / N. FP64 latency is long on this
+        // part, so the dependent chain is kept short: one scan of (R, S) pairs, no division.
+        double* Rr = s_f;                  // R_j
+        double* Sx = s_f + (max_N + 1);    // S_{j+1}
+        const long long step = ctl->step;
+        const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
+        const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
+                                  : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
+        // R and S are linear in the deposits: R_j = c_i IR_i,j - c_e IR_e,j and S_{j+1} = c_i IS_i,j -
+        // c_e IS_e,j with the exact integer sums IR_s,j = sum_{1<=k<=j} D_s,k (64 bits: a store holds
+        // below 2^30 particles of 2^32 each) and IS_s,j = sum_{i<=j} IR_s,i (128 bits). The scans are
+        // integer; FP64 (slow on this part) is used once per node.
+        {
+            const int per = (N + BLOCK - 1) / BLOCK;
+            const int lo = min(N, tid * per), hi = min(N, lo + per);
+            long long dv[2][4];
+            ISeg own{};
+            for (int i = 0; i < 4; ++i)
+                if (i < hi - lo) {
+                    const int j = lo + i;
+                    for (int sp = 0; sp < 2; ++sp) {
+                        dv[sp][i] = j >= 1 ? (long long)D.D[sp][j] : 0;
+                        own.r[sp] += dv[sp][i];
+                        own.s[sp] += own.r[sp];
+                    }
+                }
+            own.L = hi - lo;
+            const ISeg pre = block_exclusive_iseg<BLOCK>(own, s_iseg);
+            ISeg run = pre;
+            for (int i = 0; i < 4; ++i)
+                if (i < hi - lo) {
+                    const int j = lo + i;
+                    for (int sp = 0; sp < 2; ++sp) {
+                        run.r[sp] += dv[sp][i];
+                        run.s[sp] += run.r[sp];
+                    }
+                    Rr[j] = __fma_rn(D.pc_r[1], (double)run.r[1], -D.pc_r[0] * (double)run.r[0]);
+                    Sx[j] = __fma_rn(D.pc_r[1], i128_to_double(run.s[1]), -D.pc_r[0] * i128_to_double(run.s[0]));
+                }
+            __syncthreads();
+        }
+        const double SN = N > 0 ? Sx[N - 1] : 0.0;
+        const double g1 = (SN - V0) * D.inv_N;
+        // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
+        // (the central difference of phi, without the cancellation of large phi values), and Gauss's
+        // law over the half cells at the electrodes.
+        double* phi = D.phi;
+        for (int j = tid; j <= N; j += BLOCK) {
+            double ph = V0 + (double)j * g1 - (j == 0 ? 0.0 : Sx[j - 1]);
+            if (j == N) ph = 0.0;
+            if (j == 0) ph = V0;
+            phi[j] = ph;
+            double E;
+            if (j == 0 || j == N) {
+                const double rw = __fma_rn(D.pc_w[1], (double)D.D[1][j], -D.pc_w[0] * (double)D.D[0][j]);
+                E = j == 0 ? -g1 * D.inv_dx - rw * D.hdx_eps : -(g1 - Rr[N - 1]) * D.inv_dx + rw * D.hdx_eps;
+            } else {
+                E = ((g1 - Rr[j - 1]) + (g1 - Rr[j])) * D.m_inv_2dx;
+            }
+            D.E64[j] = E;
+            reinterpret_cast<T*>(D.E)[j] = (T)E;
+            if (j == 0) ctl->E0_last[d] = E;
+        }
+        if (mode & 2) {
+            for (int j = tid; j <= N; j += BLOCK) {
+                D.acc_D[0][j] += D.D[0][j];
+                D.acc_D[1][j] += D.D[1][j];
+                D.acc_Q[j] += D.Q[j];
+                D.acc_Dprev[j] += D.Dprev[j];
+            }
+            if (tid == 0) ctl->acc_steps[d] += 1;
+        }
+        for (int j = tid; j <= N; j += BLOCK) {
+            D.Dprev[j] = D.D[0][j];
+            D.D[0][j] = 0;
+            D.D[1][j] = 0;
+            D.Q[j] = 0;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (s_err) atomicOr(&ctl->error, s_err);
+        if (mode & 2) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
+            if (prev == gridDim.x * gridDim.y - 1) {
+                ctl->fin_done = 0;
+                ctl->step = ctl->step + 1;
+                __threadfence();
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1648,18 +1670,17 @@ int sweep_occupancy(int fp64, int block, int ppt, int max_N) {
 }
 
 cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, int max_slices,
-                            cudaStream_t st) {
-    const size_t smem = sizeof(double) * 3 * (MAXN + 1);
+                            int max_N, cudaStream_t st) {
+    const size_t smem = sizeof(double) * 2 * ((size_t)max_N + 1);
+    const int nsl = (mode & 1) ? (max_slices > 0 ? max_slices : 1) : 0;
+    const dim3 grid(nsl + 1, 2 * n_disc);
     if (fp64) {
-        smem_attr(k_finalize<double>, smem);
-        k_finalize<double><<<dim3(n_disc, 3), 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
+        smem_attr(k_post<double>, smem);
+        k_post<double><<<grid, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode, nsl, max_N);
     } else {
-        smem_attr(k_finalize<float>, smem);
-        k_finalize<float><<<dim3(n_disc, 3), 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode);
+        smem_attr(k_post<float>, smem);
+        k_post<float><<<grid, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode, nsl, max_N);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !(mode & 1)) return e;
-    k_seg_apply<<<dim3(max_slices > 0 ? max_slices : 1, 2 * n_disc), 1024, 0, st>>>(discs, ctl, out_buf);
     return cudaGetLastError();
 }
 
@@ -1763,6 +1784,11 @@ cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int
                                 int32_t* c, void* sv, int grid, cudaStream_t st) {
     if (fp64) k_unpack_state<double><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (double*)sv);
     else k_unpack_state<float><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (float*)sv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const Disc* discs, int n_disc, Ctl* ctl, int full_step, cudaStream_t st) {
+    k_totals<<<1, 32 * (n_disc < 32 ? n_disc : 32), 0, st>>>(discs, n_disc, ctl, full_step);
     return cudaGetLastError();
 }
 

@@ -13,9 +13,11 @@ struct SweepLaunch {
 };
 
 cudaError_t launch_sweep(const SweepLaunch& L);
+// Store totals after a sweep (slice offsets, new counts), one warp per discharge.
+cudaError_t launch_totals(const Disc* discs, int n_disc, Ctl* ctl, int full_step, cudaStream_t st);
 int sweep_occupancy(int fp64, int block, int ppt, int max_N);
 cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, int max_slices,
-                            cudaStream_t st);
+                            int max_N, cudaStream_t st);
 cudaError_t launch_load(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
                         int grid_x, cudaStream_t st);
 cudaError_t launch_deposit(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int buf, int max_N, int grid_x,
