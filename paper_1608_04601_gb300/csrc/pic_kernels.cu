@@ -255,10 +255,12 @@ __device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, Part<T>* bo
         const T R = mul_((T)u01(r.y), K.kmax_e);
         const int j = (R < C0) ? 0 : (R < C1) ? 1 : (R < C2) ? 2 : (R < C3) ? 3 : 4;
         if (j < 4) {
+            // the scattered electron's direction: the same draw for every process, so it is
+            // formed once, outside the per-process branches
             T nx, ny, nz;
+            iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
             if (j == 0) {  // elastic, target at rest: v' = beta v + (1-beta)|v| n
                 const T g = sqrt_(e2);
-                iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
                 const T og = mul_(K.omb, g);
                 vx = fma_(K.beta, vx, mul_(og, nx));
                 vy = fma_(K.beta, vy, mul_(og, ny));
@@ -268,7 +270,6 @@ __device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, Part<T>* bo
                 const T e2n = sub_(e2, K.de2_exc[j - 1]);
                 if (e2n > (T)0) {
                     const T sp = sqrt_(e2n);
-                    iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
                     vx = mul_(sp, nx);
                     vy = mul_(sp, ny);
                     vz = mul_(sp, nz);
@@ -280,7 +281,6 @@ __device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, Part<T>* bo
                 const T e2r = sub_(e2, K.de2_iz);
                 if (e2r > (T)0) {
                     const T sp = sqrt_(mul_((T)0.5, e2r));
-                    iso_dir(u01(r.z), u01(r.w), nx, ny, nz);
                     vx = mul_(sp, nx);
                     vy = mul_(sp, ny);
                     vz = mul_(sp, nz);
@@ -766,15 +766,9 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     };
 
     for (long long g = blockIdx.x; g < total_tiles; g += gridDim.x) {
-        int seg = 0;
-        {
-            int hi = 2 * n_disc - 1;  // largest store with segstart <= g
-            while (seg < hi) {
-                const int mid = (seg + hi + 1) >> 1;
-                if (s_segstart[mid] <= g) seg = mid;
-                else hi = mid - 1;
-            }
-        }
+        // the store of tile g: the CTA's tiles increase, so its store only moves forward
+        int seg = cur_seg < 0 ? 0 : cur_seg;
+        while (seg + 1 < 2 * n_disc && s_segstart[seg + 1] <= g) ++seg;
         if (seg != cur_seg) {
             if (cur_seg >= 0) flush();
             const int d = seg >> 1, sp = seg & 1;
