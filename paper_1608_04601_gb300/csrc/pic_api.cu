@@ -46,6 +46,9 @@ struct pic_ctx {
     unsigned* sort_hist = nullptr;
     unsigned* sort_tot = nullptr;
     long long* sort_hoff = nullptr;
+    unsigned* sort_kr = nullptr;    // per slot of every store: cell | rank in its sort tile << 16
+    unsigned* sort_off = nullptr;   // per slot of every store: record offset
+    long long* sort_eoff = nullptr; // first slot of each store in sort_kr / sort_off
     std::vector<void*> allocs;
     int cur = 0;
     long long step = 0;
@@ -339,6 +342,18 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ALLOC(ctx->sort_hoff, long long*, sizeof(long long) * 2 * MAXD);
         cudaMemcpyAsync(ctx->sort_hoff, hoff.data(), sizeof(long long) * 2 * MAXD, cudaMemcpyHostToDevice,
                         ctx->stream);
+        std::vector<long long> eoff(2 * MAXD, 0);
+        long long ea = 0;
+        for (int i = 0; i < n_dis; ++i)
+            for (int sp = 0; sp < 2; ++sp) {
+                eoff[2 * i + sp] = ea;
+                ea += sp ? ctx->dis[i].weights.capacity_i : ctx->dis[i].weights.capacity_e;
+            }
+        ALLOC(ctx->sort_kr, unsigned*, sizeof(unsigned) * (size_t)std::max(ea, 1ll));
+        ALLOC(ctx->sort_off, unsigned*, sizeof(unsigned) * (size_t)std::max(ea, 1ll));
+        ALLOC(ctx->sort_eoff, long long*, sizeof(long long) * 2 * MAXD);
+        cudaMemcpyAsync(ctx->sort_eoff, eoff.data(), sizeof(long long) * 2 * MAXD, cudaMemcpyHostToDevice,
+                        ctx->stream);
     }
 
     // per-discharge buffers and descriptors
@@ -577,7 +592,8 @@ static pic_status enqueue_finalize(pic_ctx* ctx, int mode) {
 static pic_status enqueue_sort(pic_ctx* ctx) {
     const int gx = std::max(1, ctx->num_sms * 2);
     CK(launch_sort(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->cur, 1 - ctx->cur, ctx->sort_hist,
-                   ctx->sort_hoff, ctx->sort_tot, ctx->max_N, gx, ctx->stream),
+                   ctx->sort_hoff, ctx->sort_tot, ctx->sort_kr, ctx->sort_off, ctx->sort_eoff, ctx->max_N, gx,
+                   ctx->stream),
        "sort launch");
     CK(launch_set_dense(ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->stream), "sort launch");
     ctx->cur = 1 - ctx->cur;

@@ -1305,16 +1305,23 @@ __global__ void k_tables(int n_pts, int n_proc, double de, double M, const doubl
 constexpr int SORT_BLOCK = 256, SORT_NW = SORT_BLOCK / 32, SORT_R = 16, SORT_TILE = SORT_BLOCK * SORT_R;
 constexpr int SORT_WARP = 32 * SORT_R;  // consecutive slots of one warp in a sort tile
 
-// Stable counting sort of every store by cell, in three passes over tiles of
-// SORT_TILE slots (warp w of tile t owns slots t SORT_TILE + w SORT_WARP ...):
-// per-tile cell counts (hist[seg][t N + c]); per cell an exclusive scan over the
-// tiles plus the cell starts; the scatter, where each warp places its slots in
-// order (rank among equal cells by match_any). Input through the store's
-// segment table, output dense.
+// Stable counting sort of every store by cell, over tiles of SORT_TILE slots
+// (warp w of tile t owns slots t SORT_TILE + w SORT_WARP ...):
+//   k_sort_count   per tile: each slot's cell and its rank among the tile's
+//                  slots of the same cell (in slot order), packed with the cell
+//                  into kr[slot], its record offset into off[slot], and the
+//                  tile's cell counts into hist[seg][t N + c]; input read
+//                  through the store's segment table;
+//   k_sort_rows    per cell: exclusive scan of the counts over the tiles;
+//   k_sort_cells   per store: exclusive scan of the cell totals;
+//   k_sort_scatter streaming, one slot per thread: destination = first slot of
+//                  its cell + the tile's offset in that cell + its rank.
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                            int buf, unsigned* __restrict__ hist,
-                                                           const long long* __restrict__ hoff) {
-    extern __shared__ __align__(16) unsigned s_c[];
+                                                           const long long* __restrict__ hoff,
+                                                           unsigned* __restrict__ kr_all, unsigned* __restrict__ off_all,
+                                                           const long long* __restrict__ eoff, int max_N) {
+    extern __shared__ __align__(16) unsigned s_w[];  // [SORT_NW][max_N] per-warp counts, then prefixes
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
@@ -1323,33 +1330,62 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restric
     const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
     const int32_t* __restrict__ cc = D.c[buf][sp];
     unsigned* H = hist + hoff[seg];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned* KR = kr_all + eoff[seg];
+    unsigned* OF = off_all + eoff[seg];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned* Wc = s_w + warp * max_N;
     for (unsigned t = blockIdx.x; t < Ts; t += gridDim.x) {
-        for (int j = threadIdx.x; j < N; j += SORT_BLOCK) s_c[j] = 0;
+        for (int j = tid; j < SORT_NW * max_N; j += SORT_BLOCK) s_w[j] = 0;
         __syncthreads();
         const unsigned wbase = t * SORT_TILE + warp * SORT_WARP;
-        if (wbase < n) {
-            SegCursor cur;
-            cur.init(D.seg_start[sp], D.seg_src[sp], D.first_seg[sp], nseg, wbase, D.chunk, lane);
-            int key[SORT_R];
+        unsigned kr[SORT_R], off[SORT_R];  // cell (then | rank in the warp << 16), record offset
+        SegCursor cur;
+        if (wbase < n) cur.init(D.seg_start[sp], D.seg_src[sp], D.first_seg[sp], nseg, wbase, D.chunk, lane);
 #pragma unroll
-            for (int r = 0; r < SORT_R; ++r) {  // all loads first
-                const unsigned s0 = wbase + 32 * r, slot = s0 + lane;
-                key[r] = N;
-                if (s0 < n) {
-                    const unsigned off = cur.offset(s0, slot);
-                    if (slot < n) key[r] = __ldcs(cc + off);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < SORT_R; ++r) {
-                const unsigned peers = __match_any_sync(FULL, key[r]);
-                if ((unsigned)key[r] < (unsigned)N && lane == __ffs(peers) - 1)
-                    atomicAdd(&s_c[key[r]], (unsigned)__popc(peers));
+        for (int r = 0; r < SORT_R; ++r) {  // all cell loads first
+            const unsigned s0 = wbase + 32 * r, slot = s0 + lane;
+            kr[r] = 0xFFFFu;
+            off[r] = 0;
+            if (s0 < n) {
+                off[r] = cur.offset(s0, slot);
+                if (slot < n) kr[r] = (unsigned)__ldcs(cc + off[r]);  // checked below, after all loads are issued
             }
         }
+#pragma unroll
+        for (int r = 0; r < SORT_R; ++r) {  // rank among the warp's equal cells so far
+            if (kr[r] >= (unsigned)N) kr[r] = 0xFFFFu;  // past the store, or a corrupt cell index: not placed
+            const int k = (int)kr[r];
+            const unsigned peers = __match_any_sync(FULL, k);
+            if (k < N) {
+                const unsigned b = Wc[k];
+                kr[r] |= (b + __popc(peers & lt)) << 16;
+                __syncwarp(peers);
+                if (lane == __ffs(peers) - 1) Wc[k] = b + __popc(peers);
+            }
+            __syncwarp();
+        }
         __syncthreads();
-        for (int j = threadIdx.x; j < N; j += SORT_BLOCK) H[(size_t)t * N + j] = s_c[j];
+        for (int j = tid; j < N; j += SORT_BLOCK) {  // per cell: prefix over the warps, tile count
+            unsigned run = 0;
+#pragma unroll
+            for (int w = 0; w < SORT_NW; ++w) {
+                const unsigned v = s_w[w * max_N + j];
+                s_w[w * max_N + j] = run;
+                run += v;
+            }
+            H[(size_t)t * N + j] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SORT_R; ++r) {
+            const unsigned slot = wbase + 32 * r + lane;
+            if (slot < n) {
+                const int k = (int)(kr[r] & 0xFFFFu);
+                KR[slot] = k < N ? (unsigned)k | ((Wc[k] + (kr[r] >> 16)) << 16) : 0xFFFFu;
+                OF[slot] = off[r];
+            }
+        }
         __syncthreads();
     }
 }
@@ -1430,79 +1466,31 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
                                                              const Ctl* __restrict__ ctl, int src, int dst,
                                                              const unsigned* __restrict__ hist,
                                                              const long long* __restrict__ hoff,
-                                                             const unsigned* __restrict__ tot, int max_N) {
-    extern __shared__ __align__(16) unsigned s_w[];  // [SORT_NW][max_N]
+                                                             const unsigned* __restrict__ tot,
+                                                             const unsigned* __restrict__ kr_all,
+                                                             const unsigned* __restrict__ off_all,
+                                                             const long long* __restrict__ eoff) {
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
     const unsigned n = (unsigned)ctl->count[d][sp];
-    const int nseg = ctl->nseg[d][sp];
-    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
-    const int32_t* __restrict__ cs = D.c[src][sp];
-    int32_t* __restrict__ cd = D.c[dst][sp];
     using R = typename Rec<T>::type;
     const R* __restrict__ ps = reinterpret_cast<const R*>(D.p[src][sp]);
     R* __restrict__ pd = reinterpret_cast<R*>(D.p[dst][sp]);
+    int32_t* __restrict__ cd = D.c[dst][sp];
     const unsigned* H = hist + hoff[seg];
     const unsigned* cstart = tot + (long long)seg * MAXN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned* Wc = s_w + warp * max_N;
-    for (unsigned t = blockIdx.x; t < Ts; t += gridDim.x) {
-        for (int j = tid; j < SORT_NW * max_N; j += SORT_BLOCK) s_w[j] = 0;
-        __syncthreads();
-        const unsigned wbase = t * SORT_TILE + warp * SORT_WARP;
-        uint32_t kr[SORT_R];  // cell | rank among the warp's equal cells so far << 16
-        unsigned off[SORT_R];
-        SegCursor cur;
-        if (wbase < n) cur.init(D.seg_start[sp], D.seg_src[sp], D.first_seg[sp], nseg, wbase, D.chunk, lane);
-#pragma unroll
-        for (int r = 0; r < SORT_R; ++r) {  // all cell loads first
-            const unsigned s0 = wbase + 32 * r, slot = s0 + lane;
-            int key = N;
-            off[r] = 0;
-            if (s0 < n) {
-                off[r] = cur.offset(s0, slot);
-                if (slot < n) key = __ldcs(cs + off[r]);
-            }
-            kr[r] = (uint32_t)key;
+    const unsigned* KR = kr_all + eoff[seg];
+    const unsigned* OF = off_all + eoff[seg];
+    for (unsigned i = blockIdx.x * SORT_BLOCK + threadIdx.x; i < n; i += gridDim.x * SORT_BLOCK) {
+        const unsigned kr = __ldcs(KR + i);
+        const int k = (int)(kr & 0xFFFFu);
+        if (k >= N) continue;  // a corrupt cell index (reported by the sweep): dropped
+        const unsigned o = cstart[k] + H[(size_t)(i / SORT_TILE) * N + k] + (kr >> 16);
+        if (o < n) {
+            cd[o] = k;
+            pd[o] = ps[__ldcs(OF + i)];
         }
-#pragma unroll
-        for (int r = 0; r < SORT_R; ++r) {  // rank of each slot among the warp's equal cells
-            const int key = (int)kr[r];
-            const unsigned peers = __match_any_sync(FULL, key);
-            if ((unsigned)key < (unsigned)N) {
-                const unsigned b = Wc[key];
-                kr[r] |= (b + __popc(peers & lt)) << 16;
-                __syncwarp(peers);
-                if (lane == __ffs(peers) - 1) Wc[key] = b + __popc(peers);
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        // per cell: its first output slot for each warp of the tile
-        for (int j = tid; j < N; j += SORT_BLOCK) {
-            unsigned run = cstart[j] + H[(size_t)t * N + j];
-#pragma unroll
-            for (int w = 0; w < SORT_NW; ++w) {
-                const unsigned v = s_w[w * max_N + j];
-                s_w[w * max_N + j] = run;
-                run += v;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < SORT_R; ++r) {
-            const int k = (int)(kr[r] & 0xFFFFu);
-            if ((unsigned)k < (unsigned)N) {
-                const unsigned o = Wc[k] + (kr[r] >> 16);
-                if (o < n) {
-                    cd[o] = k;
-                    pd[o] = ps[off[r]];
-                }
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -1745,10 +1733,14 @@ cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, 
 }
 
 cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int src, int dst, unsigned* hist,
-                        const long long* hoff, unsigned* tot, int max_N, int grid_x, cudaStream_t st) {
+                        const long long* hoff, unsigned* tot, unsigned* kr, unsigned* off, const long long* eoff,
+                        int max_N, int grid_x, cudaStream_t st) {
     dim3 g(grid_x, 2 * n_disc);
-    k_sort_count<<<g, SORT_BLOCK, sizeof(unsigned) * max_N, st>>>(discs, ctl, src, hist, hoff);
-    cudaError_t e = cudaGetLastError();
+    const size_t smem = sizeof(unsigned) * SORT_NW * max_N;
+    cudaError_t e = smem_attr(k_sort_count, smem);
+    if (e != cudaSuccess) return e;
+    k_sort_count<<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, hist, hoff, kr, off, eoff, max_N);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sort_rows<<<dim3((max_N + 31) / 32, 2 * n_disc), 1024, 0, st>>>(discs, ctl, hist, hoff, tot);
     e = cudaGetLastError();
@@ -1756,14 +1748,9 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
     k_sort_cells<<<2 * n_disc, 1024, 0, st>>>(discs, tot);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(unsigned) * SORT_NW * max_N;
-    if (fp64) {
-        smem_attr(k_sort_scatter<double>, smem);
-        k_sort_scatter<double><<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, dst, hist, hoff, tot, max_N);
-    } else {
-        smem_attr(k_sort_scatter<float>, smem);
-        k_sort_scatter<float><<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, dst, hist, hoff, tot, max_N);
-    }
+    const dim3 gs(4 * grid_x, 2 * n_disc);
+    if (fp64) k_sort_scatter<double><<<gs, SORT_BLOCK, 0, st>>>(discs, ctl, src, dst, hist, hoff, tot, kr, off, eoff);
+    else k_sort_scatter<float><<<gs, SORT_BLOCK, 0, st>>>(discs, ctl, src, dst, hist, hoff, tot, kr, off, eoff);
     return cudaGetLastError();
 }
 
