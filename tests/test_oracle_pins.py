@@ -250,6 +250,50 @@ def test_constant_field_parabola():
     assert np.max(np.abs(z - z_ref)) <= 1e-11 * gap
 
 
+def test_harmonic_oscillation_in_uniform_background_charge():
+    """Uniform fixed positive charge n0 e between grounded plates (V = 0): the node field is exactly
+    E = e n0 (z - d/2) / eps0 (the 3-point stencil is exact for the quadratic potential) and the
+    CIC gather of a linear field is exact, so a test electron released at rest at d/2 + A is a
+    harmonic oscillator of omega^2 = e^2 n0 / (m_e eps0). Velocity Verlet then gives exactly
+    z_n - d/2 = A cos(w n dt) with cos(w dt) = 1 - (omega dt)^2 / 2 (the numerical frequency
+    (2/dt) arcsin(omega dt / 2)). Pins gather, both half kicks, drift and the Poisson solve
+    together: a wrong kick factor, sign or kick placement fails it."""
+    N, gap, n0 = 64, 0.025, 8e14
+    m_per_cell = 16
+    d = I.discharge(n_cells=N, gap_m=gap, n_e0=10 ** 15, n_i0=N * m_per_cell, n_init_m3=n0, V_rf_V=0.0)
+    dt, dx = d.dt_s, gap / N
+    o = O.Oracle(_no_collision_gas(mass=1.0), d, "f64", load=False)   # ions of 1 kg: they stay put
+    k = np.arange(N * m_per_cell)
+    ions = {"c": (k // m_per_cell).astype(np.int32), "f": ((k % m_per_cell) + 0.5) / m_per_cell,
+            "vx": np.zeros(k.size), "vy": np.zeros(k.size), "vz": np.zeros(k.size)}
+    A = 0.2 * gap
+    z0 = gap / 2 + A
+    c0 = int(z0 // dx)
+    e = {"c": np.array([c0], np.int32), "f": np.array([z0 / dx - c0]), "vx": np.zeros(1), "vy": np.zeros(1),
+         "vz": np.zeros(1)}
+    # the oracle deposits the ions (field-free sweep) and solves for their field
+    o.set_field(np.zeros(N + 1))
+    o.set_state(1, ions)
+    o.set_state(0, e)
+    o.sweep()
+    o.solve()
+    eps0 = 8.8541878128e-12
+    E_z0 = I.E_CH * n0 * (z0 - gap / 2) / eps0
+    assert np.allclose(o.get_field64(), I.E_CH * n0 * (np.arange(N + 1) * dx - gap / 2) / eps0, rtol=1e-9,
+                       atol=1e-9 * abs(E_z0))
+    # released at rest: the stored velocity is v_0 - (q/m) E(z0) dt / 2
+    e["vz"] = np.array([-(-I.E_CH / I.M_E) * E_z0 * dt / 2])
+    o.set_state(0, e)
+    omega = math.sqrt(I.E_CH ** 2 * n0 / (I.M_E * eps0))
+    assert 0.1 < omega * dt < 1.0
+    w = math.acos(1 - 0.5 * (omega * dt) ** 2) / dt
+    for n in range(1, 201):
+        o.step(1)
+        st = o.get_state(0)
+        z = (st["c"][0] + st["f"][0]) * dx
+        assert abs((z - gap / 2) - A * math.cos(w * n * dt)) <= 1e-9 * A, n
+
+
 # --------------------------------------------------------------------------- MCC
 
 def test_brute_force_collision_probability_electrons():
