@@ -428,3 +428,51 @@ def test_state_upload_round_trip_and_rejects_bad_cells(P, prec):
         sim.set_state(0, 1, bad)
     assert sim.count(0, 1) == 0
     sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_harmonic_oscillation_tracks_oracle(P, prec, tol):
+    """A test electron released at rest in a uniform fixed ion background (grounded plates): the
+    kernels' gather, half kicks, drift and Poisson solve follow the oracle, which the CPU pins tie
+    to the velocity-Verlet closed form A cos(w n dt). Positions agree to tol x amplitude over
+    200 steps (about nine oscillations)."""
+    N, gap, n0, m = 64, 0.025, 8e14, 16
+    gas = X.constant_sigma(0.0, mass_kg=1.0)  # no collisions; ions of 1 kg stay put
+    d = I.discharge(n_cells=N, gap_m=gap, n_e0=N * m, n_i0=N * m, n_init_m3=n0, V_rf_V=0.0)
+    dt, dx = d.dt_s, gap / N
+    dtype = np.float64 if prec == "fp64" else np.float32
+    sim = P.Simulation(gas, d, precision=prec, load=False)
+    ref = O.Oracle(gas, d, _prec(prec), load=False)
+    k = np.arange(N * m)
+    ions = {"c": (k // m).astype(np.int32), "f": (((k % m) + 0.5) / m).astype(dtype),
+            "vx": np.zeros(k.size, dtype), "vy": np.zeros(k.size, dtype), "vz": np.zeros(k.size, dtype)}
+    A = 0.2 * gap
+    z0 = gap / 2 + A
+    c0 = int(z0 // dx)
+    e = {"c": np.array([c0], np.int32), "f": np.array([z0 / dx - c0], dtype), "vx": np.zeros(1, dtype),
+         "vy": np.zeros(1, dtype), "vz": np.zeros(1, dtype)}
+    for obj in (sim, ref):
+        if obj is sim:
+            sim.set_field(0, np.zeros(N + 1, dtype))
+            sim.set_state(0, 1, ions)
+            sim.set_state(0, 0, e)
+        else:
+            ref.set_field(np.zeros(N + 1, dtype))
+            ref.set_state(1, ions)
+            ref.set_state(0, e)
+        obj.sweep()
+        obj.solve()
+    E_z0 = float(np.interp(z0, np.arange(N + 1) * dx, ref.get_field64()))
+    e["vz"] = np.array([(I.E_CH / I.M_E) * E_z0 * dt / 2], dtype)  # released at rest
+    sim.set_state(0, 0, e)
+    ref.set_state(0, e)
+    for n in range(1, 201):
+        sim.step(1)
+        ref.step(1)
+        if n in (1, 7, 50, 200):
+            a, b = sim.get_state(0, 0), ref.get_state(0)
+            za = (float(a["c"][0]) + float(a["f"][0])) * dx
+            zb = (float(b["c"][0]) + float(b["f"][0])) * dx
+            assert abs(za - zb) <= tol * A, (prec, n, za, zb)
+    sim.close()
