@@ -175,9 +175,10 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def measure(prec: str, steps: int, warmup: int, sort_every: int):
-        sim = pic.Simulation(gas, d, seed=d.seed, precision=prec, sort_every=sort_every, stream="torch",
-                             block=args.block, ppt=args.ppt)
+    def measure(prec: str, steps: int, warmup: int, sort_every: int, disc=None, disc_gas=None):
+        dd = disc if disc is not None else d
+        sim = pic.Simulation(disc_gas if disc_gas is not None else gas, dd, seed=dd.seed, precision=prec,
+                             sort_every=sort_every, stream="torch", block=args.block, ppt=args.ppt)
         sim.step(warmup)
         sim.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -305,6 +306,20 @@ def run_gpu(args, rank: int, world: int):
     fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
     e2e = measure_e2e("fp32", max(3, min(10, args.steps)), sort_every)
     batch = measure_batch(max(4, args.steps // 2), 3, sort_every) if not args.no_batch else None
+    c3 = None
+    if args.c3 and world == 1:
+        # the large workload: 2e7 + 2e7 particles, 2048 cells, secondary emission (800 MB per record
+        # buffer, far beyond L2)
+        from paper_1608_04601_gb300.workloads import c3 as c3_disc
+        dc = c3_disc()
+        r3 = measure("fp32", 20, 6, sort_every, disc=dc, disc_gas=gas_for(dc))
+        lp3 = r3["ps"] / max(1, r3["sweep_launches"])
+        s3 = r3["sweep_ms"] * 1e-3 / max(1, r3["sweep_launches"])
+        c3 = {"workload": dc.name, "value": r3["ps"] / (r3["total_ms"] * 1e-3), "unit": UNIT,
+              "ms_per_step": r3["total_ms"] / 20, "steps": 20, "warmup": 6,
+              "sweep_avg_launch_ms": s3 * 1e3, "sweep_gbs": BYTES_PER_PS["fp32"] * lp3 / s3 / 1e9,
+              "sweep_frac_of_peak": BYTES_PER_PS["fp32"] * lp3 / s3 / 1e9 / peaks()[0],
+              "particles": int(lp3), "clocks": r3["clocks"]}
     warm = None
     if args.warm_start and world == 1:
         # rf periods to the steady state from the homogeneous start vs from the network's profiles
@@ -344,6 +359,8 @@ def run_gpu(args, rank: int, world: int):
            "e2e": e2e, "clocks": main["clocks"], "gpu_launches": main["gpu_launches"]}
     if batch:
         res["batch_c4"] = batch
+    if c3:
+        res["c3"] = c3
     if warm:
         res["warm_start"] = warm
     return res
@@ -381,6 +398,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-c3", dest="c3", action="store_false", help="skip the 2e7 + 2e7 particle workload")
     ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
                     help="skip the warm-start experiment (training runs, network training, cold vs warm runs)")
     ap.add_argument("--ws-train", type=int, default=64, help="training discharges of the warm-start experiment")
