@@ -198,7 +198,7 @@ extern "C" void pic_destroy(pic_ctx* ctx) {
     delete ctx;
 }
 
-static pic_status enqueue_sweep(pic_ctx* ctx, int full_step);
+static pic_status enqueue_sweep(pic_ctx* ctx);
 static pic_status enqueue_finalize(pic_ctx* ctx, int mode);
 static pic_status enqueue_sort(pic_ctx* ctx);
 
@@ -444,9 +444,9 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
             ALLOC(D.cnt_birth[sp], int*, sizeof(int) * (mc + 1));
             const size_t ns = (mc + SLICE - 1) / SLICE + 1;
             ctx->max_slices = std::max(ctx->max_slices, (int)ns);
-            ALLOC(D.slice_tot[sp], unsigned*, sizeof(unsigned) * 3 * ns);
-            ALLOC(D.slice_pre[sp], unsigned*, sizeof(unsigned) * 3 * ns);
-            if (cudaMemset(D.slice_tot[sp], 0, sizeof(unsigned) * 3 * ns) != cudaSuccess) {
+            D.slice_n[sp] = (int)ns;
+            ALLOC(D.slice_tot[sp], unsigned*, sizeof(unsigned) * 2 * 3 * ns);  // two parities
+            if (cudaMemset(D.slice_tot[sp], 0, sizeof(unsigned) * 2 * 3 * ns) != cudaSuccess) {
                 pic_status s_ = fail(ctx, PIC_ERR_CUDA, "slice sums");
                 pic_destroy(ctx);
                 return s_;
@@ -540,7 +540,7 @@ extern "C" pic_status pic_create(pic_ctx** out, const pic_gas* gas, double gap_m
 }
 
 // ---------------------------------------------------------------------------
-static pic_status enqueue_sweep(pic_ctx* ctx, int full_step) {
+static pic_status enqueue_sweep(pic_ctx* ctx) {
     if (!ctx->deposits_zero) {
         for (auto& D : ctx->hd) {
             const size_t b = 8 * ((size_t)D.N + 1);
@@ -574,7 +574,6 @@ static pic_status enqueue_sweep(pic_ctx* ctx, int full_step) {
     }
     CK(launch_sweep(L), "sweep launch");
     if (evp) cudaEventRecord(evp->second, ctx->stream);
-    CK(launch_totals(ctx->d_discs, ctx->n_disc, ctx->d_ctl, full_step, ctx->stream), "totals launch");
     ctx->deposits_zero = false;
     return PIC_OK;
 }
@@ -603,7 +602,7 @@ static pic_status enqueue_sort(pic_ctx* ctx) {
 // Sweep + births + solve: the sweep reads buffer cur and writes 1-cur; the
 // finalize appends births into 1-cur; cur flips.
 static pic_status enqueue_step(pic_ctx* ctx) {
-    pic_status s = enqueue_sweep(ctx, 1);
+    pic_status s = enqueue_sweep(ctx);
     if (s != PIC_OK) return s;
     s = enqueue_finalize(ctx, 3);
     if (s != PIC_OK) return s;
@@ -673,7 +672,7 @@ extern "C" pic_status pic_step(pic_ctx* ctx, int64_t n_steps) {
 
 extern "C" pic_status pic_sweep(pic_ctx* ctx) {
     if (!ctx) return PIC_ERR_ARG;
-    pic_status s = enqueue_sweep(ctx, 0);
+    pic_status s = enqueue_sweep(ctx);
     if (s != PIC_OK) return s;
     // births appended and counts updated; no solve, no step advance
     CK(launch_finalize(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, 1 - ctx->cur, 1 | 8, ctx->max_slices,

@@ -86,11 +86,12 @@ struct Disc {
     void* bp[2];              //   chunk k owns records [k chunk, (k+1) chunk)
     int32_t* sc;              // ionization electrons of the electron sweep, same chunk regions
     void* sp_;
-    // per slice of SLICE sweep chunks of species sp, [k][3]: 0 survivors, 1 other-species
-    // newborns, 2 same-species newborns. slice_tot: sums (the sweep adds, the segment pass
-    // clears); slice_pre: output offsets of the slice's first chunk (finalize)
+    // per slice of SLICE sweep chunks of species sp, [parity][k][3]: 0 survivors, 1 other-species
+    // newborns, 2 same-species newborns. The sweep adds into parity Ctl::slice_par; k_post reads
+    // it and clears the other parity for the next sweep
     unsigned* slice_tot[2];
-    unsigned* slice_pre[2];
+    int slice_n[2];           // slices per parity
+
     long long bcap;           // births region size in the record buffers
     void* E;                  // node field for the gather (T), N+1
     double* E64;              // node field, FP64
@@ -110,11 +111,11 @@ struct Ctl {
     long long step;           // current step index n
     unsigned int tile_ctr;    // sweep tile dispenser
     unsigned int done;        // sweep CTAs finished
-    unsigned int fin_done;    // finalize CTAs finished
+    unsigned int fin_done;    // k_post CTAs finished
     int error;                // ERR_* bits
     long long count[MAXD][2]; // superparticles per store
     long long count_in[MAXD][2]; // the counts the last sweep read (its tiles)
-    long long see_base[MAXD];    // offset of the SEE electrons among store 0's newborns (after the ionization electrons)
+    int slice_par;               // parity of the slice sums the next sweep adds into
     int nseg[MAXD][2];        // segments per store
     long long acc_steps[MAXD];
     double E0_last[MAXD];

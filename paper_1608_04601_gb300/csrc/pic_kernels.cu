@@ -1,7 +1,7 @@
 // pic_kernels.cu -- CUDA kernels (sm_103a) of the 1d3v PIC/MCC time step of
 // arXiv:1608.04601, section "PIC/MCC simulation procedure".
 //
-// One time step is three launches (and the sort every K steps):
+// One time step is two launches (and the sort every K steps):
 //   k_sweep     persistent; tiles of BLOCK x PPT slots of all stores in a
 //               static grid-stride order; each warp owns a chunk of 32 PPT
 //               slots and loads, pushes (CIC gather of E_n from shared
@@ -11,12 +11,11 @@
 //               chunk's newborn regions, with no barrier inside a tile. CIC
 //               deposits go to warp-aggregated shared-memory int64 histograms,
 //               flushed with global atomics. Chunk counts are summed per slice.
-//   k_totals    one warp per discharge: slice sums -> output offsets, new store
-//               counts.
 //   k_post      per slice of chunks: the segment table entries and the newborn
-//               copies; per discharge, concurrently: Poisson (Eq. poisson, rf
-//               Dirichlet boundary) from exact integer prefix sums of the
-//               deposits, node field, cycle-average accumulators.
+//               copies; per discharge, concurrently: the store totals (new
+//               counts) and Poisson (Eq. poisson, rf Dirichlet boundary) from
+//               exact integer prefix sums of the deposits, node field,
+//               cycle-average accumulators.
 //   sort        every K steps: stable counting sort of each store by cell
 //               into a dense store.
 #include "pic_internal.h"
@@ -419,58 +418,40 @@ __device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, doub
     f = a.x; vx = a.y; vy = b.x; vz = b.y;
 }
 
-// Store totals after a sweep, for discharge d, by one warp (k_totals): the
-// output offsets of every slice of sweep chunks (slice_pre),
-// the new counts and segment counts, the newborn segment and its first_seg
-// entries; on a full step also the per-period mean counts. The per-chunk
-// segment entries and the newborn copies follow in k_post.
-__device__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, bool full_step, int& err) {
+// Store totals after a sweep, for discharge d, by one warp of k_post: from the
+// slice sums of parity par, the new counts and segment counts, the newborn
+// segment and its first_seg entries, on a full step the per-period mean
+// counts; then the slice sums of the other parity cleared for the next sweep.
+__device__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, int par, bool full_step, int& err) {
     const int TILE = D.tile, CHUNK = D.chunk;
     long long chunks[2], slices[2];
     for (int sp = 0; sp < 2; ++sp) {
         chunks[sp] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
         slices[sp] = (chunks[sp] + SLICE - 1) / SLICE;
     }
-    // exclusive warp scans of the five slice-sum columns (survivors of both sweeps, ionization
-    // electrons and ions of the electron sweep, SEE electrons of the ion sweep) into slice_pre,
-    // 32 slices a round, all loads of a round issued first. The SEE electrons' offsets are
-    // relative: k_post adds see_base, the count of ionization electrons that precede them.
+    const unsigned* T0 = D.slice_tot[0] + (size_t)par * 3 * D.slice_n[0];
+    const unsigned* T1 = D.slice_tot[1] + (size_t)par * 3 * D.slice_n[1];
+    // survivors of both sweeps, ionization electrons and ions of the electron sweep, SEE electrons
     long long main0 = 0, main1 = 0, same0 = 0, see = 0, ions = 0;
-    const long long rounds = (max(slices[0], slices[1]) + 31) / 32;
-    for (long long r = 0; r < rounds; ++r) {
-        const long long k = r * 32 + lane;
-        const bool e = k < slices[0], i = k < slices[1];
-        long long v[5] = {e ? (long long)__ldcg(&D.slice_tot[0][3 * k + 0]) : 0,
-                          i ? (long long)__ldcg(&D.slice_tot[1][3 * k + 0]) : 0,
-                          e ? (long long)__ldcg(&D.slice_tot[0][3 * k + 2]) : 0,
-                          i ? (long long)__ldcg(&D.slice_tot[1][3 * k + 1]) : 0,
-                          e ? (long long)__ldcg(&D.slice_tot[0][3 * k + 1]) : 0};
-        long long x[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            x[q] = v[q];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long y = __shfl_up_sync(FULL, x[q], o);
-                if (lane >= o) x[q] += y;
-            }
+    for (long long k = lane; k < max(slices[0], slices[1]); k += 32) {
+        if (k < slices[0]) {
+            main0 += T0[3 * k + 0];
+            ions += T0[3 * k + 1];
+            same0 += T0[3 * k + 2];
         }
-        if (e) {
-            D.slice_pre[0][3 * k + 0] = (unsigned)(main0 + x[0] - v[0]);
-            D.slice_pre[0][3 * k + 2] = (unsigned)(same0 + x[2] - v[2]);
-            D.slice_pre[0][3 * k + 1] = (unsigned)(ions + x[4] - v[4]);
+        if (k < slices[1]) {
+            main1 += T1[3 * k + 0];
+            see += T1[3 * k + 1];
         }
-        if (i) {
-            D.slice_pre[1][3 * k + 0] = (unsigned)(main1 + x[1] - v[1]);
-            D.slice_pre[1][3 * k + 1] = (unsigned)(see + x[3] - v[3]);
-        }
-        main0 += __shfl_sync(FULL, x[0], 31);
-        main1 += __shfl_sync(FULL, x[1], 31);
-        same0 += __shfl_sync(FULL, x[2], 31);
-        see += __shfl_sync(FULL, x[3], 31);
-        ions += __shfl_sync(FULL, x[4], 31);
     }
-    if (lane == 0) ctl->see_base[d] = same0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        main0 += __shfl_xor_sync(FULL, main0, o);
+        main1 += __shfl_xor_sync(FULL, main1, o);
+        same0 += __shfl_xor_sync(FULL, same0, o);
+        see += __shfl_xor_sync(FULL, see, o);
+        ions += __shfl_xor_sync(FULL, ions, o);
+    }
     for (int sp = 0; sp < 2; ++sp) {
         const long long main_total = sp == 0 ? main0 : main1;
         const long long nb = sp == 0 ? same0 + see : ions;
@@ -508,6 +489,9 @@ __device__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, bool full
         const long long jmax = (long long)D.max_tiles[sp] * D.warps;
         for (long long j = (main_total + CHUNK - 1) / CHUNK + lane; j * CHUNK < n_new && j <= jmax; j += 32)
             D.first_seg[sp][j] = (int)ch;
+        // the next sweep adds into the other parity
+        unsigned* Tn = D.slice_tot[sp] + (size_t)(par ^ 1) * 3 * D.slice_n[sp];
+        for (int k = lane; k < 3 * D.slice_n[sp]; k += 32) Tn[k] = 0;
     }
 }
 
@@ -567,6 +551,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     __shared__ long long s_segstart[2 * MAXD + 1];
     __shared__ Seg<T> S;
     __shared__ long long s_step;
+    __shared__ int s_par;
     __shared__ unsigned s_cnt[NCNT];
     __shared__ int s_err;
 
@@ -580,6 +565,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         }
         s_segstart[2 * n_disc] = acc;
         s_step = ctl->step;
+        s_par = ctl->slice_par;
         s_err = 0;
     }
     __syncthreads();
@@ -807,7 +793,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 S.cnt_main = D.cnt_main[sp];
                 S.cnt_birth = D.cnt_birth[sp];
                 S.cnt_same = D.cnt_same;
-                S.slice_tot = D.slice_tot[sp];
+                S.slice_tot = D.slice_tot[sp] + (size_t)s_par * 3 * D.slice_n[sp];
             }
             if (tid < NCNT) s_cnt[tid] = 0;
             __syncthreads();
@@ -846,13 +832,6 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     }
 }
 
-// Store totals of every discharge after a sweep, one warp per discharge.
-__global__ void k_totals(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl, int full_step) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int err = 0;
-    for (int d = warp; d < n_disc; d += nw) store_totals(discs[d], d, ctl, lane, full_step != 0, err);
-    if (err) atomicOr(&ctl->error, err);
-}
 
 // ---------------------------------------------------------------------------
 // Integer prefix segment of the Poisson sums for both species: r = sum of
@@ -940,6 +919,36 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
     const long long chunks = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
     const long long t0 = (long long)blockIdx.x * SLICE;
     if (t0 >= chunks) return;
+    // output offsets of this slice: the sums of the slices before it (survivors, other-species
+    // newborns, same-species newborns); the ion sweep's SEE electrons follow all ionization
+    // electrons of the electron sweep
+    __shared__ long long s_pre[3];
+    if (warp == 0) {
+        const int par = ctl->slice_par;
+        const unsigned* Tp = D.slice_tot[sp] + (size_t)par * 3 * D.slice_n[sp];
+        long long a = 0, b = 0, c = 0;
+        for (int k = lane; k < (int)blockIdx.x; k += 32) {
+            a += Tp[3 * k + 0];
+            b += Tp[3 * k + 1];
+            c += Tp[3 * k + 2];
+        }
+        if (sp == 1) {
+            const long long ch0 = (ctl->count_in[d][0] + TILE - 1) / TILE * D.warps;
+            const unsigned* T0 = D.slice_tot[0] + (size_t)par * 3 * D.slice_n[0];
+            for (long long k = lane; k < (ch0 + SLICE - 1) / SLICE; k += 32) b += T0[3 * k + 2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(FULL, a, o);
+            b += __shfl_xor_sync(FULL, b, o);
+            c += __shfl_xor_sync(FULL, c, o);
+        }
+        if (lane == 0) {
+            s_pre[0] = a;
+            s_pre[1] = b;
+            s_pre[2] = c;
+        }
+    }
     const long long tb = t0 + (long long)tid * K;
     int cm[K], cb[K], cs[K];
     int rm = 0, rb = 0, rs = 0;
@@ -980,11 +989,9 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
         s_w[warp][lane] = x - v;
     }
     __syncthreads();
-    const unsigned* pre = D.slice_pre[sp] + 3 * blockIdx.x;
-    long long em = (long long)pre[0] + s_w[0][warp] + xm - rm;
-    // other-species newborns: the ion sweep's SEE electrons follow all ionization electrons
-    long long eb = (long long)pre[1] + s_w[1][warp] + xb - rb + (sp == 1 ? ctl->see_base[d] : 0);
-    long long es = (long long)pre[2] + s_w[2][warp] + xs - rs;
+    long long em = s_pre[0] + s_w[0][warp] + xm - rm;
+    long long eb = s_pre[1] + s_w[1][warp] + xb - rb;
+    long long es = s_pre[2] + s_w[2][warp] + xs - rs;
     using R = float4;
     int* st = D.seg_start[sp];
     int* sr = D.seg_src[sp];
@@ -1029,7 +1036,6 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
         es += cs[i];
     }
     if (err) atomicOr(&ctl->error, err);
-    if (tid < 3) D.slice_tot[sp][3 * blockIdx.x + tid] = 0;
 }
 
 template <typename T>
@@ -1044,6 +1050,12 @@ __global__ void __launch_bounds__(1024) k_post(const Disc* __restrict__ discs, i
     __syncthreads();
     if ((int)blockIdx.x < nsl) {
         seg_apply<BLOCK>(discs, ctl, out_buf, tid, lane, warp);
+    } else if ((mode & 1) && (blockIdx.y & 1) == 1) {  // store totals of discharge y / 2
+        if (warp == 0) {
+            int e2 = 0;
+            store_totals(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, lane, ctl->slice_par, (mode & 2) != 0, e2);
+            if (e2 && lane == 0) atomicOr(&s_err, e2);
+        }
     } else if (!(mode & 8) && (blockIdx.y & 1) == 0) {
         const int d = blockIdx.y >> 1;
         const Disc& D = discs[d];
@@ -1130,16 +1142,15 @@ __global__ void __launch_bounds__(1024) k_post(const Disc* __restrict__ discs, i
         }
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {  // the last CTA advances the step (bit 2) and, after a sweep, the slice parity
         if (s_err) atomicOr(&ctl->error, s_err);
-        if (mode & 2) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
+        if (prev == gridDim.x * gridDim.y - 1) {
+            ctl->fin_done = 0;
+            if (mode & 2) ctl->step = ctl->step + 1;
+            if (mode & 1) ctl->slice_par = ctl->slice_par ^ 1;
             __threadfence();
-            const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
-            if (prev == gridDim.x * gridDim.y - 1) {
-                ctl->fin_done = 0;
-                ctl->step = ctl->step + 1;
-                __threadfence();
-            }
         }
     }
 }
@@ -1768,10 +1779,6 @@ cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_totals(const Disc* discs, int n_disc, Ctl* ctl, int full_step, cudaStream_t st) {
-    k_totals<<<1, 32 * (n_disc < 32 ? n_disc : 32), 0, st>>>(discs, n_disc, ctl, full_step);
-    return cudaGetLastError();
-}
 
 long long sort_tile() { return SORT_TILE; }
 

@@ -13,8 +13,6 @@ struct SweepLaunch {
 };
 
 cudaError_t launch_sweep(const SweepLaunch& L);
-// Store totals after a sweep (slice offsets, new counts), one warp per discharge.
-cudaError_t launch_totals(const Disc* discs, int n_disc, Ctl* ctl, int full_step, cudaStream_t st);
 int sweep_occupancy(int fp64, int block, int ppt, int max_N);
 cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, int max_slices,
                             int max_N, cudaStream_t st);
