@@ -86,6 +86,13 @@ struct Seg {
 // lives at seg_src[k] + (s - seg_start[k]), k the last segment with
 // seg_start[k] <= s. The 32 segments from the first one of the walk sit in
 // registers (lane j holds segment k0 + j); later ones are read from memory.
+// Programmatic dependent launch (the kernels of a step, launched by launch_pdl): wait until the
+// previous kernel in the stream has completed and its writes are visible. Every such kernel calls
+// this before its first memory access (a no-op for a kernel launched without the attribute). No
+// kernel triggers its dependents early: they launch as its CTAs exit, so no CTA of a later kernel
+// shares an SM's L1 with a CTA that may still read data the kernel in between rewrites.
+__device__ __forceinline__ void grid_dep_sync() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 struct SegCursor {
     const int* start;
     const int* src;
@@ -422,7 +429,8 @@ __device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, doub
 // slice sums of parity par, the new counts and segment counts, the newborn
 // segment and its first_seg entries, on a full step the per-period mean
 // counts; then the slice sums of the other parity cleared for the next sweep.
-__device__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, int par, bool full_step, int& err) {
+__device__ __forceinline__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, int par, bool full_step,
+                                             int& err) {
     const int TILE = D.tile, CHUNK = D.chunk;
     long long chunks[2], slices[2];
     for (int sp = 0; sp < 2; ++sp) {
@@ -556,6 +564,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     __shared__ int s_err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    grid_dep_sync();
     if (tid == 0) {
         long long acc = 0;
         for (int s = 0; s < 2 * n_disc; ++s) {
@@ -834,63 +843,69 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
 
 
 // ---------------------------------------------------------------------------
-// Integer prefix segment of the Poisson sums for both species: r = sum of
-// deposits, s = sum of the running r, L = elements. Segment A followed by B:
-// (r_A + r_B, s_A + L_B r_A + s_B, L_A + L_B); exact, so any order gives the same.
-struct ISeg {
-    long long r[2];
-    __int128 s[2];
-    int L;
+// Exact prefix terms of the Poisson solve for both species over a run of nodes: r = sum of the
+// deposits D_k, m = sum of k D_k. With R_j = sum_{1<=k<=j} D_k and M_j = sum_{1<=k<=j} k D_k the
+// double sum S_{j+1} = sum_{i<=j} R_i equals (j + 1) R_j - M_j, so one scan of plain integer sums
+// gives both R and S (no products inside the scan; integer, so any order gives the same).
+struct PSum {
+    unsigned long long r[2];
+    unsigned __int128 m[2];
 };
-__device__ __forceinline__ ISeg iseg_join(const ISeg& a, const ISeg& b) {
-    ISeg c;
+__device__ __forceinline__ void psum_add(PSum& a, const PSum& b) {
+#pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-        c.r[sp] = a.r[sp] + b.r[sp];
-        c.s[sp] = a.s[sp] + (__int128)b.L * a.r[sp] + b.s[sp];
+        a.r[sp] += b.r[sp];
+        a.m[sp] += b.m[sp];
     }
-    c.L = a.L + b.L;
-    return c;
 }
-__device__ __forceinline__ ISeg iseg_shfl_up(const ISeg& x, int o) {
-    ISeg y;
+__device__ __forceinline__ PSum psum_shfl_up(const PSum& x, int o) {
+    PSum y;
+#pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
         y.r[sp] = __shfl_up_sync(FULL, x.r[sp], o);
-        const unsigned long long lo = __shfl_up_sync(FULL, (unsigned long long)x.s[sp], o);
-        const long long hi = __shfl_up_sync(FULL, (long long)(x.s[sp] >> 64), o);
-        y.s[sp] = ((__int128)hi << 64) | (__int128)lo;
+        const unsigned long long lo = __shfl_up_sync(FULL, (unsigned long long)x.m[sp], o);
+        const unsigned long long hi = __shfl_up_sync(FULL, (unsigned long long)(x.m[sp] >> 64), o);
+        y.m[sp] = ((unsigned __int128)hi << 64) | lo;
     }
-    y.L = __shfl_up_sync(FULL, x.L, o);
     return y;
 }
-// Exclusive block scan of one ISeg per thread (s_w: 32 entries).
-template <int BLOCK>
-__device__ ISeg block_exclusive_iseg(const ISeg& own, ISeg* s_w) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = BLOCK / 32;
-    ISeg x = own;
-#pragma unroll
+// Exclusive scan of one PSum per thread over the first NT threads of the block (NT / 32 warps,
+// named barrier 1; the other warps of the block do not take part). s_w: NT / 32 entries.
+template <int NT>
+__device__ __forceinline__ PSum block_exclusive_psum(const PSum& own, PSum* s_w, int lane, int warp) {
+    constexpr int NW = NT / 32;
+    PSum x = own;
+#pragma unroll 1
     for (int o = 1; o < 32; o <<= 1) {
-        const ISeg y = iseg_shfl_up(x, o);
-        if (lane >= o) x = iseg_join(y, x);
+        const PSum y = psum_shfl_up(x, o);
+        if (lane >= o) psum_add(x, y);
     }
-    ISeg e = iseg_shfl_up(x, 1);
-    if (lane == 0) e = ISeg{};
     if (lane == 31) s_w[warp] = x;
-    __syncthreads();
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
     if (warp == 0) {
-        ISeg w = lane < NW ? s_w[lane] : ISeg{};
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const ISeg y = iseg_shfl_up(w, o);
-            if (lane >= o) w = iseg_join(y, w);
+        const PSum v = lane < NW ? s_w[lane] : PSum{};
+        PSum w = v;
+#pragma unroll 1
+        for (int o = 1; o < NW; o <<= 1) {
+            const PSum y = psum_shfl_up(w, o);
+            if (lane >= o) psum_add(w, y);
         }
-        ISeg p = iseg_shfl_up(w, 1);
-        if (lane == 0) p = ISeg{};
-        if (lane < NW) s_w[lane] = p;
+        if (lane < NW) {
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {  // inclusive -> exclusive
+                w.r[sp] -= v.r[sp];
+                w.m[sp] -= v.m[sp];
+            }
+            s_w[lane] = w;
+        }
     }
-    __syncthreads();
-    const ISeg r = iseg_join(s_w[warp], e);
-    __syncthreads();
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    PSum r = s_w[warp];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {  // + this warp's inclusive sum before the thread
+        r.r[sp] += x.r[sp] - own.r[sp];
+        r.m[sp] += x.m[sp] - own.m[sp];
+    }
     return r;
 }
 // Nearest double of a 128-bit integer below 2^115 in magnitude (two roundings at most).
@@ -909,14 +924,43 @@ __device__ __forceinline__ double i128_to_double(__int128 x) {
 // step; 4 initial solve at t = n dt (load); 8 segments only (no solve,
 // deposits kept). The last CTA to finish advances the step (mode bit 2).
 template <int BLOCK>
-__device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int out_buf, int tid, int lane,
+__device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int out_buf, int tid, int lane,
                           int warp) {
     constexpr int K = SLICE / BLOCK, NW = BLOCK / 32;
+    static_assert(SLICE % BLOCK == 0 && NW <= 32 && NW >= 3, "seg_apply block shape");
+    using R = float4;
     __shared__ int s_w[3][NW];
+    // the slice's chunk counts (each at most one chunk of slots: 16 bits) and segment starts,
+    // staged so that global loads and stores are coalesced while every thread scans K
+    // consecutive chunks
+    __shared__ unsigned short s_cnt[3][SLICE];
+    __shared__ int s_st[SLICE];
     const int d = blockIdx.y >> 1, sp = blockIdx.y & 1;
     const Disc& D = discs[d];
-    const int TILE = D.tile, CHUNK = D.chunk;
-    const long long chunks = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
+    // every field is read before the first store (the stores could otherwise alias them)
+    const int TILE = D.tile, CHUNK = D.chunk, WARPS = D.warps;
+    const int* __restrict__ cnt_m = D.cnt_main[sp];
+    const int* __restrict__ cnt_b = D.cnt_birth[sp];
+    const int* __restrict__ cnt_s = D.cnt_same;
+    int* __restrict__ st = D.seg_start[sp];
+    int* __restrict__ sr = D.seg_src[sp];
+    int* __restrict__ fs = D.first_seg[sp];
+    const long long jmax = D.max_tiles[sp] * WARPS;
+    const int q = 1 - sp;  // store of the other-species newborns
+    const long long bcap = D.bcap;
+    const int rw = D.rec_words;  // record size in 16-byte words
+    int32_t* __restrict__ oc_q = D.c[out_buf][q] + D.R0[q];
+    R* __restrict__ op_q = reinterpret_cast<R*>(D.p[out_buf][q]) + D.R0[q] * rw;
+    int32_t* __restrict__ oc_0 = D.c[out_buf][0] + D.R0[0];
+    R* __restrict__ op_0 = reinterpret_cast<R*>(D.p[out_buf][0]) + D.R0[0] * rw;
+    const int32_t* __restrict__ bc = D.bc[sp];
+    const R* __restrict__ bp = reinterpret_cast<const R*>(D.bp[sp]);
+    const int32_t* __restrict__ sc = D.sc;
+    const R* __restrict__ spr = reinterpret_cast<const R*>(D.sp_);
+    const unsigned* __restrict__ slice0 = D.slice_tot[0];
+    const unsigned* __restrict__ slice_s = D.slice_tot[sp];
+    const int sn0 = D.slice_n[0], sn_s = D.slice_n[sp];
+    const long long chunks = (ctl->count_in[d][sp] + TILE - 1) / TILE * WARPS;
     const long long t0 = (long long)blockIdx.x * SLICE;
     if (t0 >= chunks) return;
     // output offsets of this slice: the sums of the slices before it (survivors, other-species
@@ -925,7 +969,7 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
     __shared__ long long s_pre[3];
     if (warp == 0) {
         const int par = ctl->slice_par;
-        const unsigned* Tp = D.slice_tot[sp] + (size_t)par * 3 * D.slice_n[sp];
+        const unsigned* Tp = slice_s + (size_t)par * 3 * sn_s;
         long long a = 0, b = 0, c = 0;
         for (int k = lane; k < (int)blockIdx.x; k += 32) {
             a += Tp[3 * k + 0];
@@ -933,8 +977,8 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
             c += Tp[3 * k + 2];
         }
         if (sp == 1) {
-            const long long ch0 = (ctl->count_in[d][0] + TILE - 1) / TILE * D.warps;
-            const unsigned* T0 = D.slice_tot[0] + (size_t)par * 3 * D.slice_n[0];
+            const long long ch0 = (ctl->count_in[d][0] + TILE - 1) / TILE * WARPS;
+            const unsigned* T0 = slice0 + (size_t)par * 3 * sn0;
             for (long long k = lane; k < (ch0 + SLICE - 1) / SLICE; k += 32) b += T0[3 * k + 2];
         }
 #pragma unroll
@@ -949,15 +993,23 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
             s_pre[2] = c;
         }
     }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int k = i * BLOCK + tid;
+        const bool in = t0 + k < chunks;
+        s_cnt[0][k] = (unsigned short)(in ? cnt_m[t0 + k] : 0);
+        s_cnt[1][k] = (unsigned short)(in ? cnt_b[t0 + k] : 0);
+        s_cnt[2][k] = (unsigned short)((in && sp == 0) ? cnt_s[t0 + k] : 0);
+    }
+    __syncthreads();
     const long long tb = t0 + (long long)tid * K;
     int cm[K], cb[K], cs[K];
     int rm = 0, rb = 0, rs = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const bool in = tb + i < chunks;
-        cm[i] = in ? D.cnt_main[sp][tb + i] : 0;
-        cb[i] = in ? D.cnt_birth[sp][tb + i] : 0;
-        cs[i] = (in && sp == 0) ? D.cnt_same[tb + i] : 0;
+        cm[i] = s_cnt[0][tid * K + i];
+        cb[i] = s_cnt[1][tid * K + i];
+        cs[i] = s_cnt[2][tid * K + i];
         rm += cm[i];
         rb += cb[i];
         rs += cs[i];
@@ -978,42 +1030,33 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
         s_w[2][warp] = xs;
     }
     __syncthreads();
-    if (warp < 3) {
-        const int v = s_w[warp][lane];
+    if (warp < 3) {  // warp k scans the NW warp sums of count k (NW <= 32)
+        const int v = lane < NW ? s_w[warp][lane] : 0;
         int x = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
+        for (int o = 1; o < NW; o <<= 1) {
             const int y = __shfl_up_sync(FULL, x, o);
             if (lane >= o) x += y;
         }
-        s_w[warp][lane] = x - v;
+        if (lane < NW) s_w[warp][lane] = x - v;
     }
     __syncthreads();
     long long em = s_pre[0] + s_w[0][warp] + xm - rm;
     long long eb = s_pre[1] + s_w[1][warp] + xb - rb;
     long long es = s_pre[2] + s_w[2][warp] + xs - rs;
-    using R = float4;
-    int* st = D.seg_start[sp];
-    int* sr = D.seg_src[sp];
-    int* fs = D.first_seg[sp];
-    const long long jmax = (long long)D.max_tiles[sp] * D.warps;
-    const int q = 1 - sp;  // store of the other-species newborns
-    const long long bcap = D.bcap;
-    const int rw = D.rec_words;  // record size in 16-byte words
     int err = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const long long t = tb + i;
+        s_st[tid * K + i] = (int)em;
         if (t < chunks) {
-            st[t] = (int)em;
-            sr[t] = (int)(t * CHUNK);
             for (long long j = (em + CHUNK - 1) / CHUNK; j * CHUNK < em + cm[i] && j <= jmax; ++j) fs[j] = (int)t;
             for (int k = 0; k < cb[i]; ++k) {
                 const long long o = eb + k;
                 if (o < bcap) {
-                    D.c[out_buf][q][D.R0[q] + o] = D.bc[sp][t * CHUNK + k];
-                    const R* src = reinterpret_cast<const R*>(D.bp[sp]) + (t * CHUNK + k) * rw;
-                    R* dst = reinterpret_cast<R*>(D.p[out_buf][q]) + (D.R0[q] + o) * rw;
+                    oc_q[o] = bc[t * CHUNK + k];
+                    const R* src = bp + (t * CHUNK + k) * rw;
+                    R* dst = op_q + o * rw;
                     for (int w = 0; w < rw; ++w) dst[w] = src[w];
                 } else {
                     err = ERR_CAPACITY;
@@ -1022,9 +1065,9 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
             for (int k = 0; k < cs[i]; ++k) {
                 const long long o = es + k;
                 if (o < bcap) {
-                    D.c[out_buf][0][D.R0[0] + o] = D.sc[t * CHUNK + k];
-                    const R* src = reinterpret_cast<const R*>(D.sp_) + (t * CHUNK + k) * rw;
-                    R* dst = reinterpret_cast<R*>(D.p[out_buf][0]) + (D.R0[0] + o) * rw;
+                    oc_0[o] = sc[t * CHUNK + k];
+                    const R* src = spr + (t * CHUNK + k) * rw;
+                    R* dst = op_0 + o * rw;
                     for (int w = 0; w < rw; ++w) dst[w] = src[w];
                 } else {
                     err = ERR_CAPACITY;
@@ -1035,17 +1078,145 @@ __device__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
         eb += cb[i];
         es += cs[i];
     }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < K; ++i) {  // segment entries, coalesced
+        const int k = i * BLOCK + tid;
+        if (t0 + k < chunks) {
+            st[t0 + k] = s_st[k];
+            sr[t0 + k] = (int)((t0 + k) * CHUNK);
+        }
+    }
     if (err) atomicOr(&ctl->error, err);
 }
 
+// Field of one discharge after its deposits are complete (the field role of k_post; all
+// POST_BLOCK threads of the CTA). Poisson, Eq. (poisson): phi_{j-1} - 2 phi_j + phi_{j+1} = -r_j with
+// r_j = rho_j dx^2 / eps0, phi_0 = V_rf sin(2 pi f t), phi_N = 0. With R_j = sum_{k<=j} r_k and
+// S_j = sum_{i<j} R_i: phi_j = phi_0 + j g_1 - S_j, g_1 = (phi_N - phi_0 + S_N) / N. R and S are
+// linear in the deposits: R_j = c_i IR_i,j - c_e IR_e,j, S_{j+1} = c_i IS_i,j - c_e IS_e,j with the
+// exact integer sums IR_s,j = sum_{1<=k<=j} D_s,k (64 bits: a store holds below 2^30 particles of
+// 2^32 each) and IS_s,j = sum_{i<=j} IR_s,i (128 bits), from one scan of plain sums (PSum). FP64
+// (slow on this part) is used once per node, with no division (host reciprocals).
+constexpr int POST_BLOCK = 512;  // threads per k_post CTA
+constexpr int FIELD_SCAN = 256;  // threads of the integer scan
 template <typename T>
-__global__ void __launch_bounds__(1024) k_post(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
-                                               int out_buf, int mode, int nsl, int max_N) {
-    constexpr int BLOCK = 1024;
+__device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restrict__ ctl, int mode, int tid, int lane,
+                                            int warp, double* s_f, int max_N, PSum* s_ps) {
+    constexpr int BLOCK = POST_BLOCK;
+    // every field of the discharge is read before the first store
+    const int N = D.N;
+    unsigned long long* __restrict__ De = D.D[0];
+    unsigned long long* __restrict__ Di = D.D[1];
+    unsigned long long* __restrict__ Qd = D.Q;
+    unsigned long long* __restrict__ Dp = D.Dprev;
+    unsigned __int128* __restrict__ aDe = D.acc_D[0];
+    unsigned __int128* __restrict__ aDi = D.acc_D[1];
+    unsigned __int128* __restrict__ aQ = D.acc_Q;
+    unsigned __int128* __restrict__ aDp = D.acc_Dprev;
+    double* __restrict__ phi = D.phi;
+    double* __restrict__ E64 = D.E64;
+    T* __restrict__ Ef = reinterpret_cast<T*>(D.E);
+    const double pr0 = D.pc_r[0], pr1 = D.pc_r[1], pw0 = D.pc_w[0], pw1 = D.pc_w[1];
+    const double inv_dx = D.inv_dx, m_inv_2dx = D.m_inv_2dx, hdx_eps = D.hdx_eps, inv_N = D.inv_N;
+    const long long step = ctl->step;
+    const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
+    const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
+                              : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
+    // stage the deposits in shared memory (no global store before the solve: the stores of the
+    // moments and of the cleared deposits come last)
+    unsigned long long* sde = reinterpret_cast<unsigned long long*>(s_f);
+    unsigned long long* sdi = sde + (max_N + 1);
+    __shared__ unsigned long long s_wall[4];  // D_e,0, D_i,0, D_e,N, D_i,N
+    for (int j = tid; j <= N; j += BLOCK) {
+        const unsigned long long de = De[j], di = Di[j];
+        sde[j] = de;
+        sdi[j] = di;
+        if (j == 0 || j == N) {
+            s_wall[j == 0 ? 0 : 2] = de;
+            s_wall[j == 0 ? 1 : 3] = di;
+        }
+    }
+    __syncthreads();
+    // R_j and S_{j+1} for j < N (node 0 carries no deposit term); Rr / Sx overwrite the staged
+    // deposits node by node, each node read and written by the same thread
+    double* Rr = s_f;                // R_j
+    double* Sx = s_f + (max_N + 1);  // S_{j+1}
+    if (tid < FIELD_SCAN) {
+        const int per = (N + FIELD_SCAN - 1) / FIELD_SCAN;
+        const int lo = min(N, tid * per), hi = min(N, lo + per);
+        PSum own{};
+        for (int j = max(lo, 1); j < hi; ++j) {
+            own.r[0] += sde[j];
+            own.r[1] += sdi[j];
+            own.m[0] += (unsigned __int128)j * sde[j];
+            own.m[1] += (unsigned __int128)j * sdi[j];
+        }
+        PSum run = block_exclusive_psum<FIELD_SCAN>(own, s_ps, lane, warp);
+        for (int j = lo; j < hi; ++j) {
+            if (j >= 1) {
+                const unsigned long long e = sde[j], i = sdi[j];
+                run.r[0] += e;
+                run.r[1] += i;
+                run.m[0] += (unsigned __int128)j * e;
+                run.m[1] += (unsigned __int128)j * i;
+            }
+            const __int128 S0 = (__int128)((unsigned __int128)(j + 1) * run.r[0] - run.m[0]);
+            const __int128 S1 = (__int128)((unsigned __int128)(j + 1) * run.r[1] - run.m[1]);
+            Rr[j] = __fma_rn(pr1, (double)(long long)run.r[1], -pr0 * (double)(long long)run.r[0]);
+            Sx[j] = __fma_rn(pr1, i128_to_double(S1), -pr0 * i128_to_double(S0));
+        }
+    }
+    __syncthreads();
+    const double SN = N > 0 ? Sx[N - 1] : 0.0;
+    const double g1 = (SN - V0) * inv_N;
+    // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
+    // (the central difference of phi, without the cancellation of large phi values), and Gauss's
+    // law over the half cells at the electrodes.
+    for (int j = tid; j <= N; j += BLOCK) {
+        double ph = V0 + (double)j * g1 - (j == 0 ? 0.0 : Sx[j - 1]);
+        if (j == N) ph = 0.0;
+        if (j == 0) ph = V0;
+        double E;
+        if (j == 0 || j == N) {
+            const int w = j == 0 ? 0 : 2;
+            const double rw = __fma_rn(pw1, (double)s_wall[w + 1], -pw0 * (double)s_wall[w]);
+            E = j == 0 ? -g1 * inv_dx - rw * hdx_eps : -(g1 - Rr[N - 1]) * inv_dx + rw * hdx_eps;
+        } else {
+            E = ((g1 - Rr[j - 1]) + (g1 - Rr[j])) * m_inv_2dx;
+        }
+        phi[j] = ph;
+        E64[j] = E;
+        Ef[j] = (T)E;
+        if (j == 0) ctl->E0_last[d] = E;
+    }
+    // accumulate the moments (mode bit 2) and hand the next sweep zeroed deposit arrays
+    for (int j = tid; j <= N; j += BLOCK) {
+        const unsigned long long de = De[j], di = Di[j], q = Qd[j], dp = Dp[j];
+        if (mode & 2) {
+            const unsigned __int128 a0 = aDe[j], a1 = aDi[j], aq = aQ[j], ap = aDp[j];
+            aDe[j] = a0 + de;
+            aDi[j] = a1 + di;
+            aQ[j] = aq + q;
+            aDp[j] = ap + dp;
+        }
+        Dp[j] = de;
+        De[j] = 0;
+        Di[j] = 0;
+        Qd[j] = 0;
+    }
+    if (tid == 0 && (mode & 2)) ctl->acc_steps[d] += 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
+                                                     int out_buf, int mode, int nsl, int max_N) {
+    constexpr int BLOCK = POST_BLOCK;
     extern __shared__ __align__(16) double s_f[];
-    __shared__ ISeg s_iseg[32];
+    __shared__ PSum s_ps[FIELD_SCAN / 32];
     __shared__ int s_err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    grid_dep_sync();
     if (tid == 0) s_err = 0;
     __syncthreads();
     if ((int)blockIdx.x < nsl) {
@@ -1057,89 +1228,7 @@ __global__ void __launch_bounds__(1024) k_post(const Disc* __restrict__ discs, i
             if (e2 && lane == 0) atomicOr(&s_err, e2);
         }
     } else if (!(mode & 8) && (blockIdx.y & 1) == 0) {
-        const int d = blockIdx.y >> 1;
-        const Disc& D = discs[d];
-        const int N = D.N;
-        // Poisson, Eq. (poisson): phi_{j-1} - 2 phi_j + phi_{j+1} = -r_j, r_j = rho_j dx^2 / eps0,
-        // phi_0 = V_rf sin(2 pi f t), phi_N = 0. With R_j = sum_{k<=j} r_k and S_j = sum_{i<j} R_i:
-        // phi_j = phi_0 + j g_1 - S_j, g_1 = (phi_N - phi_0 + S_N) / N. FP64 latency is long on this
-        // part, so the dependent chain is kept short: one scan of (R, S) pairs, no division.
-        double* Rr = s_f;                  // R_j
-        double* Sx = s_f + (max_N + 1);    // S_{j+1}
-        const long long step = ctl->step;
-        const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
-        const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
-                                  : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
-        // R and S are linear in the deposits: R_j = c_i IR_i,j - c_e IR_e,j and S_{j+1} = c_i IS_i,j -
-        // c_e IS_e,j with the exact integer sums IR_s,j = sum_{1<=k<=j} D_s,k (64 bits: a store holds
-        // below 2^30 particles of 2^32 each) and IS_s,j = sum_{i<=j} IR_s,i (128 bits). The scans are
-        // integer; FP64 (slow on this part) is used once per node.
-        {
-            const int per = (N + BLOCK - 1) / BLOCK;
-            const int lo = min(N, tid * per), hi = min(N, lo + per);
-            long long dv[2][4];
-            ISeg own{};
-            for (int i = 0; i < 4; ++i)
-                if (i < hi - lo) {
-                    const int j = lo + i;
-                    for (int sp = 0; sp < 2; ++sp) {
-                        dv[sp][i] = j >= 1 ? (long long)D.D[sp][j] : 0;
-                        own.r[sp] += dv[sp][i];
-                        own.s[sp] += own.r[sp];
-                    }
-                }
-            own.L = hi - lo;
-            const ISeg pre = block_exclusive_iseg<BLOCK>(own, s_iseg);
-            ISeg run = pre;
-            for (int i = 0; i < 4; ++i)
-                if (i < hi - lo) {
-                    const int j = lo + i;
-                    for (int sp = 0; sp < 2; ++sp) {
-                        run.r[sp] += dv[sp][i];
-                        run.s[sp] += run.r[sp];
-                    }
-                    Rr[j] = __fma_rn(D.pc_r[1], (double)run.r[1], -D.pc_r[0] * (double)run.r[0]);
-                    Sx[j] = __fma_rn(D.pc_r[1], i128_to_double(run.s[1]), -D.pc_r[0] * i128_to_double(run.s[0]));
-                }
-            __syncthreads();
-        }
-        const double SN = N > 0 ? Sx[N - 1] : 0.0;
-        const double g1 = (SN - V0) * D.inv_N;
-        // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
-        // (the central difference of phi, without the cancellation of large phi values), and Gauss's
-        // law over the half cells at the electrodes.
-        double* phi = D.phi;
-        for (int j = tid; j <= N; j += BLOCK) {
-            double ph = V0 + (double)j * g1 - (j == 0 ? 0.0 : Sx[j - 1]);
-            if (j == N) ph = 0.0;
-            if (j == 0) ph = V0;
-            phi[j] = ph;
-            double E;
-            if (j == 0 || j == N) {
-                const double rw = __fma_rn(D.pc_w[1], (double)D.D[1][j], -D.pc_w[0] * (double)D.D[0][j]);
-                E = j == 0 ? -g1 * D.inv_dx - rw * D.hdx_eps : -(g1 - Rr[N - 1]) * D.inv_dx + rw * D.hdx_eps;
-            } else {
-                E = ((g1 - Rr[j - 1]) + (g1 - Rr[j])) * D.m_inv_2dx;
-            }
-            D.E64[j] = E;
-            reinterpret_cast<T*>(D.E)[j] = (T)E;
-            if (j == 0) ctl->E0_last[d] = E;
-        }
-        if (mode & 2) {
-            for (int j = tid; j <= N; j += BLOCK) {
-                D.acc_D[0][j] += D.D[0][j];
-                D.acc_D[1][j] += D.D[1][j];
-                D.acc_Q[j] += D.Q[j];
-                D.acc_Dprev[j] += D.Dprev[j];
-            }
-            if (tid == 0) ctl->acc_steps[d] += 1;
-        }
-        for (int j = tid; j <= N; j += BLOCK) {
-            D.Dprev[j] = D.D[0][j];
-            D.D[0][j] = 0;
-            D.D[1][j] = 0;
-            D.Q[j] = 0;
-        }
+        field_solve<T>(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, mode, tid, lane, warp, s_f, max_N, s_ps);
     }
     __syncthreads();
     if (tid == 0) {  // the last CTA advances the step (bit 2) and, after a sweep, the slice parity
@@ -1332,6 +1421,7 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restric
                                                            const long long* __restrict__ hoff,
                                                            unsigned* __restrict__ kr_all, unsigned* __restrict__ off_all,
                                                            const long long* __restrict__ eoff, int max_N) {
+    grid_dep_sync();
     extern __shared__ __align__(16) unsigned s_w[];  // [SORT_NW][max_N] per-warp counts, then prefixes
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
@@ -1406,6 +1496,7 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restric
 __global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                     unsigned* __restrict__ hist, const long long* __restrict__ hoff,
                                                     unsigned* __restrict__ tot) {
+    grid_dep_sync();
     __shared__ unsigned s_sum[32][33];
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const int N = discs[d].N;
@@ -1434,6 +1525,7 @@ __global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ dis
 
 // Per store: exclusive scan of the row totals -> first slot of every cell.
 __global__ void __launch_bounds__(1024) k_sort_cells(const Disc* __restrict__ discs, unsigned* __restrict__ tot) {
+    grid_dep_sync();
     const int seg = blockIdx.x, d = seg >> 1;
     const int N = discs[d].N;
     unsigned* a = tot + (long long)seg * MAXN;
@@ -1481,6 +1573,7 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
                                                              const unsigned* __restrict__ kr_all,
                                                              const unsigned* __restrict__ off_all,
                                                              const long long* __restrict__ eoff) {
+    grid_dep_sync();
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
     const int N = D.N;
@@ -1548,6 +1641,7 @@ __global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __rest
 
 // Every store becomes one dense segment [0, count) (after a load, an upload or a sort).
 __global__ void k_set_dense(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl) {
+    grid_dep_sync();
     const int i = threadIdx.x;
     if (i >= 2 * n_disc) return;
     const int d = i >> 1, sp = i & 1;
@@ -1613,13 +1707,35 @@ static cudaError_t smem_attr(K kern, size_t smem) {
     return e;
 }
 
+// Launch with programmatic stream serialization: the grid may be scheduled while the kernel before
+// it in the stream is still finishing (it takes SMs as they free up), and every such kernel starts
+// with grid_dep_wait(), which returns once that kernel has completed and its memory is visible. So
+// the kernel-to-kernel gap of a step shrinks while the ordering stays that of plain launches.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename T, int BLOCK, int PPT>
 static cudaError_t launch_sweep_t(const SweepLaunch& L) {
     const size_t smem = sweep_smem<T, BLOCK, PPT>(L.max_N);
     auto kern = k_sweep<T, BLOCK, PPT>;
     cudaError_t e = smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<L.grid, BLOCK, smem, L.stream>>>(L.discs, L.n_disc, L.ctl, L.in_buf, L.seed, L.max_N);
+    e = launch_pdl(kern, dim3(L.grid), dim3(BLOCK), smem, L.stream, L.discs, L.n_disc, L.ctl, L.in_buf, L.seed,
+                   L.max_N);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1669,12 +1785,13 @@ cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, i
     const dim3 grid(nsl + 1, 2 * n_disc);
     if (fp64) {
         smem_attr(k_post<double>, smem);
-        k_post<double><<<grid, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode, nsl, max_N);
+        return launch_pdl(k_post<double>, grid, dim3(POST_BLOCK), smem, st, discs, n_disc, ctl, out_buf, mode, nsl,
+                          max_N);
     } else {
         smem_attr(k_post<float>, smem);
-        k_post<float><<<grid, 1024, smem, st>>>(discs, n_disc, ctl, out_buf, mode, nsl, max_N);
+        return launch_pdl(k_post<float>, grid, dim3(POST_BLOCK), smem, st, discs, n_disc, ctl, out_buf, mode, nsl,
+                          max_N);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_load(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
@@ -1750,19 +1867,24 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
     const size_t smem = sizeof(unsigned) * SORT_NW * max_N;
     cudaError_t e = smem_attr(k_sort_count, smem);
     if (e != cudaSuccess) return e;
-    k_sort_count<<<g, SORT_BLOCK, smem, st>>>(discs, ctl, src, hist, hoff, kr, off, eoff, max_N);
+    e = launch_pdl(k_sort_count, g, dim3(SORT_BLOCK), smem, st, discs, ctl, src, hist, hoff, kr, off, eoff, max_N);
+    if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sort_rows<<<dim3((max_N + 31) / 32, 2 * n_disc), 1024, 0, st>>>(discs, ctl, hist, hoff, tot);
+    e = launch_pdl(k_sort_rows, dim3((max_N + 31) / 32, 2 * n_disc), dim3(1024), 0, st, discs, ctl, hist, hoff, tot);
+    if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sort_cells<<<2 * n_disc, 1024, 0, st>>>(discs, tot);
+    e = launch_pdl(k_sort_cells, dim3(2 * n_disc), dim3(1024), 0, st, discs, tot);
+    if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 gs(4 * grid_x, 2 * n_disc);
-    if (fp64) k_sort_scatter<double><<<gs, SORT_BLOCK, 0, st>>>(discs, ctl, src, dst, hist, hoff, tot, kr, off, eoff);
-    else k_sort_scatter<float><<<gs, SORT_BLOCK, 0, st>>>(discs, ctl, src, dst, hist, hoff, tot, kr, off, eoff);
-    return cudaGetLastError();
+    if (fp64)
+        return launch_pdl(k_sort_scatter<double>, gs, dim3(SORT_BLOCK), 0, st, discs, ctl, src, dst, hist, hoff, tot, kr,
+                          off, eoff);
+    return launch_pdl(k_sort_scatter<float>, gs, dim3(SORT_BLOCK), 0, st, discs, ctl, src, dst, hist, hoff, tot, kr, off,
+                      eoff);
 }
 
 cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
@@ -1783,8 +1905,7 @@ cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int
 long long sort_tile() { return SORT_TILE; }
 
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st) {
-    k_set_dense<<<1, 128, 0, st>>>(discs, n_disc, ctl);
-    return cudaGetLastError();
+    return launch_pdl(k_set_dense, dim3(1), dim3(128), 0, st, discs, n_disc, ctl);
 }
 
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
