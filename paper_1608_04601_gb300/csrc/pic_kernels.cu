@@ -829,14 +829,14 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     if (cur_seg >= 0) flush();
     if (err) atomicOr(&s_err, err);
     __syncthreads();
+    // the last CTA snapshots the counts the sweep read; it uses no other CTA's results (the counts
+    // do not change during the sweep), so no fence: the kernel boundary publishes everything
     if (tid == 0) {
         if (s_err) atomicOr(&ctl->error, s_err);
-        __threadfence();
         const unsigned prev = atomicAdd(&ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             for (int i = 0; i < 2 * n_disc; ++i) ctl->count_in[i >> 1][i & 1] = ctl->count[i >> 1][i & 1];
             ctl->done = 0;
-            __threadfence();
         }
     }
 }
@@ -870,9 +870,10 @@ __device__ __forceinline__ PSum psum_shfl_up(const PSum& x, int o) {
     return y;
 }
 // Exclusive scan of one PSum per thread over the first NT threads of the block (NT / 32 warps,
-// named barrier 1; the other warps of the block do not take part). s_w: NT / 32 entries.
+// named barrier 1; the other warps of the block do not take part), and the total over all of
+// them. s_w: NT / 32 + 1 entries.
 template <int NT>
-__device__ __forceinline__ PSum block_exclusive_psum(const PSum& own, PSum* s_w, int lane, int warp) {
+__device__ __forceinline__ PSum block_exclusive_psum(const PSum& own, PSum* s_w, int lane, int warp, PSum& total) {
     constexpr int NW = NT / 32;
     PSum x = own;
 #pragma unroll 1
@@ -890,6 +891,7 @@ __device__ __forceinline__ PSum block_exclusive_psum(const PSum& own, PSum* s_w,
             const PSum y = psum_shfl_up(w, o);
             if (lane >= o) psum_add(w, y);
         }
+        if (lane == NW - 1) s_w[NW] = w;
         if (lane < NW) {
 #pragma unroll
             for (int sp = 0; sp < 2; ++sp) {  // inclusive -> exclusive
@@ -900,6 +902,7 @@ __device__ __forceinline__ PSum block_exclusive_psum(const PSum& own, PSum* s_w,
         }
     }
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    total = s_w[NW];
     PSum r = s_w[warp];
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {  // + this warp's inclusive sum before the thread
@@ -930,11 +933,9 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
     static_assert(SLICE % BLOCK == 0 && NW <= 32 && NW >= 3, "seg_apply block shape");
     using R = float4;
     __shared__ int s_w[3][NW];
-    // the slice's chunk counts (each at most one chunk of slots: 16 bits) and segment starts,
-    // staged so that global loads and stores are coalesced while every thread scans K
-    // consecutive chunks
+    // the slice's chunk counts (each at most one chunk of slots: 16 bits), loaded coalesced while
+    // every thread scans K consecutive chunks
     __shared__ unsigned short s_cnt[3][SLICE];
-    __shared__ int s_st[SLICE];
     const int d = blockIdx.y >> 1, sp = blockIdx.y & 1;
     const Disc& D = discs[d];
     // every field is read before the first store (the stores could otherwise alias them)
@@ -1003,16 +1004,12 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
     }
     __syncthreads();
     const long long tb = t0 + (long long)tid * K;
-    int cm[K], cb[K], cs[K];
     int rm = 0, rb = 0, rs = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        cm[i] = s_cnt[0][tid * K + i];
-        cb[i] = s_cnt[1][tid * K + i];
-        cs[i] = s_cnt[2][tid * K + i];
-        rm += cm[i];
-        rb += cb[i];
-        rs += cs[i];
+        rm += s_cnt[0][tid * K + i];
+        rb += s_cnt[1][tid * K + i];
+        rs += s_cnt[2][tid * K + i];
     }
     int xm = rm, xb = rb, xs = rs;
 #pragma unroll
@@ -1045,13 +1042,15 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
     long long eb = s_pre[1] + s_w[1][warp] + xb - rb;
     long long es = s_pre[2] + s_w[2][warp] + xs - rs;
     int err = 0;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) {  // rolled: this code runs once per step, from a cold instruction cache
         const long long t = tb + i;
-        s_st[tid * K + i] = (int)em;
+        const int cm = s_cnt[0][tid * K + i], cb = s_cnt[1][tid * K + i], cs = s_cnt[2][tid * K + i];
         if (t < chunks) {
-            for (long long j = (em + CHUNK - 1) / CHUNK; j * CHUNK < em + cm[i] && j <= jmax; ++j) fs[j] = (int)t;
-            for (int k = 0; k < cb[i]; ++k) {
+            st[t] = (int)em;
+            sr[t] = (int)(t * CHUNK);
+            for (long long j = (em + CHUNK - 1) / CHUNK; j * CHUNK < em + cm && j <= jmax; ++j) fs[j] = (int)t;
+            for (int k = 0; k < cb; ++k) {
                 const long long o = eb + k;
                 if (o < bcap) {
                     oc_q[o] = bc[t * CHUNK + k];
@@ -1062,7 +1061,7 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
                     err = ERR_CAPACITY;
                 }
             }
-            for (int k = 0; k < cs[i]; ++k) {
+            for (int k = 0; k < cs; ++k) {
                 const long long o = es + k;
                 if (o < bcap) {
                     oc_0[o] = sc[t * CHUNK + k];
@@ -1074,18 +1073,9 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
                 }
             }
         }
-        em += cm[i];
-        eb += cb[i];
-        es += cs[i];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < K; ++i) {  // segment entries, coalesced
-        const int k = i * BLOCK + tid;
-        if (t0 + k < chunks) {
-            st[t0 + k] = s_st[k];
-            sr[t0 + k] = (int)((t0 + k) * CHUNK);
-        }
+        em += cm;
+        eb += cb;
+        es += cs;
     }
     if (err) atomicOr(&ctl->error, err);
 }
@@ -1123,74 +1113,10 @@ __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restric
     const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
     const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
                               : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
-    // stage the deposits in shared memory (no global store before the solve: the stores of the
-    // moments and of the cleared deposits come last)
+    // one pass over the nodes: stage the deposits in shared memory, accumulate the moments (mode
+    // bit 2) and hand the next sweep zeroed deposit arrays
     unsigned long long* sde = reinterpret_cast<unsigned long long*>(s_f);
     unsigned long long* sdi = sde + (max_N + 1);
-    __shared__ unsigned long long s_wall[4];  // D_e,0, D_i,0, D_e,N, D_i,N
-    for (int j = tid; j <= N; j += BLOCK) {
-        const unsigned long long de = De[j], di = Di[j];
-        sde[j] = de;
-        sdi[j] = di;
-        if (j == 0 || j == N) {
-            s_wall[j == 0 ? 0 : 2] = de;
-            s_wall[j == 0 ? 1 : 3] = di;
-        }
-    }
-    __syncthreads();
-    // R_j and S_{j+1} for j < N (node 0 carries no deposit term); Rr / Sx overwrite the staged
-    // deposits node by node, each node read and written by the same thread
-    double* Rr = s_f;                // R_j
-    double* Sx = s_f + (max_N + 1);  // S_{j+1}
-    if (tid < FIELD_SCAN) {
-        const int per = (N + FIELD_SCAN - 1) / FIELD_SCAN;
-        const int lo = min(N, tid * per), hi = min(N, lo + per);
-        PSum own{};
-        for (int j = max(lo, 1); j < hi; ++j) {
-            own.r[0] += sde[j];
-            own.r[1] += sdi[j];
-            own.m[0] += (unsigned __int128)j * sde[j];
-            own.m[1] += (unsigned __int128)j * sdi[j];
-        }
-        PSum run = block_exclusive_psum<FIELD_SCAN>(own, s_ps, lane, warp);
-        for (int j = lo; j < hi; ++j) {
-            if (j >= 1) {
-                const unsigned long long e = sde[j], i = sdi[j];
-                run.r[0] += e;
-                run.r[1] += i;
-                run.m[0] += (unsigned __int128)j * e;
-                run.m[1] += (unsigned __int128)j * i;
-            }
-            const __int128 S0 = (__int128)((unsigned __int128)(j + 1) * run.r[0] - run.m[0]);
-            const __int128 S1 = (__int128)((unsigned __int128)(j + 1) * run.r[1] - run.m[1]);
-            Rr[j] = __fma_rn(pr1, (double)(long long)run.r[1], -pr0 * (double)(long long)run.r[0]);
-            Sx[j] = __fma_rn(pr1, i128_to_double(S1), -pr0 * i128_to_double(S0));
-        }
-    }
-    __syncthreads();
-    const double SN = N > 0 ? Sx[N - 1] : 0.0;
-    const double g1 = (SN - V0) * inv_N;
-    // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
-    // (the central difference of phi, without the cancellation of large phi values), and Gauss's
-    // law over the half cells at the electrodes.
-    for (int j = tid; j <= N; j += BLOCK) {
-        double ph = V0 + (double)j * g1 - (j == 0 ? 0.0 : Sx[j - 1]);
-        if (j == N) ph = 0.0;
-        if (j == 0) ph = V0;
-        double E;
-        if (j == 0 || j == N) {
-            const int w = j == 0 ? 0 : 2;
-            const double rw = __fma_rn(pw1, (double)s_wall[w + 1], -pw0 * (double)s_wall[w]);
-            E = j == 0 ? -g1 * inv_dx - rw * hdx_eps : -(g1 - Rr[N - 1]) * inv_dx + rw * hdx_eps;
-        } else {
-            E = ((g1 - Rr[j - 1]) + (g1 - Rr[j])) * m_inv_2dx;
-        }
-        phi[j] = ph;
-        E64[j] = E;
-        Ef[j] = (T)E;
-        if (j == 0) ctl->E0_last[d] = E;
-    }
-    // accumulate the moments (mode bit 2) and hand the next sweep zeroed deposit arrays
     for (int j = tid; j <= N; j += BLOCK) {
         const unsigned long long de = De[j], di = Di[j], q = Qd[j], dp = Dp[j];
         if (mode & 2) {
@@ -1204,8 +1130,71 @@ __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restric
         De[j] = 0;
         Di[j] = 0;
         Qd[j] = 0;
+        sde[j] = de;
+        sdi[j] = di;
     }
     if (tid == 0 && (mode & 2)) ctl->acc_steps[d] += 1;
+    __syncthreads();
+    if (tid >= FIELD_SCAN) return;
+    // thread t owns nodes [lo, hi); node 0 carries no deposit term; node N is done by the owner of N - 1
+    const int per = (N + FIELD_SCAN - 1) / FIELD_SCAN;
+    const int lo = min(N, tid * per), hi = min(N, lo + per);
+    PSum own{};
+    for (int j = max(lo, 1); j < hi; ++j) {
+        own.r[0] += sde[j];
+        own.r[1] += sdi[j];
+        own.m[0] += (unsigned __int128)j * sde[j];
+        own.m[1] += (unsigned __int128)j * sdi[j];
+    }
+    PSum tot;
+    PSum run = block_exclusive_psum<FIELD_SCAN>(own, s_ps, lane, warp, tot);
+    // R_j -> r_j sums in FP64 (Rr), S_{j+1} = (j + 1) R_j - M_j -> FP64 (Sx), as c_i x_i - c_e x_e
+    auto Rr_of = [&](const PSum& p) {
+        return __fma_rn(pr1, (double)(long long)p.r[1], -pr0 * (double)(long long)p.r[0]);
+    };
+    auto Sx_of = [&](const PSum& p, int j1) {  // S at node j1 from the sums through node j1 - 1
+        const __int128 S0 = (__int128)((unsigned __int128)j1 * p.r[0] - p.m[0]);
+        const __int128 S1 = (__int128)((unsigned __int128)j1 * p.r[1] - p.m[1]);
+        return __fma_rn(pr1, i128_to_double(S1), -pr0 * i128_to_double(S0));
+    };
+    const double g1 = (Sx_of(tot, N) - V0) * inv_N;  // S_N from the totals
+    // g_j = phi_j - phi_{j-1} = g_1 - R_{j-1}; node field E_j = -(g_j + g_{j+1}) / (2 dx) inside
+    // (the central difference of phi, without the cancellation of large phi values), and Gauss's
+    // law over the half cells at the electrodes
+    double Rprev = Rr_of(run);      // R_{lo-1}
+    double Sprev = Sx_of(run, lo);  // S_lo
+    for (int j = lo; j < hi; ++j) {
+        if (j >= 1) {
+            const unsigned long long e = sde[j], i = sdi[j];
+            run.r[0] += e;
+            run.r[1] += i;
+            run.m[0] += (unsigned __int128)j * e;
+            run.m[1] += (unsigned __int128)j * i;
+        }
+        const double Rj = Rr_of(run);
+        double ph, E;
+        if (j == 0) {
+            ph = V0;
+            const double rw = __fma_rn(pw1, (double)sdi[0], -pw0 * (double)sde[0]);
+            E = -g1 * inv_dx - rw * hdx_eps;
+            ctl->E0_last[d] = E;
+        } else {
+            ph = V0 + (double)j * g1 - Sprev;
+            E = ((g1 - Rprev) + (g1 - Rj)) * m_inv_2dx;
+        }
+        phi[j] = ph;
+        E64[j] = E;
+        Ef[j] = (T)E;
+        Rprev = Rj;
+        Sprev = Sx_of(run, j + 1);
+    }
+    if (lo < hi && hi == N) {  // the electrode at x = L
+        const double rw = __fma_rn(pw1, (double)sdi[N], -pw0 * (double)sde[N]);
+        const double E = -(g1 - Rprev) * inv_dx + rw * hdx_eps;
+        phi[N] = 0.0;
+        E64[N] = E;
+        Ef[N] = (T)E;
+    }
 }
 
 template <typename T>
@@ -1213,7 +1202,7 @@ __global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ di
                                                      int out_buf, int mode, int nsl, int max_N) {
     constexpr int BLOCK = POST_BLOCK;
     extern __shared__ __align__(16) double s_f[];
-    __shared__ PSum s_ps[FIELD_SCAN / 32];
+    __shared__ PSum s_ps[FIELD_SCAN / 32 + 1];
     __shared__ int s_err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     grid_dep_sync();
@@ -1231,15 +1220,16 @@ __global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ di
         field_solve<T>(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, mode, tid, lane, warp, s_f, max_N, s_ps);
     }
     __syncthreads();
-    if (tid == 0) {  // the last CTA advances the step (bit 2) and, after a sweep, the slice parity
+    // the last CTA advances the step (bit 2) and, after a sweep, the slice parity. Every CTA has
+    // consumed its reads of both before its count (data dependence), and the last CTA reads no other
+    // CTA's results, so no fence: the kernel boundary publishes everything
+    if (tid == 0) {
         if (s_err) atomicOr(&ctl->error, s_err);
-        __threadfence();
         const unsigned prev = atomicAdd(&ctl->fin_done, 1u);
         if (prev == gridDim.x * gridDim.y - 1) {
             ctl->fin_done = 0;
             if (mode & 2) ctl->step = ctl->step + 1;
             if (mode & 1) ctl->slice_par = ctl->slice_par ^ 1;
-            __threadfence();
         }
     }
 }
