@@ -594,7 +594,6 @@ static pic_status enqueue_sort(pic_ctx* ctx) {
                    ctx->sort_hoff, ctx->sort_tot, ctx->sort_kr, ctx->sort_off, ctx->sort_eoff, ctx->max_N, gx,
                    ctx->stream),
        "sort launch");
-    CK(launch_set_dense(ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->stream), "sort launch");
     ctx->cur = 1 - ctx->cur;
     return PIC_OK;
 }

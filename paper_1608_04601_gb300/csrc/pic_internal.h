@@ -120,6 +120,7 @@ struct Ctl {
     long long acc_steps[MAXD];
     double E0_last[MAXD];
     double period_acc[MAXD][2];   // sum of the counts over the steps of the current rf period
+    unsigned sort_rows_done[MAXD][2];  // k_sort_rows CTAs finished, per store (reset by the last)
 };
 
 constexpr int PERIOD_HIST = 1 << 16;  // rf periods of mean counts kept per discharge (ring)

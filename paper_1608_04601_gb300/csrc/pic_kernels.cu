@@ -1402,10 +1402,12 @@ constexpr int SORT_WARP = 32 * SORT_R;  // consecutive slots of one warp in a so
 //                  into kr[slot], its record offset into off[slot], and the
 //                  tile's cell counts into hist[seg][t N + c]; input read
 //                  through the store's segment table;
-//   k_sort_rows    per cell: exclusive scan of the counts over the tiles;
-//   k_sort_cells   per store: exclusive scan of the cell totals;
+//   k_sort_rows    per cell: exclusive scan of the counts over the tiles; the
+//                  last CTA of a store scans the cell totals (first slot of
+//                  every cell);
 //   k_sort_scatter streaming, one slot per thread: destination = first slot of
-//                  its cell + the tile's offset in that cell + its rank.
+//                  its cell + the tile's offset in that cell + its rank; its
+//                  first CTA marks the sorted store as one dense segment.
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                            int buf, unsigned* __restrict__ hist,
                                                            const long long* __restrict__ hoff,
@@ -1481,48 +1483,13 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restric
     }
 }
 
-// Per (store, group of 32 cells): exclusive scan over the tiles in place (lane = cell, each warp
-// a contiguous range of tiles, so rows are read 128 bytes at a time); row totals out.
-__global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
-                                                    unsigned* __restrict__ hist, const long long* __restrict__ hoff,
-                                                    unsigned* __restrict__ tot) {
-    grid_dep_sync();
-    __shared__ unsigned s_sum[32][33];
-    const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
-    const int N = discs[d].N;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * 32 + lane;
-    if (blockIdx.x * 32 >= N) return;
-    const unsigned n = (unsigned)ctl->count[d][sp];
-    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
-    unsigned* H = hist + hoff[seg];
-    const unsigned per = (Ts + 31) / 32, t0 = min(Ts, warp * per), t1 = min(Ts, t0 + per);
-    unsigned sum = 0;
-    if (c < N)
-        for (unsigned t = t0; t < t1; ++t) sum += H[(size_t)t * N + c];
-    s_sum[warp][lane] = sum;
-    __syncthreads();
-    unsigned pre = 0;
-    for (int w = 0; w < warp; ++w) pre += s_sum[w][lane];
-    if (warp == 31 && c < N) tot[(long long)seg * MAXN + c] = pre + sum;
-    if (c < N)
-        for (unsigned t = t0; t < t1; ++t) {
-            const unsigned v = H[(size_t)t * N + c];
-            H[(size_t)t * N + c] = pre;
-            pre += v;
-        }
-}
-
-// Per store: exclusive scan of the row totals -> first slot of every cell.
-__global__ void __launch_bounds__(1024) k_sort_cells(const Disc* __restrict__ discs, unsigned* __restrict__ tot) {
-    grid_dep_sync();
-    const int seg = blockIdx.x, d = seg >> 1;
-    const int N = discs[d].N;
-    unsigned* a = tot + (long long)seg * MAXN;
+// Exclusive scan of one store's N row totals in place -> the first slot of every cell (1024
+// threads; the totals were written by other CTAs of the same grid, so they are read from L2).
+__device__ __forceinline__ void cells_scan(unsigned* a, int N) {
     __shared__ unsigned s_v[MAXN];
     __shared__ unsigned s_w[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j = tid; j < N; j += 1024) s_v[j] = a[j];
+    for (int j = tid; j < N; j += 1024) s_v[j] = __ldcg(a + j);
     __syncthreads();
     const int per = (N + 1023) / 1024, lo = tid * per, hi = min(N, lo + per);
     unsigned run = 0;
@@ -1554,9 +1521,54 @@ __global__ void __launch_bounds__(1024) k_sort_cells(const Disc* __restrict__ di
     }
 }
 
+// Per (store, group of 32 cells): exclusive scan over the tiles in place (lane = cell, each warp
+// a contiguous range of tiles, so rows are read 128 bytes at a time); row totals out.
+__global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
+                                                    unsigned* __restrict__ hist, const long long* __restrict__ hoff,
+                                                    unsigned* __restrict__ tot) {
+    grid_dep_sync();
+    __shared__ unsigned s_sum[32][33];
+    const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
+    const int N = discs[d].N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= N) return;
+    const unsigned n = (unsigned)ctl->count[d][sp];
+    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
+    unsigned* H = hist + hoff[seg];
+    const unsigned per = (Ts + 31) / 32, t0 = min(Ts, warp * per), t1 = min(Ts, t0 + per);
+    unsigned sum = 0;
+    if (c < N)
+        for (unsigned t = t0; t < t1; ++t) sum += H[(size_t)t * N + c];
+    s_sum[warp][lane] = sum;
+    __syncthreads();
+    unsigned pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_sum[w][lane];
+    if (warp == 31 && c < N) tot[(long long)seg * MAXN + c] = pre + sum;
+    if (c < N)
+        for (unsigned t = t0; t < t1; ++t) {
+            const unsigned v = H[(size_t)t * N + c];
+            H[(size_t)t * N + c] = pre;
+            pre += v;
+        }
+    // the last CTA of the store turns the row totals into the first slot of every cell
+    __shared__ int s_last;
+    if (warp == 31) __threadfence();  // this CTA's totals, before its count
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&ctl->sort_rows_done[d][sp], 1u);
+        s_last = prev == (unsigned)((N + 31) / 32 - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    cells_scan(tot + (long long)seg * MAXN, N);
+    if (threadIdx.x == 0) ctl->sort_rows_done[d][sp] = 0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restrict__ discs,
-                                                             const Ctl* __restrict__ ctl, int src, int dst,
+                                                             Ctl* __restrict__ ctl, int src, int dst,
                                                              const unsigned* __restrict__ hist,
                                                              const long long* __restrict__ hoff,
                                                              const unsigned* __restrict__ tot,
@@ -1576,6 +1588,13 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
     const unsigned* cstart = tot + (long long)seg * MAXN;
     const unsigned* KR = kr_all + eoff[seg];
     const unsigned* OF = off_all + eoff[seg];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the sorted store is one dense segment
+        D.seg_start[sp][0] = 0;
+        D.seg_start[sp][1] = (int)n;
+        D.seg_src[sp][0] = 0;
+        D.first_seg[sp][0] = 0;
+        ctl->nseg[d][sp] = 1;
+    }
     for (unsigned i = blockIdx.x * SORT_BLOCK + threadIdx.x; i < n; i += gridDim.x * SORT_BLOCK) {
         const unsigned kr = __ldcs(KR + i);
         const int k = (int)(kr & 0xFFFFu);
@@ -1850,7 +1869,7 @@ cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int src, int dst, unsigned* hist,
+cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int src, int dst, unsigned* hist,
                         const long long* hoff, unsigned* tot, unsigned* kr, unsigned* off, const long long* eoff,
                         int max_N, int grid_x, cudaStream_t st) {
     dim3 g(grid_x, 2 * n_disc);
@@ -1864,8 +1883,6 @@ cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
     e = launch_pdl(k_sort_rows, dim3((max_N + 31) / 32, 2 * n_disc), dim3(1024), 0, st, discs, ctl, hist, hoff, tot);
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(k_sort_cells, dim3(2 * n_disc), dim3(1024), 0, st, discs, tot);
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

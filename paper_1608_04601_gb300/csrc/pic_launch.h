@@ -24,7 +24,7 @@ cudaError_t launch_backkick(int fp64, const Disc* discs, int n_disc, const Ctl* 
                             cudaStream_t st);
 cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, const double* se, const double* si,
                           void* Te, void* Ti, unsigned long long* kmax, cudaStream_t st);
-cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int src, int dst, unsigned* hist,
+cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int src, int dst, unsigned* hist,
                         const long long* hoff, unsigned* tot, unsigned* kr, unsigned* off, const long long* eoff,
                         int max_N, int grid_x, cudaStream_t st);
 cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
