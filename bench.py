@@ -299,7 +299,7 @@ def run_gpu(args, rank: int, world: int):
         # small search of the launch shape and the sort period on this workload (whole steps, L2 flushed)
         from paper_1608_04601_gb300 import autotune
         tuned = autotune.autotune([gas], [(d, 0)], "fp32", tiles=[(256, 2), (256, 4), (128, 4)], ctas=[0],
-                                  sorts=[4, 8], use_cache=False)
+                                  sorts=[8, 16], use_cache=False)
         args.block, args.ppt, args.sort_every = tuned["block"], tuned["ppt"], tuned["sort_every"]
     sort_every = args.sort_every
     main = measure("fp32", args.steps, args.warmup, sort_every)
@@ -392,7 +392,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--sort-every", type=int, default=4)
+    ap.add_argument("--sort-every", type=int, default=16)
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--ppt", type=int, default=4)
     ap.add_argument("--cpu-steps", type=int, default=40)

@@ -85,7 +85,9 @@ def autotune(gases, discharges, precision: str = "fp32", tiles=None, ctas=None, 
     for block, ppt in (tiles or TILES):
         for c in (ctas or CTAS):
             for k in (sorts or sort_periods(spp)):
-                ms = time_config(gases, discharges, precision, block, ppt, c, k)
+                # warm-up through the first sort, then two whole sort periods
+                ms = time_config(gases, discharges, precision, block, ppt, c, k, steps=max(12, 2 * k),
+                                 warmup=max(4, k))
                 results.append({"block": block, "ppt": ppt, "ctas_per_sm": c, "sort_every": k, "ms_per_step": ms})
                 if log:
                     log(results[-1])

@@ -189,10 +189,29 @@ __device__ __forceinline__ unsigned long long cic_F(double f) {
 // parts (redux) and its first lane applies them:
 //   deposit (PAIR = false): v = 2^40 + F  ->  node key += count 2^32 - sum F, node key+1 += sum F
 //   moment  (PAIR = true):  v = lo + hi 2^32 (lo, hi < 2^26) -> node key += sum lo, key+1 += sum hi
+// The group reductions of a warp run one after another (one per distinct member mask), so their
+// cost grows with the number of groups: a warp with more than HIST_GROUPS distinct keys adds lane by
+// lane instead (measured on C2: the sweep of an unsorted store 140 -> 55 us; two groups is the best
+// threshold within a sort period). Integer adds: the same sums either way.
+constexpr int HIST_GROUPS = 2;
 template <bool PAIR>
 __device__ __forceinline__ void warp_hist(unsigned long long* h, int key, unsigned long long v, int lane) {
     const unsigned peers = __match_any_sync(FULL, key);
     const bool leader = lane == __ffs(peers) - 1;
+    if (__popc(__ballot_sync(FULL, leader)) > HIST_GROUPS) {
+        if (key >= 0) {
+            if (PAIR) {
+                const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
+                if (lo) sadd64(&h[key], lo);
+                if (hi) sadd64(&h[key + 1], hi);
+            } else {
+                const unsigned long long F = v & ((1ull << 40) - 1);  // <= 2^32
+                sadd64(&h[key], (1ull << 32) - F);
+                if (F) sadd64(&h[key + 1], F);
+            }
+        }
+        return;
+    }
     if (PAIR) {
         const unsigned lo = __reduce_add_sync(peers, (unsigned)v);
         const unsigned hi = __reduce_add_sync(peers, (unsigned)(v >> 32));
