@@ -57,6 +57,8 @@ struct pic_ctx {
     int max_slices = 0;  // slices of sweep chunks of the largest store
     void* stage = nullptr;  // device staging of state transfers
     size_t stage_bytes = 0;
+    void* h_pin = nullptr;  // pinned host scratch for read-backs (one stream sync per call)
+    size_t h_pin_bytes = 0;
     std::string err;
     pic_counters cnt_at_reset[MAXD];
     bool timing = false;
@@ -194,6 +196,7 @@ extern "C" void pic_destroy(pic_ctx* ctx) {
     }
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -705,12 +708,28 @@ extern "C" pic_status pic_sync(pic_ctx* ctx) {
 // ---------------------------------------------------------------------------
 static bool bad_d(pic_ctx* ctx, int d) { return !ctx || d < 0 || d >= ctx->n_disc; }
 
+// Pinned host scratch of at least `bytes` for read-backs: device -> host copies into it are
+// queued on the context's stream and waited for with one synchronisation.
+static pic_status pinned(pic_ctx* ctx, size_t bytes) {
+    if (ctx->h_pin_bytes >= bytes) return PIC_OK;
+    bytes = std::max(bytes, (size_t)1 << 16);
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    ctx->h_pin = nullptr;
+    ctx->h_pin_bytes = 0;
+    CK(cudaMallocHost(&ctx->h_pin, bytes), "pinned scratch");
+    ctx->h_pin_bytes = bytes;
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_get_count(pic_ctx* ctx, int32_t d, int32_t sp, int64_t* n) {
     if (bad_d(ctx, d) || (sp & ~1) || !n) return PIC_ERR_ARG;
-    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
-    long long v = 0;
-    CK(cudaMemcpy(&v, &ctx->d_ctl->count[d][sp], 8, cudaMemcpyDeviceToHost), "count");
-    *n = v;
+    pic_status s = pinned(ctx, 64);
+    if (s != PIC_OK) return s;
+    long long* v = static_cast<long long*>(ctx->h_pin);
+    CK(cudaMemcpyAsync(v, &ctx->d_ctl->count[d][sp], 8, cudaMemcpyDeviceToHost, ctx->stream), "count");
+    CK(cudaStreamSynchronize(ctx->stream), "count");
+    *n = *v;
     return PIC_OK;
 }
 
@@ -775,17 +794,15 @@ extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
         CK(launch_pack_state(ctx->fp64, ctx->d_discs, d, sp, ctx->cur, n, sc, sv, bad, grid, ctx->stream),
            "state pack");
     }
-    unsigned nbad = 0;
-    CK(cudaMemcpyAsync(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream), "state check");
+    // count and segment table on the device (a rejected upload leaves an empty store), then one
+    // synchronisation for the check word
+    CK(launch_finish_upload(ctx->d_discs, ctx->d_ctl, d, sp, n, bad, ctx->stream), "state finish");
+    s = pinned(ctx, 64);
+    if (s != PIC_OK) return s;
+    unsigned* hbad = static_cast<unsigned*>(ctx->h_pin);
+    CK(cudaMemcpyAsync(hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream), "state check");
     CK(cudaStreamSynchronize(ctx->stream), "state copy");
-    long long v = nbad ? 0 : n;  // a rejected upload leaves an empty store
-    CK(cudaMemcpy(&ctx->d_ctl->count[d][sp], &v, 8, cudaMemcpyHostToDevice), "count");
-    const int seg[2] = {0, (int)v}, zero = 0, one = 1;
-    CK(cudaMemcpy(D.seg_start[sp], seg, sizeof(seg), cudaMemcpyHostToDevice), "segments");
-    CK(cudaMemcpy(D.seg_src[sp], &zero, sizeof(int), cudaMemcpyHostToDevice), "segments");
-    CK(cudaMemcpy(D.first_seg[sp], &zero, sizeof(int), cudaMemcpyHostToDevice), "segments");
-    CK(cudaMemcpy(&ctx->d_ctl->nseg[d][sp], &one, sizeof(int), cudaMemcpyHostToDevice), "segments");
-    if (nbad) return fail(ctx, PIC_ERR_ARG, "cell index out of range");
+    if (*hbad) return fail(ctx, PIC_ERR_ARG, "cell index out of range");
     return PIC_OK;
 }
 
@@ -848,10 +865,7 @@ extern "C" pic_status pic_set_step(pic_ctx* ctx, int64_t step) {
     return PIC_OK;
 }
 
-static pic_status read_counters(pic_ctx* ctx, int d, pic_counters* o) {
-    unsigned long long c[NCNT];
-    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
-    CK(cudaMemcpy(c, ctx->hd[d].cnt, sizeof(c), cudaMemcpyDeviceToHost), "counters");
+static void parse_counters(const unsigned long long* c, pic_counters* o) {
     std::memset(o, 0, sizeof(*o));
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) o->absorbed[a][b] = (int64_t)c[CNT_ABS + 2 * a + b];
@@ -863,6 +877,14 @@ static pic_status read_counters(pic_ctx* ctx, int d, pic_counters* o) {
     o->candidates[1] = (int64_t)c[CNT_CAND + 1];
     o->table_clamped[0] = (int64_t)c[CNT_CLAMP];
     o->table_clamped[1] = (int64_t)c[CNT_CLAMP + 1];
+}
+static pic_status read_counters(pic_ctx* ctx, int d, pic_counters* o) {
+    pic_status s = pinned(ctx, 8 * NCNT);
+    if (s != PIC_OK) return s;
+    unsigned long long* c = static_cast<unsigned long long*>(ctx->h_pin);
+    CK(cudaMemcpyAsync(c, ctx->hd[d].cnt, 8 * NCNT, cudaMemcpyDeviceToHost, ctx->stream), "counters");
+    CK(cudaStreamSynchronize(ctx->stream), "counters");
+    parse_counters(c, o);
     return PIC_OK;
 }
 
@@ -889,47 +911,49 @@ extern "C" pic_status pic_get_tables(pic_ctx* ctx, int32_t g, void* Te, void* Ti
 
 extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
     if (bad_d(ctx, d) || !out) return PIC_ERR_ARG;
-    pic_status s = pic_sync(ctx);
-    if (s != PIC_OK) return s;
     const Disc& D = ctx->hd[d];
     const int N = D.N;
     const size_t N1 = (size_t)N + 1;
-    std::vector<unsigned __int128> iD0(N1), iD1(N1), iQ(N1), iP(N1);
-    CK(cudaMemcpy(iD0.data(), D.acc_D[0], 16 * N1, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(iD1.data(), D.acc_D[1], 16 * N1, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(iQ.data(), D.acc_Q, 16 * N1, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(iP.data(), D.acc_Dprev, 16 * N1, cudaMemcpyDeviceToHost), "moments");
-    std::vector<double> aD0(N1), aD1(N1), aQ(N1), aP(N1);
-    for (size_t j = 0; j < N1; ++j) {
-        aD0[j] = (double)iD0[j];
-        aD1[j] = (double)iD1[j];
-        aQ[j] = (double)iQ[j];
-        aP[j] = (double)iP[j];
-    }
-    long long steps = 0, cnt[2] = {0, 0};
-    double E0 = 0;
-    CK(cudaMemcpy(&steps, &ctx->d_ctl->acc_steps[d], 8, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(cnt, &ctx->d_ctl->count[d][0], 16, cudaMemcpyDeviceToHost), "moments");
-    CK(cudaMemcpy(&E0, &ctx->d_ctl->E0_last[d], 8, cudaMemcpyDeviceToHost), "moments");
+    // every read-back of the call into pinned memory, one synchronisation: the four exact
+    // accumulators, the control block and the counters
+    const size_t acc = 16 * N1, o_ctl = 4 * acc, o_cnt = o_ctl + ((sizeof(Ctl) + 15) / 16) * 16;
+    pic_status s = pinned(ctx, o_cnt + 8 * NCNT);
+    if (s != PIC_OK) return s;
+    unsigned char* h = static_cast<unsigned char*>(ctx->h_pin);
+    const void* src[4] = {D.acc_D[0], D.acc_D[1], D.acc_Q, D.acc_Dprev};
+    for (int q = 0; q < 4; ++q)
+        CK(cudaMemcpyAsync(h + q * acc, src[q], acc, cudaMemcpyDeviceToHost, ctx->stream), "moments");
+    CK(cudaMemcpyAsync(h + o_ctl, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream), "moments");
+    CK(cudaMemcpyAsync(h + o_cnt, D.cnt, 8 * NCNT, cudaMemcpyDeviceToHost, ctx->stream), "moments");
+    CK(cudaStreamSynchronize(ctx->stream), "moments");
+    const Ctl& hc = *reinterpret_cast<const Ctl*>(h + o_ctl);
+    if (hc.error & ERR_TIMEOUT) return fail(ctx, PIC_ERR_TIMEOUT, "a bounded device-side wait timed out");
+    if (hc.error & ERR_CAPACITY) return fail(ctx, PIC_ERR_CAPACITY, "particle or birth buffer capacity exceeded");
+    if (hc.error & ERR_NONFINITE) return fail(ctx, PIC_ERR_NONFINITE, "non-finite particle coordinate");
+    const unsigned __int128* iD0 = reinterpret_cast<const unsigned __int128*>(h);
+    const unsigned __int128* iD1 = reinterpret_cast<const unsigned __int128*>(h + acc);
+    const unsigned __int128* iQ = reinterpret_cast<const unsigned __int128*>(h + 2 * acc);
+    const unsigned __int128* iP = reinterpret_cast<const unsigned __int128*>(h + 3 * acc);
+    const long long steps = hc.acc_steps[d];
     const double dx = D.dx, ns = steps > 0 ? (double)steps : 1.0;
     for (int j = 0; j <= N; ++j) {
         const double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
-        if (out->n_e) out->n_e[j] = D.w[0] * aD0[j] / (H_TWO32 * Vj * ns);
-        if (out->n_i) out->n_i[j] = D.w[1] * aD1[j] / (H_TWO32 * Vj * ns);
-        if (out->mean_eps) out->mean_eps[j] = aP[j] > 0.0 ? (aQ[j] / 4096.0) / (aP[j] / H_TWO32) : 0.0;
+        const double aD0 = (double)iD0[j], aD1 = (double)iD1[j], aQ = (double)iQ[j], aP = (double)iP[j];
+        if (out->n_e) out->n_e[j] = D.w[0] * aD0 / (H_TWO32 * Vj * ns);
+        if (out->n_i) out->n_i[j] = D.w[1] * aD1 / (H_TWO32 * Vj * ns);
+        if (out->mean_eps) out->mean_eps[j] = aP > 0.0 ? (aQ / 4096.0) / (aP / H_TWO32) : 0.0;
     }
     pic_counters c;
-    s = read_counters(ctx, d, &c);
-    if (s != PIC_OK) return s;
+    parse_counters(reinterpret_cast<const unsigned long long*>(h + o_cnt), &c);
     out->steps = steps;
-    out->count[0] = cnt[0];
-    out->count[1] = cnt[1];
+    out->count[0] = hc.count[d][0];
+    out->count[1] = hc.count[d][1];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
             out->absorbed[a][b] = (double)(c.absorbed[a][b] - ctx->cnt_at_reset[d].absorbed[a][b]);
             out->flux[a][b] = steps > 0 ? out->absorbed[a][b] * D.w[a] / ((double)steps * D.dt) : 0.0;
         }
-    out->surface_charge = 8.8541878128e-12 * E0;
+    out->surface_charge = 8.8541878128e-12 * hc.E0_last[d];
     return PIC_OK;
 }
 

@@ -1668,6 +1668,19 @@ __global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __rest
 }
 
 // Every store becomes one dense segment [0, count) (after a load, an upload or a sort).
+// End of a state upload (one thread): the store holds n particles, or none if the pack kernel
+// found a cell out of range, as one dense segment.
+__global__ void k_finish_upload(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int d, int sp, long long n,
+                                const unsigned* __restrict__ bad) {
+    const Disc& D = discs[d];
+    const long long v = *bad ? 0 : n;
+    ctl->count[d][sp] = v;
+    D.seg_start[sp][0] = 0;
+    D.seg_start[sp][1] = (int)v;
+    D.seg_src[sp][0] = 0;
+    D.first_seg[sp][0] = 0;
+    ctl->nseg[d][sp] = 1;
+}
 __global__ void k_set_dense(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl) {
     grid_dep_sync();
     const int i = threadIdx.x;
@@ -1929,6 +1942,12 @@ cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int
 
 
 long long sort_tile() { return SORT_TILE; }
+
+cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, long long n, const unsigned* bad,
+                                 cudaStream_t st) {
+    k_finish_upload<<<1, 1, 0, st>>>(discs, ctl, d, sp, n, bad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st) {
     return launch_pdl(k_set_dense, dim3(1), dim3(128), 0, st, discs, n_disc, ctl);

@@ -38,6 +38,8 @@ size_t warm_desc_bytes(int fp64);
 void warm_desc_fill(int fp64, void* out, const void* cdf_e, const void* cdf_i, const void* eps, int P, double scale,
                     double K23);
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, long long n, const unsigned* bad,
+                                 cudaStream_t st);
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_debug_math(long long n, const float* x, const float* y, float* lg, float* sn, float* cs,
