@@ -142,13 +142,13 @@ class Simulation:
     def get_state(self, d: int, species: int, out: dict = None) -> dict:
         """The store of (d, species) as host arrays; `out` may hold preallocated arrays (keys c, f,
         vx, vy, vz, e.g. in pinned memory) of at least the store's size, which are then filled."""
-        n = self.count(d, species)
-        if out is not None:
+        if out is not None:  # the library reads the count itself
             c = out["c"]
             arrs = [out[k] for k in ("f", "vx", "vy", "vz")]
             assert c.dtype == np.int32 and all(a.dtype == self.dtype for a in arrs)
             cap = min(c.size, *[a.size for a in arrs])
         else:
+            n = self.count(d, species)
             c = np.zeros(max(n, 1), np.int32)
             arrs = [np.zeros(max(n, 1), self.dtype) for _ in range(4)]
             cap = max(n, 1)
