@@ -180,27 +180,19 @@ def run_gpu(args, rank: int, world: int):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def measure(prec: str, steps: int, warmup: int, sort_every: int, disc=None, disc_gas=None):
-        """Two passes over the same steps (the step is deterministic for a seed). The timed pass: L2
-        flushed, then one step between two events, with nothing else on the stream and no host
-        synchronisation, so the host stays ahead of the GPU. The replay from the same seed reads the
-        particle count before every step (the particle-steps of the timed pass) and times every
-        sweep launch with events on the library's stream (the roofline's kernel time), also with L2
-        flushed before every step; it must end with the timed pass's particle count."""
         dd = disc if disc is not None else d
-        gg = disc_gas if disc_gas is not None else gas
-
-        def make():
-            return pic.Simulation(gg, dd, seed=dd.seed, precision=prec, sort_every=sort_every, stream="torch",
-                                  block=args.block, ppt=args.ppt)
-
-        sim = make()
+        sim = pic.Simulation(disc_gas if disc_gas is not None else gas, dd, seed=dd.seed, precision=prec,
+                             sort_every=sort_every, stream="torch", block=args.block, ppt=args.ppt)
         sim.step(warmup)
         sim.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        counts = []
+        sim.sweep_timing(True)
         torch.cuda.synchronize()
         with Clocks(dev) as clk:
             clk.mark(True)
             for k in range(steps):
+                counts.append(sim.count(0, 0) + sim.count(0, 1))
                 flush.fill_(float(k))
                 ev[k][0].record(stream)
                 sim.step(1)
@@ -208,34 +200,19 @@ def run_gpu(args, rank: int, world: int):
             torch.cuda.synchronize()
             clk.mark(False)
         sim.sync()
-        final = sim.count(0, 0) + sim.count(0, 1)
-        step_index = sim.step_index
-        sim.close()
+        sweep_ms, launches = sim.sweep_timing(False)
         step_ms = [a.elapsed_time(b) for a, b in ev]
         total_ms = sum(step_ms)
-        rep = make()
-        rep.step(warmup)
-        rep.sync()
-        counts = []
-        rep.sweep_timing(True)
-        for k in range(steps):
-            counts.append(rep.count(0, 0) + rep.count(0, 1))
-            flush.fill_(float(k))
-            rep.step(1)
-        rep.sync()
-        sweep_ms, launches = rep.sweep_timing(False)
-        if rep.count(0, 0) + rep.count(0, 1) != final:
-            raise RuntimeError("the replay of the timed steps ended with another particle count")
-        rep.close()
         ps = float(sum(counts))
         out = {"ps": ps, "total_ms": total_ms, "sweep_ms": sweep_ms, "sweep_launches": launches,
                "clocks": clk.summary(), "counts": (counts[0], counts[-1])}
         # kernels launched per step: the sweep and the post-sweep kernel (segment tables, newborn
         # copies, store totals, field, moments); when a sort is due its count, row-scan (with the
         # cell scan in its last CTA per store) and scatter (with the dense reset) kernels
-        step0 = step_index - steps
+        step0 = sim.step_index - steps
         sorts = sum(1 for n in range(step0 + 1, step0 + steps + 1) if sort_every > 0 and n % sort_every == 0)
         out["gpu_launches"] = 2 * steps + 3 * sorts
+        sim.close()
         return out
 
     def measure_e2e(prec: str, steps: int, sort_every: int):
@@ -368,8 +345,8 @@ def run_gpu(args, rank: int, world: int):
                 "kernel": "k_sweep<float,%d,%d>" % (args.block, args.ppt),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_note,
                 "avg_launch_ms": avg_sweep_s * 1e3,
-                "kernel_timing": "CUDA events around every sweep launch, on the library's stream, in a replay of "
-                                 "the timed steps (same seed, L2 flushed before every step)",
+                "kernel_timing": "CUDA events around every sweep launch, on the library's stream, inside the timed "
+                                 "steps (L2 flushed before every step)",
                 "sweep_share_of_step": main["sweep_ms"] / main["total_ms"]}
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
