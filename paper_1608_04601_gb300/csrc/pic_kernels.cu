@@ -937,14 +937,16 @@ __device__ __forceinline__ double i128_to_double(__int128 x) {
     return __fma_rn((double)hi, 0x1p64, __ull2double_rn(lo));
 }
 
-// After a sweep (mode bit 1) and for every solve, one grid (x = slice or the
-// field role, y = store): CTAs x < nsl write the segment entries of slice x of
-// store y (seg_start/seg_src of its chunks, first_seg of the slots they hold),
-// copy its newborns into the newborn regions and clear the slice sums; CTAs
-// x = nsl, y even solve the field of discharge y / 2 and accumulate the moments.
-// mode bits: 1 segments after a sweep; 2 accumulate moments and advance the
-// step; 4 initial solve at t = n dt (load); 8 segments only (no solve,
-// deposits kept). The last CTA to finish advances the step (mode bit 2).
+// After a sweep (mode bit 1) and for every solve, one grid (x = slice or role,
+// y = store): CTAs x < nsl write the segment entries of slice x of store y
+// (seg_start/seg_src of its chunks, first_seg of the slots they hold) and copy
+// its newborns into the newborn regions; CTA x = nsl, y even solves the field of
+// discharge y / 2 and accumulates the moments; CTA x = nsl, y odd turns the
+// slice sums of discharge y / 2 into the new counts and clears the sums of the
+// other parity for the next sweep. mode bits: 1 segments after a sweep; 2
+// accumulate moments and advance the step; 4 initial solve at t = n dt (load);
+// 8 segments only (no solve, deposits kept). The last CTA to finish advances
+// the step (mode bit 2) and flips the slice parity (mode bit 1).
 template <int BLOCK>
 __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int out_buf, int tid, int lane,
                           int warp) {
