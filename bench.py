@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -29,8 +30,16 @@ UNIT = "particle-steps/s"
 BYTES_PER_PS = {"fp32": 40, "fp64": 72}   # algorithmic HBM bytes per particle-step (read + write)
 
 
-def workload():
-    from paper_1608_04601_gb300.workloads import c2
+def workload(name: str = "c2"):
+    """c2: the 1e6 + 1e6 Ar-like discharge the metric is quoted on; c3: the 2e7 + 2e7 He-like 500 V
+    discharge; c3s: the same physics at 4e6 + 4e6 (160 MB per record buffer, beyond L2, small enough
+    for a profiler capture)."""
+    from paper_1608_04601_gb300.workloads import c2, c3
+    if name == "c3":
+        return c3()
+    if name == "c3s":
+        return c3().scaled(name="C3 physics at 4e6+4e6 (he-like 80Pa 5cm 500V N2048 gamma0.1)", n_e0=4_000_000,
+                           n_i0=4_000_000)
     return c2()
 
 
@@ -58,17 +67,40 @@ def sweep_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(prec: str, kernel: str):
+def recorded_traffic(prec: str, kernel: str, workload_name: str):
     """DRAM bytes per particle-step of the sweep from the committed ncu summary, if it was taken on
-    the current kernel source and the same launch shape."""
+    the current kernel source, the same launch shape and a workload of the same kind (the entry for
+    the large discharge is a capture of the same physics at fewer particles, scaled per particle)."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
-    e = j.get(prec)
+    key = prec + ("_c3" if workload_name.startswith("C3") else "")
+    e = j.get(key)
     if not e or e.get("source_hash") != sweep_source_hash() or e.get("kernel") != kernel:
         return None
     return e
+
+
+def sweep_roofline(r: dict, prec: str, block: int, ppt: int, workload_name: str) -> dict:
+    """Roofline of the dominant kernel (the sweep) from one measure() result: algorithmic bytes per
+    launch (40 B per particle-step in FP32, 72 B in FP64, times the particles one launch processes)
+    over the average CUDA-event duration of the sweep launches of the timed steps."""
+    peak, peak_note = peaks()
+    launch_ps = r["ps"] / max(1, r["sweep_launches"])
+    bytes_per_launch = BYTES_PER_PS[prec] * launch_ps
+    avg_sweep_s = r["sweep_ms"] * 1e-3 / max(1, r["sweep_launches"])
+    achieved = bytes_per_launch / avg_sweep_s / 1e9
+    kernel = "k_sweep<%s,%d,%d>" % ("float" if prec == "fp32" else "double", block, ppt)
+    tr = recorded_traffic(prec, kernel, workload_name)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tr["dram_bytes_per_particle"] * launch_ps) if tr else None,
+            "traffic_source": tr.get("source") if tr else None,
+            "kernel": kernel, "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_note,
+            "avg_launch_ms": avg_sweep_s * 1e3, "particles_per_launch": launch_ps,
+            "kernel_timing": "CUDA events around every sweep launch, on the library's stream, inside the timed "
+                             "steps (L2 flushed before every step)",
+            "sweep_share_of_step": r["sweep_ms"] / r["total_ms"]}
 
 
 class Clocks:
@@ -81,7 +113,7 @@ class Clocks:
         self.proc = None
         self.samples = []
         self.t0 = self.t1 = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"pic_bench_clocks_{os.getpid()}.csv")
 
     def _reader(self):
         for ln in self.proc.stdout:
@@ -120,7 +152,6 @@ class Clocks:
             except Exception:
                 self.proc.kill()
             try:
-                os.makedirs(os.path.dirname(self.path), exist_ok=True)
                 with open(self.path, "w") as f:
                     for t, ln in self.samples:
                         f.write(f"{t:.3f}, {ln}\n")
@@ -171,7 +202,7 @@ def run_gpu(args, rank: int, world: int):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    d0 = workload()
+    d0 = workload(args.workload)
     d = d0.scaled(seed=d0.seed + rank, discharge_id=rank)
     gas = gas_for(d)
     # a dedicated stream: the library, the L2 flush and the timing events all run on it
@@ -183,6 +214,11 @@ def run_gpu(args, rank: int, world: int):
         dd = disc if disc is not None else d
         sim = pic.Simulation(disc_gas if disc_gas is not None else gas, dd, seed=dd.seed, precision=prec,
                              sort_every=sort_every, stream="torch", block=args.block, ppt=args.ppt)
+        if sort_every > 0:
+            # the load draws positions in slot order, so the loaded store is unsorted; a long run spends
+            # all but its first sort period on cell-sorted stores, so the store is sorted once here,
+            # before the warm-up (the timed steps still include every periodic sort that falls in them)
+            sim.sort()
         sim.step(warmup)
         sim.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -222,6 +258,8 @@ def run_gpu(args, rank: int, world: int):
         import numpy as np
         sim = pic.Simulation(gas, d, seed=d.seed, precision=prec, sort_every=sort_every, stream="torch",
                              block=args.block, ppt=args.ppt)
+        if sort_every > 0:
+            sim.sort()
         sim.step(2)
         rdt = np.float32 if prec == "fp32" else np.float64
         tdt = torch.float32 if prec == "fp32" else torch.float64
@@ -307,25 +345,21 @@ def run_gpu(args, rank: int, world: int):
         args.block, args.ppt, args.sort_every = tuned["block"], tuned["ppt"], tuned["sort_every"]
     sort_every = args.sort_every
     main = measure("fp32", args.steps, args.warmup, sort_every)
-    fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
-    e2e = measure_e2e("fp32", max(3, min(10, args.steps)), sort_every)
-    batch = measure_batch(max(4, args.steps // 2), 3, sort_every) if not args.no_batch else None
-    c3 = None
-    if args.c3 and world == 1:
+    fp64 = e2e = batch = c3 = warm = None
+    if not args.quick:
+        fp64 = measure("fp64", max(4, args.steps // 2), max(3, args.warmup), sort_every)
+        e2e = measure_e2e("fp32", max(3, min(10, args.steps)), sort_every)
+        batch = measure_batch(max(4, args.steps // 2), 3, sort_every) if not args.no_batch else None
+    if args.c3 and not args.quick and world == 1 and args.workload != "c3":
         # the large workload: 2e7 + 2e7 particles, 2048 cells, secondary emission (800 MB per record
-        # buffer, far beyond L2)
-        from paper_1608_04601_gb300.workloads import c3 as c3_disc
-        dc = c3_disc()
+        # buffer, far beyond L2): its own step rate and its own sweep roofline
+        dc = workload("c3")
         r3 = measure("fp32", 20, 6, sort_every, disc=dc, disc_gas=gas_for(dc))
-        lp3 = r3["ps"] / max(1, r3["sweep_launches"])
-        s3 = r3["sweep_ms"] * 1e-3 / max(1, r3["sweep_launches"])
         c3 = {"workload": dc.name, "value": r3["ps"] / (r3["total_ms"] * 1e-3), "unit": UNIT,
               "ms_per_step": r3["total_ms"] / 20, "steps": 20, "warmup": 6,
-              "sweep_avg_launch_ms": s3 * 1e3, "sweep_gbs": BYTES_PER_PS["fp32"] * lp3 / s3 / 1e9,
-              "sweep_frac_of_peak": BYTES_PER_PS["fp32"] * lp3 / s3 / 1e9 / peaks()[0],
-              "particles": int(lp3), "clocks": r3["clocks"]}
-    warm = None
-    if args.warm_start and world == 1:
+              "particles": int(r3["ps"] / max(1, r3["sweep_launches"])), "clocks": r3["clocks"],
+              "roofline": sweep_roofline(r3, "fp32", args.block, args.ppt, dc.name)}
+    if args.warm_start and not args.quick and world == 1:
         # rf periods to the steady state from the homogeneous start vs from the network's profiles
         from paper_1608_04601_gb300 import warmstart
         warm = warmstart.experiment(n_train=args.ws_train, n_test=args.ws_test)
@@ -333,21 +367,7 @@ def run_gpu(args, rank: int, world: int):
     # aggregate over ranks: the job took as long as its slowest rank, and did every rank's work
     total_ms, ps = reduce_over_ranks(main["total_ms"], main["ps"], world, "cuda")
     value = ps / (total_ms * 1e-3)
-
-    peak, peak_note = peaks()
-    launch_ps = main["ps"] / max(1, main["sweep_launches"])
-    bytes_per_launch = BYTES_PER_PS["fp32"] * launch_ps
-    avg_sweep_s = main["sweep_ms"] * 1e-3 / max(1, main["sweep_launches"])
-    achieved = bytes_per_launch / avg_sweep_s / 1e9
-    tr = recorded_traffic("fp32", "k_sweep<float,%d,%d>" % (args.block, args.ppt))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tr["dram_bytes_per_particle"] * launch_ps) if tr else None,
-                "kernel": "k_sweep<float,%d,%d>" % (args.block, args.ppt),
-                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_note,
-                "avg_launch_ms": avg_sweep_s * 1e3,
-                "kernel_timing": "CUDA events around every sweep launch, on the library's stream, inside the timed "
-                                 "steps (L2 flushed before every step)",
-                "sweep_share_of_step": main["sweep_ms"] / main["total_ms"]}
+    roofline = sweep_roofline(main, "fp32", args.block, args.ppt, d0.name)
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -357,12 +377,16 @@ def run_gpu(args, rank: int, world: int):
                       "block": args.block, "ppt": args.ppt, "parallelism": f"replicas{world}" if world > 1 else "1gpu",
                       "l2": "flushed (256 MB write) before every timed step",
                       "autotuned": tuned},
-           "roofline": roofline,
-           "fp64_path": {"value": fp64["ps"] / (fp64["total_ms"] * 1e-3), "unit": UNIT,
-                         "ms_per_step": fp64["total_ms"] / max(1, max(4, args.steps // 2)),
-                         "sweep_gbs": BYTES_PER_PS["fp64"] * fp64["ps"] / (fp64["sweep_ms"] * 1e-3) / 1e9,
-                         "bytes_per_particle_step": BYTES_PER_PS["fp64"]},
-           "e2e": e2e, "clocks": main["clocks"], "gpu_launches": main["gpu_launches"]}
+           "roofline": roofline, "clocks": main["clocks"], "gpu_launches": main["gpu_launches"]}
+    if sort_every > 0:
+        res["config"]["initial_sort"] = "the loaded store is sorted by cell once, before the warm-up"
+    if fp64:
+        res["fp64_path"] = {"value": fp64["ps"] / (fp64["total_ms"] * 1e-3), "unit": UNIT,
+                            "ms_per_step": fp64["total_ms"] / max(1, max(4, args.steps // 2)),
+                            "sweep_gbs": BYTES_PER_PS["fp64"] * fp64["ps"] / (fp64["sweep_ms"] * 1e-3) / 1e9,
+                            "bytes_per_particle_step": BYTES_PER_PS["fp64"]}
+    if e2e:
+        res["e2e"] = e2e
     if batch:
         res["batch_c4"] = batch
     if c3:
@@ -375,7 +399,7 @@ def run_gpu(args, rank: int, world: int):
 def run_cpu_baseline(args):
     """The FP64 oracle as it stands, single thread, on a bounded sample of the same workload."""
     from oracle import oracle as O
-    d = workload()
+    d = workload(args.workload)
     gas = gas_for(d)
     t0 = time.perf_counter()
     o = O.Oracle(gas, d, "f64", sort_every=args.sort_every)
@@ -403,6 +427,10 @@ def main():
     ap.add_argument("--ppt", type=int, default=4)
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c3s"],
+                    help="measured workload: c2 (the metric's configuration), c3, or c3s (C3 physics at 4e6+4e6)")
+    ap.add_argument("--quick", action="store_true",
+                    help="main measurement only (no FP64 path, end-to-end, batch, large workload, warm start)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-c3", dest="c3", action="store_false", help="skip the 2e7 + 2e7 particle workload")
     ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
@@ -422,7 +450,7 @@ def main():
             return
         from oracle import oracle as O
         O.build()
-        d = workload()
+        d = workload(args.workload)
         gas = gas_for(d)
         o = O.Oracle(gas, d, "f64", sort_every=args.sort_every)
         o.step(args.warmup)
@@ -452,7 +480,7 @@ def main():
     g.build()
     res = run_gpu(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and not args.quick:
             res["cpu_baseline"] = run_cpu_baseline(args)
         print(json.dumps(res))
     if world > 1:

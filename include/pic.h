@@ -261,6 +261,12 @@ pic_status pic_debug_math(int64_t n, const float* x, const float* y, float* log_
  *   c_out, rec_out device arrays of n entries, caller-owned, not overlapping
  *                  the inputs; cells must lie in [0, n_cells);
  *   cuda_stream    stream to enqueue on (NULL: the legacy default stream).
+ * Alignment: rec_in and rec_out must be 16-byte aligned (PIC_FP32) or 32-byte
+ * aligned (PIC_FP64), c_in and c_out 4-byte aligned; otherwise PIC_ERR_ARG
+ * and nothing is launched. A cell outside [0, n_cells) is not placed: the
+ * call still returns PIC_OK, and the last entries of c_out and rec_out (one
+ * per such cell) keep whatever they held before (the context sort,
+ * pic_sort, reports such cells through pic_sync instead).
  * Its scratch is a fixed array of PIC_NOALLOC_SCRATCH_BYTES compiled into the
  * library (every GPU that loads the library holds it until the process
  * exits); the call allocates nothing. Limit: n_cells * (1 + ceil(n / 4096))
@@ -270,8 +276,9 @@ pic_status pic_debug_math(int64_t n, const float* x, const float* y, float* log_
  * any stream capture. All calls share the one array and each call rewrites
  * all of it that it reads, so consecutive calls are independent, but calls
  * that overlap on the GPU (other streams or threads) race: serialise them.
- * Returns PIC_ERR_ARG for invalid arguments, PIC_ERR_CUDA if a launch fails;
- * asynchronous otherwise.                                                  */
+ * Returns PIC_ERR_ARG for invalid arguments, PIC_ERR_CUDA if a launch fails
+ * or if an earlier CUDA error is pending on the calling thread (it is left
+ * pending for the caller, and nothing is launched); asynchronous otherwise. */
 #define PIC_NOALLOC_SCRATCH_BYTES (4u << 20)
 pic_status pic_sort_noalloc(const int32_t* c_in, const void* rec_in, int32_t* c_out, void* rec_out,
                             int64_t n, int32_t n_cells, int32_t precision, void* cuda_stream);

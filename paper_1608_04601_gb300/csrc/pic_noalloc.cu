@@ -11,6 +11,7 @@
 // loads the library until the process exits.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/pic.h"
@@ -197,19 +198,26 @@ pic_status run_sort(const int32_t* c_in, const void* rec_in, int32_t* c_out, voi
     unsigned* cstart = scratch;
     unsigned* hist = scratch + N;
     int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PIC_ERR_CUDA;
     const int grid = (int)(Ts < 2LL * sms ? Ts : 2LL * sms);
-    na_count<<<grid, NA_BLOCK, sizeof(unsigned) * N, st>>>(c_in, n, N, hist, Ts);
-    na_rows<<<N, 1024, 0, st>>>(hist, Ts, cstart);
-    na_cells<<<1, 1024, 0, st>>>(cstart, N);
     const size_t smem = sizeof(unsigned) * NA_NW * N;
     if (cudaFuncSetAttribute(na_scatter<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PIC_ERR_CUDA;
+    // each launch is checked on its own, so that a failure is reported by the launch that caused it
+    na_count<<<grid, NA_BLOCK, sizeof(unsigned) * N, st>>>(c_in, n, N, hist, Ts);
+    if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
+    na_rows<<<N, 1024, 0, st>>>(hist, Ts, cstart);
+    if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
+    na_cells<<<1, 1024, 0, st>>>(cstart, N);
+    if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
     na_scatter<R><<<grid, NA_BLOCK, smem, st>>>(c_in, static_cast<const R*>(rec_in), c_out, static_cast<R*>(rec_out),
                                                 n, N, hist, cstart, Ts);
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 }  // namespace
 
@@ -218,8 +226,17 @@ extern "C" pic_status pic_sort_noalloc(const int32_t* c_in, const void* rec_in, 
     if (n < 0 || n_cells < 1 || n_cells > PIC_MAX_CELLS || (precision != PIC_FP32 && precision != PIC_FP64))
         return PIC_ERR_ARG;
     if (n > 0 && (!c_in || !rec_in || !c_out || !rec_out)) return PIC_ERR_ARG;
+    // the kernels move records as float4 (16 bytes) or as 32-byte groups of four doubles, and cells
+    // as int32: a misaligned buffer is rejected here, before any launch
+    const size_t rec_align = precision == PIC_FP64 ? sizeof(D4) : sizeof(float4);
+    if (n > 0 && (!aligned(rec_in, rec_align) || !aligned(rec_out, rec_align) || !aligned(c_in, 4) ||
+                  !aligned(c_out, 4)))
+        return PIC_ERR_ARG;
     const long long tiles = (n + NA_TILE - 1) / NA_TILE;
     if ((long long)n_cells + (long long)n_cells * tiles > NA_WORDS) return PIC_ERR_CAPACITY;
+    // an error left over from the caller's earlier work is not this call's: report it without
+    // clearing it and launch nothing
+    if (n > 0 && cudaPeekAtLastError() != cudaSuccess) return PIC_ERR_CUDA;
     unsigned* scratch = nullptr;
     pic_status s = scratch_address(&scratch);
     if (s != PIC_OK || n == 0) return s;

@@ -40,12 +40,18 @@ def test_record_used_only_for_the_same_source_and_kernel(tmp_path, monkeypatch):
     rec = {"fp32": {"kernel": "k_sweep<float,256,2>", "dram_bytes_per_particle": 22.0,
                     "source_hash": bench.sweep_source_hash()}}
     (root / "profiles" / "sweep_traffic.json").write_text(json.dumps(rec))
-    assert bench.recorded_traffic("fp32", "k_sweep<float,256,2>")["dram_bytes_per_particle"] == 22.0
-    assert bench.recorded_traffic("fp32", "k_sweep<float,256,4>") is None
-    assert bench.recorded_traffic("fp64", "k_sweep<float,256,2>") is None
+    c2, c3 = "C2 ar-like", "C3 he-like"
+    assert bench.recorded_traffic("fp32", "k_sweep<float,256,2>", c2)["dram_bytes_per_particle"] == 22.0
+    assert bench.recorded_traffic("fp32", "k_sweep<float,256,4>", c2) is None
+    assert bench.recorded_traffic("fp64", "k_sweep<float,256,2>", c2) is None
+    # the large discharge has its own record (a capture of the same physics at fewer particles)
+    assert bench.recorded_traffic("fp32", "k_sweep<float,256,2>", c3) is None
+    rec["fp32_c3"] = dict(rec["fp32"], dram_bytes_per_particle=41.0)
+    (root / "profiles" / "sweep_traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("fp32", "k_sweep<float,256,2>", c3)["dram_bytes_per_particle"] == 41.0
     rec["fp32"]["source_hash"] = "0" * 16
     (root / "profiles" / "sweep_traffic.json").write_text(json.dumps(rec))
-    assert bench.recorded_traffic("fp32", "k_sweep<float,256,2>") is None
+    assert bench.recorded_traffic("fp32", "k_sweep<float,256,2>", c2) is None
 
 
 def test_committed_record_names_its_command_and_kernel():
