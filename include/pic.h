@@ -165,8 +165,44 @@ typedef struct {
     double absorbed[2][2];   /* superparticles absorbed [species][electrode] */
     double flux[2][2];       /* particle flux to [species][electrode], m^-2 s^-1 */
     double surface_charge;   /* eps0 E(0) at the last solve, C m^-2          */
+    /* rf periods and the periodic steady state, computed by the library from the mean
+     * superparticle count of each species per period (pic_period_counts): the state is
+     * steady from the first period k (counted from 1) at which, for both species, the means
+     * over the periods [k-W, k) and [k-2W, k-W) differ by less than PIC_STEADY_TOL relative
+     * to the first, W = PIC_STEADY_BLOCK. The paper notes that its discharges needed about
+     * 1000 to 4000 periods (section "Numerical parameters and initial values").           */
+    int64_t periods_done;    /* complete rf periods since step 0                 */
+    int64_t steady_period;   /* first period at which the test held, -1 if none  */
+    double steady_metric;    /* the test's largest relative difference at the last
+                                complete period (-1 before 2 W periods)         */
+    int32_t steady;          /* 1 if steady_period >= 0                          */
+    int32_t reserved;
+    /* Discharge current density J(t) = eps0 dE(0,t)/dt + e0 (Gamma_i - Gamma_e)(0,t)
+     * (section "Boundary conditions"), FP64 on the device every step: */
+    double J_amp;            /* first-harmonic amplitude over the last complete
+                                period, A m^-2 (0 before the first period)      */
+    double J_last;           /* over the last step, A m^-2                       */
 } pic_moments_t;
+#define PIC_STEADY_BLOCK 50
+#define PIC_STEADY_TOL 1e-3
 pic_status pic_moments(pic_ctx* ctx, int32_t discharge, pic_moments_t* out);
+
+/* J(t) of every step first .. first+n-1 into host out[2 k] (at z = 0, the paper's
+ * definition) and out[2 k + 1] (the same expression at z = d; the two agree to rounding
+ * when both species have equal weights, by conservation of charge). The current of step n
+ * spans t_n .. t_{n+1}: eps0 times the change of the electrode field between the solves at
+ * t_n and t_{n+1}, over dt, plus the charge of the superparticles absorbed (and secondary
+ * electrons emitted) at that electrode during the sweep of step n, over dt. Zero for the
+ * first step after a load. The last 4 rf periods (4096 steps if steps_per_period is 0) are
+ * kept; *steps_done receives the steps completed.                                        */
+pic_status pic_current(pic_ctx* ctx, int32_t discharge, int64_t first, int64_t n, double* out,
+                       int64_t* steps_done);
+/* First-harmonic amplitude of J(t) at z = 0 over rf periods first .. first+n-1: with
+ * a = (2/P) sum_k J_k sin(w t_k), b = (2/P) sum_k J_k cos(w t_k) over the P steps of the
+ * period at their midpoints t_k, the amplitude is sqrt(a^2 + b^2) (the J_calc of Eq.
+ * adaptivevoltage). Requires a time step that divides the period (PIC_ERR_STATE). */
+pic_status pic_current_amplitude(pic_ctx* ctx, int32_t discharge, int64_t first, int64_t n, double* out,
+                                 int64_t* periods_done);
 pic_status pic_reset_moments(pic_ctx* ctx);
 
 void        pic_destroy(pic_ctx* ctx);         /* NULL-safe                 */

@@ -111,6 +111,7 @@ def _lib(prec: str):
         L.orc_get_tables.argtypes = [vp, vp, vp]
         L.orc_moments.argtypes = [vp, vp, vp, vp, C.POINTER(OrcMomentInfo)]
         L.orc_reset_moments.argtypes = [vp]
+        L.orc_last_current.argtypes = [vp, vp]
         L.orc_load_profiles.argtypes = [vp, C.c_int, vp, vp, vp]
         L.orc_load_profiles.restype = C.c_int
         L.orc_real_bytes.restype = C.c_int
@@ -329,6 +330,12 @@ class Oracle:
 
     def reset_moments(self):
         self.L.orc_reset_moments(self.h)
+
+    def last_current(self) -> np.ndarray:
+        """J(t) of the last solved step at z = 0 and at z = d, A/m^2."""
+        J = np.zeros(2)
+        self.L.orc_last_current(self.h, _p(J))
+        return J
 
 
 if __name__ == "__main__":

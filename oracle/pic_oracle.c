@@ -106,6 +106,13 @@ struct orc_ctx {
     double *acc_D[2], *acc_Q, *acc_Dprev;
     int64_t acc_steps;
     orc_counters cnt_at_reset;
+    /* discharge current density (Eq. for J(t), section "Boundary conditions"): electrode fields and
+     * particle counts at the last solve, secondary electrons emitted per electrode, and the last
+     * step's J at z = 0 and at z = d */
+    int have_solve;
+    double E_wall_prev[2];
+    int64_t abs_prev[2][2], see_side[2], see_prev[2];
+    double J_last[2];
 };
 
 /* ------------------------------------------------------------------------ */
@@ -826,6 +833,7 @@ int orc_sweep(orc_ctx* o) {
                                    side == 0 ? vn : -vn);
                         deposit(o->D[SP_E], ce, fe);
                         o->cnt.see_emitted++;
+                        o->see_side[side]++;
                     }
                 }
             }
@@ -885,8 +893,39 @@ int orc_solve(orc_ctx* o) {
     double V0 = o->p.V_rf_V * sin(2.0 * PI_D * o->p.f_rf_Hz * t);
     orc_poisson(N, dx, V0, 0.0, o->rho, o->phi, o->E64);
     for (int j = 0; j <= N; ++j) o->E[j] = (real)o->E64[j];
+    /* Discharge current density over the step just solved for (from the previous solve to this
+     * one), J = eps0 dE/dt + e0 (Gamma_i - Gamma_e), fluxes counted positive towards +z:
+     * at z = 0 absorbed ions (moving towards -z) carry -e w_i, absorbed electrons +e w_e, emitted
+     * secondary electrons (moving towards +z) -e w_e; at z = d the signs of the absorbed
+     * particles flip and emitted electrons move towards -z. */
+    if (o->have_solve) {
+        double dt = o->p.dt_s, we = o->p.w_e, wi = o->p.w_i;
+        double dA[2][2], dS[2];
+        for (int a = 0; a < 2; ++a) {
+            for (int b = 0; b < 2; ++b) dA[a][b] = (double)(o->cnt.absorbed[a][b] - o->abs_prev[a][b]);
+            dS[a] = (double)(o->see_side[a] - o->see_prev[a]);
+        }
+        double cond0 = E_CHARGE * (we * dA[SP_E][0] - wi * dA[SP_I][0] - we * dS[0]) / dt;
+        double condN = E_CHARGE * (wi * dA[SP_I][1] - we * dA[SP_E][1] + we * dS[1]) / dt;
+        o->J_last[0] = EPS0 * (o->E64[0] - o->E_wall_prev[0]) / dt + cond0;
+        o->J_last[1] = EPS0 * (o->E64[N] - o->E_wall_prev[1]) / dt + condN;
+    } else {
+        o->J_last[0] = o->J_last[1] = 0.0;
+    }
+    o->have_solve = 1;
+    o->E_wall_prev[0] = o->E64[0];
+    o->E_wall_prev[1] = o->E64[N];
+    for (int a = 0; a < 2; ++a) {
+        for (int b = 0; b < 2; ++b) o->abs_prev[a][b] = o->cnt.absorbed[a][b];
+        o->see_prev[a] = o->see_side[a];
+    }
     o->step++;
     return 0;
+}
+
+void orc_last_current(const orc_ctx* o, double J[2]) {
+    J[0] = o->J_last[0];
+    J[1] = o->J_last[1];
 }
 
 int orc_step(orc_ctx* o, int64_t n_steps) {

@@ -130,6 +130,12 @@ int      orc_moments(const orc_ctx* o, double* n_e, double* n_i, double* mean_ep
                      orc_moment_info* info);
 void     orc_reset_moments(orc_ctx* o);
 
+/* Discharge current density (section "Boundary conditions", equation for J(t)) over the step of
+ * the last solve, J = eps0 dE/dt + e0 (Gamma_i - Gamma_e), in A m^-2: J[0] at z = 0 (the
+ * powered electrode, the paper's definition), J[1] the same expression at z = d. Both are zero
+ * after the first solve of a run (no previous field).                                         */
+void     orc_last_current(const orc_ctx* o, double J[2]);
+
 /* Building blocks, exported for the pins. */
 void     orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 float    orc_uniform(uint32_t x);

@@ -44,7 +44,9 @@ class PicOptions(C.Structure):
 class PicMoments(C.Structure):
     _fields_ = [("n_e", C.c_void_p), ("n_i", C.c_void_p), ("mean_eps", C.c_void_p), ("steps", C.c_int64),
                 ("count", C.c_int64 * 2), ("absorbed", (C.c_double * 2) * 2), ("flux", (C.c_double * 2) * 2),
-                ("surface_charge", C.c_double)]
+                ("surface_charge", C.c_double), ("periods_done", C.c_int64), ("steady_period", C.c_int64),
+                ("steady_metric", C.c_double), ("steady", C.c_int32), ("reserved", C.c_int32),
+                ("J_amp", C.c_double), ("J_last", C.c_double)]
 
 
 class PicCounters(C.Structure):
@@ -112,6 +114,8 @@ PROTOTYPES = {
     "pic_debug_math": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
     "pic_sort_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp]),
     "pic_period_counts": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
+    "pic_current": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
+    "pic_current_amplitude": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
     "pic_load_profiles": (C.c_int, [_vp, _i32, _vp]),
     # include/mlp.h
     "mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _vp, _i32, _u64, _vp]),

@@ -390,6 +390,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.hdx_eps = der.dx / (2.0 * H_EPS0);
         D.inv_N = 1.0 / (double)d.n_cells;
         D.V0tab = nullptr;
+        D.jtab = nullptr;
         {
             // one rf period of V(t) when dt divides it (f dt steps_per_period = 1 to 1e-12)
             const int spp = d.weights.steps_per_period;
@@ -405,8 +406,27 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
                     return s_;
                 }
                 D.V0tab = dv;
+                // sin and cos at the step midpoints (first harmonic of J(t))
+                std::vector<double> jt(2 * (size_t)spp);
+                for (int k = 0; k < spp; ++k) {
+                    const double ph = 2.0 * H_PI * d.f_rf_Hz * (((double)k + 0.5) * d.dt_s);
+                    jt[2 * (size_t)k] = std::sin(ph);
+                    jt[2 * (size_t)k + 1] = std::cos(ph);
+                }
+                double* dj = nullptr;
+                ALLOC(dj, double*, sizeof(double) * 2 * (size_t)spp);
+                if (cudaMemcpy(dj, jt.data(), sizeof(double) * 2 * (size_t)spp, cudaMemcpyHostToDevice) !=
+                    cudaSuccess) {
+                    pic_status s_ = fail(ctx, PIC_ERR_CUDA, "current table");
+                    pic_destroy(ctx);
+                    return s_;
+                }
+                D.jtab = dj;
             }
         }
+        D.jh = d.weights.steps_per_period > 0 ? 4 * d.weights.steps_per_period : 4096;
+        ALLOC(D.J_hist, double*, sizeof(double) * 2 * (size_t)D.jh);
+        ALLOC(D.J_amp, double*, sizeof(double) * PERIOD_HIST);
         D.has_see = d.weights.gamma_see > 0.0;
         D.tile = (int)tile;
         D.chunk = 32 * o.ppt;
@@ -954,6 +974,86 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
             out->flux[a][b] = steps > 0 ? out->absorbed[a][b] * D.w[a] / ((double)steps * D.dt) : 0.0;
         }
     out->surface_charge = 8.8541878128e-12 * hc.E0_last[d];
+    // rf periods, the steady-state criterion on the per-period mean counts, J(t)
+    const int spp = ctx->dis[d].weights.steps_per_period;
+    const long long done = spp > 0 ? ctx->step / spp : 0;
+    out->periods_done = done;
+    out->steady_period = -1;
+    out->steady_metric = -1.0;
+    out->steady = 0;
+    out->reserved = 0;
+    out->J_amp = 0.0;
+    out->J_last = 0.0;
+    const long long keep = std::min(done, (long long)PERIOD_HIST);
+    if (keep >= 2 * PIC_STEADY_BLOCK) {
+        std::vector<double> pm(2 * (size_t)keep);
+        for (long long k = 0; k < keep; ++k) {  // oldest kept period first
+            const long long per = done - keep + k;
+            CK(cudaMemcpyAsync(&pm[2 * k], D.period_mean + 2 * (per % PERIOD_HIST), 2 * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream), "period counts");
+        }
+        CK(cudaStreamSynchronize(ctx->stream), "period counts");
+        std::vector<double> cum(2 * (size_t)(keep + 1), 0.0);
+        for (long long k = 0; k < keep; ++k)
+            for (int sp = 0; sp < 2; ++sp) cum[2 * (k + 1) + sp] = cum[2 * k + sp] + pm[2 * k + sp];
+        const int W = PIC_STEADY_BLOCK;
+        for (long long k = 2 * W; k <= keep; ++k) {
+            double metric = 0.0;
+            bool pos = true;
+            for (int sp = 0; sp < 2; ++sp) {
+                const double a = (cum[2 * k + sp] - cum[2 * (k - W) + sp]) / W;
+                const double b = (cum[2 * (k - W) + sp] - cum[2 * (k - 2 * W) + sp]) / W;
+                if (!(a > 0)) pos = false;
+                else metric = std::max(metric, std::fabs(a - b) / a);
+            }
+            if (!pos) metric = INFINITY;
+            if (k == keep) out->steady_metric = metric;
+            if (out->steady_period < 0 && metric < PIC_STEADY_TOL) out->steady_period = done - keep + k;
+        }
+        out->steady = out->steady_period >= 0;
+    }
+    if (ctx->step > 0) {
+        double jl[2] = {0.0, 0.0}, ja = 0.0;
+        const long long n = ctx->step - 1;
+        CK(cudaMemcpyAsync(jl, D.J_hist + 2 * (n % D.jh), 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+           "current");
+        if (done > 0 && D.jtab)
+            CK(cudaMemcpyAsync(&ja, D.J_amp + (done - 1) % PERIOD_HIST, sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream), "current amplitude");
+        CK(cudaStreamSynchronize(ctx->stream), "current");
+        out->J_last = jl[0];
+        out->J_amp = ja;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_current(pic_ctx* ctx, int32_t d, int64_t first, int64_t n, double* out,
+                                  int64_t* steps_done) {
+    if (bad_d(ctx, d) || first < 0 || n < 0 || (n && !out)) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    if (steps_done) *steps_done = ctx->step;
+    if (first + n > ctx->step || ctx->step - first > D.jh) return fail(ctx, PIC_ERR_ARG, "steps not available");
+    for (long long k = 0; k < n; ++k) {
+        const long long slot = (first + k) % D.jh;
+        CK(cudaMemcpy(out + 2 * k, D.J_hist + 2 * slot, 2 * sizeof(double), cudaMemcpyDeviceToHost), "current");
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_current_amplitude(pic_ctx* ctx, int32_t d, int64_t first, int64_t n, double* out,
+                                            int64_t* periods_done) {
+    if (bad_d(ctx, d) || first < 0 || n < 0 || (n && !out)) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    const int spp = ctx->dis[d].weights.steps_per_period;
+    const long long done = spp > 0 ? ctx->step / spp : 0;
+    if (periods_done) *periods_done = done;
+    if (!D.jtab && n > 0) return fail(ctx, PIC_ERR_STATE, "the time step does not divide the rf period");
+    if (first + n > done || done - first > PERIOD_HIST) return fail(ctx, PIC_ERR_ARG, "periods not available");
+    for (long long k = 0; k < n; ++k)
+        CK(cudaMemcpy(out + k, D.J_amp + (first + k) % PERIOD_HIST, sizeof(double), cudaMemcpyDeviceToHost),
+           "current amplitude");
     return PIC_OK;
 }
 

@@ -9,7 +9,7 @@ namespace pic {
 constexpr int MAXD = 64;      // discharges per context
 constexpr int MAXN = 4096;    // cells per discharge
 constexpr int SLICE = 4096;   // sweep chunks per slice of the segment-table pass
-constexpr int NCNT = 16;      // event counters per discharge
+constexpr int NCNT = 18;      // event counters per discharge
 
 // Event counter slots (u64 each), per discharge.
 enum {
@@ -19,7 +19,8 @@ enum {
     CNT_NULL_INEL = 10,
     CNT_SEE = 11,
     CNT_CAND = 12,     // 2
-    CNT_CLAMP = 14     // 2
+    CNT_CLAMP = 14,    // 2
+    CNT_SEE_SIDE = 16  // 2: secondary electrons emitted at electrode 0, 1
 };
 
 // Device error bits (Ctl::error).
@@ -104,6 +105,12 @@ struct Disc {
     unsigned __int128* acc_Dprev;
     unsigned long long* cnt;  // NCNT counters
     double* period_mean;      // [PERIOD_HIST][2] mean superparticle count of every rf period
+    // discharge current density J(t) at z = 0 and z = d of every step, ring of jh steps, and the
+    // first-harmonic amplitude of J at z = 0 of every rf period (ring of PERIOD_HIST)
+    double* J_hist;           // [jh][2]
+    int jh;
+    const double* jtab;       // sin, cos of 2 pi f (k + 1/2) dt, k < steps_per_period, or null
+    double* J_amp;            // [PERIOD_HIST]
 };
 
 // Control block; one per context, in device memory.
@@ -119,6 +126,12 @@ struct Ctl {
     int nseg[MAXD][2];        // segments per store
     long long acc_steps[MAXD];
     double E0_last[MAXD];
+    // J(t): electrode fields and event counters at the last solve, first-harmonic sums of the
+    // current period (sin, cos)
+    int have_solve[MAXD];
+    double E_wall[MAXD][2];
+    unsigned long long cnt_solve[MAXD][6];
+    double J_sum[MAXD][2];
     double period_acc[MAXD][2];   // sum of the counts over the steps of the current rf period
     unsigned sort_rows_done[MAXD][2];  // k_sort_rows CTAs finished, per store (reset by the last)
 };

@@ -410,6 +410,7 @@ __device__ __forceinline__ bool emit_see(const Seg<T>& S, uint32_t slot, long lo
     p = Part<T>{ce, fe, mul_(K.sig_see, (T)t0), mul_(K.sig_see, (T)t1), side == 0 ? vn : -vn};
     hist_add(S.Dother, ce, cic_F(fe));
     atomicAdd(&sC[CNT_SEE], 1u);
+    atomicAdd(&sC[CNT_SEE_SIDE + side], 1u);
     return true;
 }
 
@@ -1111,9 +1112,59 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
 // (slow on this part) is used once per node, with no division (host reciprocals).
 constexpr int POST_BLOCK = 512;  // threads per k_post CTA
 constexpr int FIELD_SCAN = 256;  // threads of the integer scan
+
+// Discharge current density over step n (section "Boundary conditions", equation for J(t)):
+// J = eps0 dE/dt + e0 (Gamma_i - Gamma_e), with the particle fluxes counted positive towards +z
+// from the step's absorbed and emitted superparticles: at z = 0 an absorbed ion (moving towards
+// -z) carries -e w_i, an absorbed electron +e w_e, an emitted secondary electron (towards +z)
+// -e w_e; at z = d the absorbed particles' signs flip and emitted electrons move towards -z.
+// FP64, by one thread of the field CTA after the new electrode fields Ew are known. The initial
+// solve of a load (mode bit 4) only records the fields and counters. On a full step the current at
+// z = 0 is also projected onto the rf period's first harmonic (sin and cos at the step midpoint);
+// at the end of a period the amplitude is stored.
+__device__ __noinline__ void discharge_current(const Disc& D, int d, Ctl* ctl, int mode, long long step,
+                                               const double* Ew) {
+    unsigned long long c[6];
+    for (int k = 0; k < 4; ++k) c[k] = D.cnt[CNT_ABS + k];  // [species][electrode]
+    c[4] = D.cnt[CNT_SEE_SIDE];
+    c[5] = D.cnt[CNT_SEE_SIDE + 1];
+    if (!(mode & 4)) {  // a solve after a sweep (or a stand-alone solve): the current of step n
+        double J0 = 0.0, JN = 0.0;  // no earlier solve: no current
+        if (ctl->have_solve[d]) {
+            double dA[4], dS[2];
+            for (int k = 0; k < 4; ++k) dA[k] = (double)(c[k] - ctl->cnt_solve[d][k]);
+            dS[0] = (double)(c[4] - ctl->cnt_solve[d][4]);
+            dS[1] = (double)(c[5] - ctl->cnt_solve[d][5]);
+            const double we = D.w[0], wi = D.w[1], dt = D.dt;
+            const double cond0 = E_CHARGE * (we * dA[0] - wi * dA[2] - we * dS[0]) / dt;
+            const double condN = E_CHARGE * (wi * dA[3] - we * dA[1] + we * dS[1]) / dt;
+            J0 = EPS0 * (Ew[0] - ctl->E_wall[d][0]) / dt + cond0;
+            JN = EPS0 * (Ew[1] - ctl->E_wall[d][1]) / dt + condN;
+        }
+        const long long slot = step % D.jh;
+        D.J_hist[2 * slot] = J0;
+        D.J_hist[2 * slot + 1] = JN;
+        if ((mode & 2) && D.jtab && D.steps_per_period > 0) {
+            const int spp = D.steps_per_period;
+            const int k = (int)(step % spp);
+            ctl->J_sum[d][0] += J0 * D.jtab[2 * k];
+            ctl->J_sum[d][1] += J0 * D.jtab[2 * k + 1];
+            if (k == spp - 1) {
+                const double a = 2.0 * ctl->J_sum[d][0] / spp, b = 2.0 * ctl->J_sum[d][1] / spp;
+                D.J_amp[(step / spp) % PERIOD_HIST] = sqrt(a * a + b * b);
+                ctl->J_sum[d][0] = 0.0;
+                ctl->J_sum[d][1] = 0.0;
+            }
+        }
+    }
+    ctl->have_solve[d] = 1;
+    ctl->E_wall[d][0] = Ew[0];
+    ctl->E_wall[d][1] = Ew[1];
+    for (int k = 0; k < 6; ++k) ctl->cnt_solve[d][k] = c[k];
+}
 template <typename T>
 __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restrict__ ctl, int mode, int tid, int lane,
-                                            int warp, double* s_f, int max_N, PSum* s_ps) {
+                                            int warp, double* s_f, int max_N, PSum* s_ps, double* s_Ew) {
     constexpr int BLOCK = POST_BLOCK;
     // every field of the discharge is read before the first store
     const int N = D.N;
@@ -1199,6 +1250,7 @@ __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restric
             const double rw = __fma_rn(pw1, (double)sdi[0], -pw0 * (double)sde[0]);
             E = -g1 * inv_dx - rw * hdx_eps;
             ctl->E0_last[d] = E;
+            s_Ew[0] = E;
         } else {
             ph = V0 + (double)j * g1 - Sprev;
             E = ((g1 - Rprev) + (g1 - Rj)) * m_inv_2dx;
@@ -1215,7 +1267,10 @@ __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restric
         phi[N] = 0.0;
         E64[N] = E;
         Ef[N] = (T)E;
+        s_Ew[1] = E;
     }
+    asm volatile("bar.sync 1, %0;" ::"n"(FIELD_SCAN) : "memory");
+    if (tid == 0) discharge_current(D, d, ctl, mode, step, s_Ew);
 }
 
 template <typename T>
@@ -1224,6 +1279,7 @@ __global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ di
     constexpr int BLOCK = POST_BLOCK;
     extern __shared__ __align__(16) double s_f[];
     __shared__ PSum s_ps[FIELD_SCAN / 32 + 1];
+    __shared__ double s_Ew[2];
     __shared__ int s_err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     grid_dep_sync();
@@ -1238,7 +1294,7 @@ __global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ di
             if (e2 && lane == 0) atomicOr(&s_err, e2);
         }
     } else if (!(mode & 8) && (blockIdx.y & 1) == 0) {
-        field_solve<T>(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, mode, tid, lane, warp, s_f, max_N, s_ps);
+        field_solve<T>(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, mode, tid, lane, warp, s_f, max_N, s_ps, s_Ew);
     }
     __syncthreads();
     // the last CTA advances the step (bit 2) and, after a sweep, the slice parity. Every CTA has

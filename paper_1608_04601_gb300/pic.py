@@ -214,7 +214,9 @@ class Simulation:
         self._ck(self.L.pic_moments(self.h, d, C.byref(m)))
         return {"n_e": ne, "n_i": ni, "mean_eps": me, "steps": m.steps, "count": list(m.count),
                 "absorbed": [[m.absorbed[a][b] for b in range(2)] for a in range(2)],
-                "flux": [[m.flux[a][b] for b in range(2)] for a in range(2)], "surface_charge": m.surface_charge}
+                "flux": [[m.flux[a][b] for b in range(2)] for a in range(2)], "surface_charge": m.surface_charge,
+                "periods_done": m.periods_done, "steady_period": None if m.steady_period < 0 else m.steady_period,
+                "steady_metric": m.steady_metric, "steady": bool(m.steady), "J_amp": m.J_amp, "J_last": m.J_last}
 
     def reset_moments(self):
         self._ck(self.L.pic_reset_moments(self.h))
@@ -236,6 +238,28 @@ class Simulation:
         out = np.zeros((max(n, 0), 2))
         if n > 0:
             self._ck(self.L.pic_period_counts(self.h, d, first, n, _ptr(out), C.byref(done)))
+        return out
+
+    def current(self, d: int = 0, first: int = 0, n=None) -> np.ndarray:
+        """(steps, 2) discharge current density J(t) at z = 0 and z = d of steps first.., A/m^2."""
+        done = C.c_int64()
+        self._ck(self.L.pic_current(self.h, d, 0, 0, None, C.byref(done)))
+        if n is None:
+            n = done.value - first
+        out = np.zeros((max(n, 0), 2))
+        if n > 0:
+            self._ck(self.L.pic_current(self.h, d, first, n, _ptr(out), C.byref(done)))
+        return out
+
+    def current_amplitude(self, d: int = 0, first: int = 0, n=None) -> np.ndarray:
+        """First-harmonic amplitude of J(t) at z = 0 of each completed rf period, A/m^2."""
+        done = C.c_int64()
+        self._ck(self.L.pic_current_amplitude(self.h, d, 0, 0, None, C.byref(done)))
+        if n is None:
+            n = done.value - first
+        out = np.zeros(max(n, 0))
+        if n > 0:
+            self._ck(self.L.pic_current_amplitude(self.h, d, first, n, _ptr(out), C.byref(done)))
         return out
 
     def sweep_timing(self, enable: bool = True):

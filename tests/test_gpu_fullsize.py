@@ -68,10 +68,12 @@ def test_fullsize_steps_bit_exact(P, case):
             assert np.array_equal(a["c"], b["c"]), f"step {n} sp{sp}: order/cells"
             for k in ("f", "vx", "vy", "vz"):
                 assert np.array_equal(a[k], b[k]), f"step {n} sp{sp}: {k}"
-        # the two FP64 solves agree closely; the next step starts from the oracle's field on both
+        # the two FP64 solves agree to their rounding (the oracle's tridiagonal elimination loses up
+        # to a few units of 2^-52 per node, so the bound grows with N); the next step starts from
+        # the oracle's field on both
         E, E64, _ = sim.get_field(0)
         R64 = ref.get_field64()
-        assert np.max(np.abs(E64 - R64)) <= 1e-12 * np.max(np.abs(R64))
+        assert np.max(np.abs(E64 - R64)) <= 4e-15 * d.n_cells * np.max(np.abs(R64))
         sim.set_field(0, ref.get_field())
     ma, mb = sim.moments(0), ref.moments()
     assert ma["steps"] == mb["steps"] == steps - 1
