@@ -47,8 +47,8 @@ struct pic_ctx {
     unsigned* sort_tot = nullptr;
     long long* sort_hoff = nullptr;
     unsigned* sort_kr = nullptr;    // per slot of every store: cell | rank in its sort tile << 16
-    unsigned* sort_off = nullptr;   // per slot of every store: record offset
-    long long* sort_eoff = nullptr; // first slot of each store in sort_kr / sort_off
+    long long* sort_eoff = nullptr; // first slot of each store in sort_kr
+    int repack_every = 0;           // order-preserving repack after every step n with (n+1) % this == 0
     std::vector<void*> allocs;
     int cur = 0;
     long long step = 0;
@@ -184,6 +184,24 @@ static void fill_consts(Consts<T>& k, const pic_derived& o, const pic_discharge&
     k.gamma = (T)d.weights.gamma_see;
     k.sig0[0] = (T)o.sig_e0;
     k.sig0[1] = (T)o.sig_i0;
+}
+
+// Region bookkeeping of a store of capacity cap (superparticles) with sweep chunks of `chunk` slots
+// and a newborn area of bcap records: a store may hold rmax regions (a quarter more than a dense
+// store of cap particles needs, and 64), the output area has room for the newborn chunks of one step
+// beyond that, and a layout never has more than maxchunks chunks.
+struct RegionSizes {
+    long long rmax, bchunks, ralloc, R0, rcap, maxchunks;
+};
+static RegionSizes region_sizes(long long cap, long long chunk, long long bcap) {
+    RegionSizes r;
+    r.rmax = (cap + chunk - 1) / chunk + (cap + 4 * chunk - 1) / (4 * chunk) + 64;
+    r.bchunks = (bcap + chunk - 1) / chunk + 1;
+    r.ralloc = r.rmax + r.bchunks;
+    r.R0 = r.ralloc * chunk;
+    r.rcap = r.R0 + r.bchunks * chunk + chunk;
+    r.maxchunks = r.ralloc + r.bchunks;
+    return r;
 }
 
 extern "C" void pic_destroy(pic_ctx* ctx) {
@@ -329,16 +347,21 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
     }
 
     const long long tile = (long long)o.block * o.ppt;
+    const long long chunk = 32ll * o.ppt;
+    auto bcap_of = [&](int i) {
+        return std::max(ctx->dis[i].weights.capacity_e, ctx->dis[i].weights.capacity_i) / 8 + 4096;
+    };
     // sort scratch: per store (cells x sort tiles) counts
     {
         std::vector<long long> hoff(2 * MAXD, 0);
         long long acc = 0;
-        const long long st = sort_tile();
+        const long long st = sort_tile_chunks((int)chunk);
         for (int i = 0; i < n_dis; ++i)
             for (int sp = 0; sp < 2; ++sp) {
                 hoff[2 * i + sp] = acc;
                 const long long cap = sp ? ctx->dis[i].weights.capacity_i : ctx->dis[i].weights.capacity_e;
-                acc += (long long)ctx->dis[i].n_cells * ((cap + st - 1) / st + 1);
+                const RegionSizes rs = region_sizes(cap, chunk, bcap_of(i));
+                acc += (long long)ctx->dis[i].n_cells * ((rs.maxchunks + st - 1) / st + 1);
             }
         ALLOC(ctx->sort_hist, unsigned*, sizeof(unsigned) * (size_t)std::max(acc, 1ll));
         ALLOC(ctx->sort_tot, unsigned*, sizeof(unsigned) * (size_t)(2 * MAXD) * MAXN);
@@ -353,7 +376,6 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
                 ea += sp ? ctx->dis[i].weights.capacity_i : ctx->dis[i].weights.capacity_e;
             }
         ALLOC(ctx->sort_kr, unsigned*, sizeof(unsigned) * (size_t)std::max(ea, 1ll));
-        ALLOC(ctx->sort_off, unsigned*, sizeof(unsigned) * (size_t)std::max(ea, 1ll));
         ALLOC(ctx->sort_eoff, long long*, sizeof(long long) * 2 * MAXD);
         cudaMemcpyAsync(ctx->sort_eoff, eoff.data(), sizeof(long long) * 2 * MAXD, cudaMemcpyHostToDevice,
                         ctx->stream);
@@ -438,13 +460,15 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.Ti = g.Ti;
         D.cap[0] = d.weights.capacity_e;
         D.cap[1] = d.weights.capacity_i;
-        D.bcap = std::max(D.cap[0], D.cap[1]) / 8 + 4096;
+        D.bcap = bcap_of(i);
         const size_t rec = 4 * rsz;
         for (int sp = 0; sp < 2; ++sp) {
-            // record buffers: one chunk region per input chunk, then the newborn region
-            D.max_tiles[sp] = (D.cap[sp] + tile - 1) / tile;
-            D.R0[sp] = D.max_tiles[sp] * tile;
-            D.rcap[sp] = D.R0[sp] + D.bcap;
+            // record buffers: one region per sweep chunk, then the newborn area
+            const RegionSizes rs = region_sizes(D.cap[sp], chunk, D.bcap);
+            D.rmax[sp] = rs.rmax;
+            D.ralloc[sp] = rs.ralloc;
+            D.R0[sp] = rs.R0;
+            D.rcap[sp] = rs.rcap;
             if (D.rcap[sp] > 0x7FFFFFF0ll) {
                 pic_status s_ = fail(ctx, PIC_ERR_ARG, "capacity too large for 32-bit segment offsets");
                 pic_destroy(ctx);
@@ -457,12 +481,10 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
                 ALLOC(D.p[b][sp], void*, rec * (size_t)(D.rcap[sp] + 16));
             }
         for (int sp = 0; sp < 2; ++sp) {
-            const size_t mt = (size_t)D.max_tiles[sp], mc = mt * (size_t)D.warps;
-            ALLOC(D.bc[sp], int32_t*, sizeof(int32_t) * (mt * tile + 16));
-            ALLOC(D.bp[sp], void*, rec * (mt * tile + 16));
-            ALLOC(D.seg_start[sp], int*, sizeof(int) * (mc + 3));
-            ALLOC(D.seg_src[sp], int*, sizeof(int) * (mc + 2));
-            ALLOC(D.first_seg[sp], int*, sizeof(int) * (mc + 2));
+            const size_t mc = (size_t)D.ralloc[sp], nrec = mc * (size_t)chunk;
+            ALLOC(D.bc[sp], int32_t*, sizeof(int32_t) * (nrec + 16));
+            ALLOC(D.bp[sp], void*, rec * (nrec + 16));
+            ALLOC(D.start[sp], int*, sizeof(int) * (mc + 2));
             ALLOC(D.cnt_main[sp], int*, sizeof(int) * (mc + 1));
             ALLOC(D.cnt_birth[sp], int*, sizeof(int) * (mc + 1));
             const size_t ns = (mc + SLICE - 1) / SLICE + 1;
@@ -475,8 +497,8 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
                 return s_;
             }
             if (sp == 0) {
-                ALLOC(D.sc, int32_t*, sizeof(int32_t) * (mt * tile + 16));
-                ALLOC(D.sp_, void*, rec * (mt * tile + 16));
+                ALLOC(D.sc, int32_t*, sizeof(int32_t) * (nrec + 16));
+                ALLOC(D.sp_, void*, rec * (nrec + 16));
                 ALLOC(D.cnt_same, int*, sizeof(int) * (mc + 1));
             }
         }
@@ -508,7 +530,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
             h.count[i][1] = o.load ? ctx->dis[i].weights.n_i0 : 0;
         }
         cudaMemcpyAsync(ctx->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream);
-        ce = launch_set_dense(ctx->d_discs, n_dis, ctx->d_ctl, ctx->stream);
+        ce = launch_set_dense(ctx->d_discs, n_dis, ctx->d_ctl, 0, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
         if (ce != cudaSuccess) {
             pic_status s = cuda_fail(ctx, ce, "store set-up");
@@ -518,7 +540,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
     }
     // sweep grid: persistent CTAs
     {
-        int occ = sweep_occupancy(ctx->fp64, o.block, o.ppt, ctx->max_N);
+        int occ = sweep_occupancy(ctx->fp64, o.block, o.ppt, ctx->max_N, n_dis);
         if (occ < 1) occ = 1;
         int per = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
         ctx->sweep_grid = std::max(1, ctx->num_sms * per);
@@ -540,6 +562,20 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
     ctx->cur = 0;
     ctx->step = 0;
     ctx->deposits_zero = true;
+    // Sweeps append regions (one per chunk, plus the newborns' chunks); a sort makes a store dense
+    // again. When it runs rarer than every 64 steps, an order-preserving repack does, every R steps
+    // with R the largest divisor of the rf period up to 64 (so that one-period graphs stay periodic).
+    {
+        const int K = o.sort_every, P = ctx->dis[0].weights.steps_per_period;
+        ctx->repack_every = 0;
+        if (!(K > 0 && K <= 64)) {
+            int R = 64;
+            if (P > 0)
+                for (R = std::min(P, 64); P % R != 0; --R) {
+                }
+            ctx->repack_every = R;
+        }
+    }
     *out = ctx;
     return PIC_OK;
 }
@@ -614,15 +650,23 @@ static pic_status enqueue_finalize(pic_ctx* ctx, int mode) {
 static pic_status enqueue_sort(pic_ctx* ctx) {
     const int gx = std::max(1, ctx->num_sms * 2);
     CK(launch_sort(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->cur, 1 - ctx->cur, ctx->sort_hist,
-                   ctx->sort_hoff, ctx->sort_tot, ctx->sort_kr, ctx->sort_off, ctx->sort_eoff, ctx->max_N, gx,
+                   ctx->sort_hoff, ctx->sort_tot, ctx->sort_kr, ctx->sort_eoff, ctx->max_N, gx,
                    ctx->stream),
        "sort launch");
     ctx->cur = 1 - ctx->cur;
     return PIC_OK;
 }
 
+static pic_status enqueue_repack(pic_ctx* ctx) {
+    const int gx = std::max(1, ctx->num_sms * 4);
+    CK(launch_repack(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->cur, 1 - ctx->cur, gx, ctx->stream),
+       "repack launch");
+    ctx->cur = 1 - ctx->cur;
+    return PIC_OK;
+}
+
 // Sweep + births + solve: the sweep reads buffer cur and writes 1-cur; the
-// finalize appends births into 1-cur; cur flips.
+// finalize appends births into 1-cur; cur flips. Then the sort, or the repack, when due.
 static pic_status enqueue_step(pic_ctx* ctx) {
     pic_status s = enqueue_sweep(ctx);
     if (s != PIC_OK) return s;
@@ -630,12 +674,13 @@ static pic_status enqueue_step(pic_ctx* ctx) {
     if (s != PIC_OK) return s;
     const int K = ctx->opt.sort_every;
     if (K > 0 && ctx->step % K == 0) return enqueue_sort(ctx);
+    if (ctx->repack_every > 0 && ctx->step % ctx->repack_every == 0) return enqueue_repack(ctx);
     return PIC_OK;
 }
 
 static pic_status run_graph_period(pic_ctx* ctx, int P) {
-    const int K = ctx->opt.sort_every;
-    const int phase = K > 0 ? (int)(ctx->step % K) : 0;
+    // the period's sorts and repacks follow from the step at which it starts
+    const int phase = (int)(ctx->step % P);
     for (auto& g : ctx->graphs)
         if (g.cur_in == ctx->cur && g.phase == phase) {
             CK(cudaGraphLaunch(g.exec, ctx->stream), "graph launch");
@@ -816,7 +861,7 @@ extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     }
     // count and segment table on the device (a rejected upload leaves an empty store), then one
     // synchronisation for the check word
-    CK(launch_finish_upload(ctx->d_discs, ctx->d_ctl, d, sp, n, bad, ctx->stream), "state finish");
+    CK(launch_finish_upload(ctx->d_discs, ctx->d_ctl, d, sp, n, bad, ctx->cur, ctx->stream), "state finish");
     s = pinned(ctx, 64);
     if (s != PIC_OK) return s;
     unsigned* hbad = static_cast<unsigned*>(ctx->h_pin);
@@ -1218,7 +1263,7 @@ extern "C" pic_status pic_load_profiles(pic_ctx* ctx, int32_t n_pts, const doubl
     ctx->cur = 0;
     if (e == cudaSuccess)
         e = launch_load_profile(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->seed, ddesc, gx, ctx->stream);
-    if (e == cudaSuccess) e = launch_set_dense(ctx->d_discs, nd, ctx->d_ctl, ctx->stream);
+    if (e == cudaSuccess) e = launch_set_dense(ctx->d_discs, nd, ctx->d_ctl, 0, ctx->stream);
     if (e == cudaSuccess) e = launch_deposit(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, ctx->max_N, gx, ctx->stream);
     if (e == cudaSuccess) e = launch_finalize(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, 4, 0, ctx->max_N, ctx->stream);
     if (e == cudaSuccess) e = launch_backkick(ctx->fp64, ctx->d_discs, nd, ctx->d_ctl, 0, gx, ctx->stream);

@@ -44,15 +44,22 @@ struct Consts {
     T sig0[2];         // initial Maxwellians
 };
 
-// A particle store (one species of one discharge) is a sequence of segments
-// of a record buffer: segment k holds slots [seg_start[k], seg_start[k+1]) at
-// buffer offsets seg_src[k] + (slot - seg_start[k]). After a load, an upload
-// or a sort the store is one dense segment; after a sweep every input tile of
-// TILE slots owns a region of 2 TILE records of the output buffer (a particle
-// and its same-species newborn at most), and the births of the other species
-// follow as one last segment in a region after all tile regions. Slots, and so
-// the random streams, number the particles exactly as a dense compacted store
-// would.
+// A particle store (one species of one discharge) is a sequence of chunks of at most CHUNK
+// slots; a sweep processes one chunk per warp and writes chunk k's survivors, compacted in slot
+// order, to region k of the other buffer (records [k CHUNK, (k+1) CHUNK)). The layout of a buffer
+// is (K, M, D0): chunks k < K are regions, chunk k holding slots [start[k], start[k+1]) at records
+// k CHUNK + (slot - start[k]), start[K] = M; chunks k >= K are the dense part, slots
+// M + (k - K) CHUNK + i at records D0 + (k - K) CHUNK + i. After a sweep the regions are the last
+// sweep's chunks and the dense part its newborns, copied to D0 = R0; after a load, an upload, a sort
+// or a repack the buffer is dense (K = 0, M = 0, D0 = 0). Slots, and so the random streams, number
+// the particles exactly as a densely compacted store would.
+struct Lay {
+    int K;                    // region chunks
+    int pad_;
+    long long M;              // slots in the regions
+    long long D0;             // record offset of the dense part
+};
+
 struct Disc {
     int N, n_exc, n_pts, gas;
     uint32_t thr[2];          // null-collision candidate thresholds (of 2^32)
@@ -74,15 +81,14 @@ struct Disc {
     int32_t* c[2][2];         // [buffer][species] cell index
     void* p[2][2];            // [buffer][species] {f, vx, vy, vz} records
     long long cap[2];         // capacity per species (superparticles)
-    long long max_tiles[2];   // ceil(cap / tile)
-    long long R0[2];          // offset of the newborn region in a record buffer: max_tiles tile
-    long long rcap[2];        // records per buffer: R0 + bcap (chunk k's survivors at [k chunk, ...))
-    int* seg_start[2];        // [max_tiles warps + 2] segment table of the current store
-    int* seg_src[2];          // [max_tiles warps + 1]
-    int* first_seg[2];        // [max_tiles warps + 1] segment holding slot j chunk
-    int* cnt_main[2];         // [max_tiles warps] survivors of each sweep chunk
-    int* cnt_birth[2];        // [max_tiles warps] other-species newborns of each sweep chunk
-    int* cnt_same;            // [max_tiles warps] ionization electrons of each electron-sweep chunk
+    long long rmax[2];        // regions a store may have (more: capacity error; a repack or sort resets)
+    long long ralloc[2];      // regions of a buffer: rmax + the newborn chunks of one step
+    long long R0[2];          // ralloc chunk: offset of the newborn (dense) area of a record buffer
+    long long rcap[2];        // records per buffer: R0 + the newborn area + one chunk
+    int* start[2];            // [ralloc + 1] first slot of each region chunk; start[K] = M
+    int* cnt_main[2];         // [ralloc] survivors of each sweep chunk
+    int* cnt_birth[2];        // [ralloc] other-species newborns of each sweep chunk
+    int* cnt_same;            // [ralloc] ionization electrons of each electron-sweep chunk
     int32_t* bc[2];           // newborns of the other species, by parent species:
     void* bp[2];              //   chunk k owns records [k chunk, (k+1) chunk)
     int32_t* sc;              // ionization electrons of the electron sweep, same chunk regions
@@ -121,9 +127,9 @@ struct Ctl {
     unsigned int fin_done;    // k_post CTAs finished
     int error;                // ERR_* bits
     long long count[MAXD][2]; // superparticles per store
-    long long count_in[MAXD][2]; // the counts the last sweep read (its tiles)
-    int slice_par;               // parity of the slice sums the next sweep adds into
-    int nseg[MAXD][2];        // segments per store
+    Lay lay[MAXD][2][2];      // [discharge][species][buffer] layout of the store in that buffer
+    int chunks_in[MAXD][2];   // chunks the last sweep processed, per store
+    int slice_par;            // parity of the slice sums the next sweep adds into
     long long acc_steps[MAXD];
     double E0_last[MAXD];
     // J(t): electrode fields and event counters at the last solve, first-harmonic sums of the
@@ -135,6 +141,11 @@ struct Ctl {
     double period_acc[MAXD][2];   // sum of the counts over the steps of the current rf period
     unsigned sort_rows_done[MAXD][2];  // k_sort_rows CTAs finished, per store (reset by the last)
 };
+
+// Chunks of a store with layout L and count n.
+__host__ __device__ inline long long chunks_of(const Lay& L, long long n, int chunk) {
+    return (long long)L.K + (n - L.M + chunk - 1) / chunk;
+}
 
 constexpr int PERIOD_HIST = 1 << 16;  // rf periods of mean counts kept per discharge (ring)
 

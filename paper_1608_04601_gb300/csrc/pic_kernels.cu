@@ -71,72 +71,22 @@ struct Seg {
     unsigned long long* Dother;
     unsigned long long* Qg;
     unsigned long long* cnt;
-    const int* seg_start;
-    const int* seg_src;
-    const int* first_seg;
-    int nseg;
+    const int* start;  // region starts of the input layout
+    int K;             // region chunks of the input layout
+    long long M, D0;   // slots in the regions, record offset of the dense part
+    long long ralloc;  // output regions
     int* cnt_main;
     int* cnt_birth;
     int* cnt_same;
     unsigned* slice_tot;
 };
 
-// Slot -> record offset through a store's segment table for a warp that walks
-// groups of 32 consecutive slots upwards (lane l holds slot s0 + l): slot s
-// lives at seg_src[k] + (s - seg_start[k]), k the last segment with
-// seg_start[k] <= s. The 32 segments from the first one of the walk sit in
-// registers (lane j holds segment k0 + j); later ones are read from memory.
 // Programmatic dependent launch (the kernels of a step, launched by launch_pdl): wait until the
 // previous kernel in the stream has completed and its writes are visible. Every such kernel calls
 // this before its first memory access (a no-op for a kernel launched without the attribute). No
 // kernel triggers its dependents early: they launch as its CTAs exit, so no CTA of a later kernel
 // shares an SM's L1 with a CTA that may still read data the kernel in between rewrites.
 __device__ __forceinline__ void grid_dep_sync() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-struct SegCursor {
-    const int* start;
-    const int* src;
-    int nseg, k0, ws, wr, ks;
-
-    // first_slot < count: first slot of the walk; first_seg[j] = segment holding slot j chunk
-    __device__ __forceinline__ void init(const int* seg_start, const int* seg_src, const int* first_seg, int nseg_,
-                                         unsigned first_slot, int chunk, int lane) {
-        start = seg_start;
-        src = seg_src;
-        nseg = nseg_;
-        k0 = 0;
-        ws = 0;
-        wr = 0;
-        if (nseg > 1) {
-            k0 = __ldg(&first_seg[first_slot / (unsigned)chunk]);
-            ws = __ldg(&start[min(k0 + lane, nseg)]);
-            wr = __ldg(&src[min(k0 + lane, nseg - 1)]);
-        }
-        ks = k0;
-    }
-    __device__ __forceinline__ unsigned start_of(int k) const {  // k uniform across the warp
-        const int v = __shfl_sync(0xFFFFFFFFu, ws, (k - k0) & 31);
-        return (unsigned)(k - k0 < 32 ? v : __ldg(&start[k]));
-    }
-    // Called by the whole warp with s0 uniform, s0 below the count and at or above the last s0.
-    __device__ __forceinline__ unsigned offset(unsigned s0, unsigned slot) {
-        if (nseg <= 1) return slot;
-        while (ks + 1 < nseg && start_of(ks + 1) <= s0) ++ks;
-        int my = ks;
-        for (int nx = ks + 1; nx < nseg; ++nx) {
-            const unsigned b = start_of(nx);
-            if (b >= s0 + 32) break;
-            if (b <= slot) my = nx;
-        }
-        const int dk = my - k0;
-        int sr = __shfl_sync(0xFFFFFFFFu, wr, dk & 31), st = __shfl_sync(0xFFFFFFFFu, ws, dk & 31);
-        if (dk >= 32) {
-            sr = __ldg(&src[my]);
-            st = __ldg(&start[my]);
-        }
-        return (unsigned)sr + (slot - (unsigned)st);
-    }
-};
 
 template <typename T>
 __device__ __forceinline__ int drift(int N, T dtdx, int c, T f, T vz, int& cn, T& fn, int& err) {
@@ -231,29 +181,61 @@ __device__ __forceinline__ void warp_hist(unsigned long long* h, int key, unsign
     }
 }
 
-// One collision candidate, queued by its warp in shared memory: the owner
-// writes the particle (cell, offset, gathered field, v_n); the lane that
-// processes the collision writes back the new velocity and flags the newborns
-// it left, after their first drift, in its scratch pair.
+template <typename T>
+__device__ __forceinline__ void store_rec(int32_t* c, void* p, unsigned i, const Part<T>& q);
+template <>
+__device__ __forceinline__ void store_rec<float>(int32_t* c, void* p, unsigned i, const Part<float>& q) {
+    c[i] = q.c;
+    reinterpret_cast<float4*>(p)[i] = make_float4(q.f, q.vx, q.vy, q.vz);
+}
+template <>
+__device__ __forceinline__ void store_rec<double>(int32_t* c, void* p, unsigned i, const Part<double>& q) {
+    c[i] = q.c;
+    double2* pp = reinterpret_cast<double2*>(p) + 2 * i;
+    pp[0] = make_double2(q.f, q.vx);
+    pp[1] = make_double2(q.vy, q.vz);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_rec(const void* p, unsigned i, T& f, T& vx, T& vy, T& vz);
+template <>
+__device__ __forceinline__ void load_rec<float>(const void* p, unsigned i, float& f, float& vx, float& vy,
+                                                float& vz) {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(p) + i);
+    f = a.x; vx = a.y; vy = a.z; vz = a.w;
+}
+template <>
+__device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, double& f, double& vx, double& vy,
+                                                 double& vz) {
+    const double2* pp = reinterpret_cast<const double2*>(p) + 2 * i;
+    const double2 a = __ldcs(pp), b = __ldcs(pp + 1);
+    f = a.x; vx = a.y; vy = b.x; vz = b.y;
+}
+
+// One collision candidate, queued by its warp in shared memory: the owner writes
+// the particle's index in its chunk, the gathered field and v_n; the lane that
+// processes the collision (reading cell and offset from the chunk's staged
+// records) writes back the new velocity and flags the newborns it left after
+// their first drift, which it stores at the candidate's rank in the chunk's
+// newborn regions (the warp then compacts them into parent-slot order).
 template <typename T>
 struct QEnt {
-    uint32_t slot;
-    int c;
-    uint32_t out;     // bit1: same-species newborn in scratch[0], bit2: other-species newborn in scratch[1]
-    T f, ef;
+    uint32_t idx;     // index in the chunk
+    uint32_t out;     // bit 1: same-species newborn, bit 2: other-species newborn
+    T ef;
     T vx, vy, vz;     // in: v_n; out: velocity after the collision
 };
 
 // The collision of a queued candidate (null-collision method: process
 // selection against the cumulative rate tables, then the kinematics).
 template <typename T>
-__device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, Part<T>* born, long long step,
-                                     unsigned long long seed, unsigned long long* sH, unsigned* sC, int& err) {
+__device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, int qc, T qf, uint32_t slot, uint32_t ridx,
+                                     long long step, unsigned long long seed, unsigned long long* sH, unsigned* sC,
+                                     int& err) {
     using Row4 = typename T4<T>::type;
     using Row2 = typename T4<T>::two;
     const Consts<T>& K = S.k;
     const int N = S.N;
-    const uint32_t slot = q.slot;
     T vx = q.vx, vy = q.vy, vz = q.vz;
     uint32_t out = 0;
     if (S.sp == 0) {
@@ -332,18 +314,18 @@ __device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, Part<T>* bo
             int cn;
             T fn;
             cvz = fma_(K.K[0], q.ef, cvz);
-            int side = drift(N, K.dtdx, q.c, q.f, cvz, cn, fn, err);
+            int side = drift(N, K.dtdx, qc, qf, cvz, cn, fn, err);
             if (side < 0) {
-                born[0] = Part<T>{cn, fn, cvx, cvy, cvz};
+                store_rec<T>(S.sc, S.sp_, ridx, Part<T>{cn, fn, cvx, cvy, cvz});
                 shist_add(sH, cn, cic_F(fn));
                 out |= 2u;
             } else {
                 atomicAdd(&sC[CNT_ABS + side], 1u);
             }
             ivz = fma_(K.K[1], q.ef, ivz);
-            side = drift(N, K.dtdx, q.c, q.f, ivz, cn, fn, err);
+            side = drift(N, K.dtdx, qc, qf, ivz, cn, fn, err);
             if (side < 0) {
-                born[1] = Part<T>{cn, fn, ivx, ivy, ivz};
+                store_rec<T>(S.bc, S.bp, ridx, Part<T>{cn, fn, ivx, ivy, ivz});
                 hist_add(S.Dother, cn, cic_F(fn));
                 out |= 4u;
             } else {
@@ -414,47 +396,27 @@ __device__ __forceinline__ bool emit_see(const Seg<T>& S, uint32_t slot, long lo
     return true;
 }
 
+// Moves one record within a buffer (newborn compaction, dst <= src; nothing to do if equal).
 template <typename T>
-__device__ __forceinline__ void store_rec(int32_t* c, void* p, unsigned i, const Part<T>& q);
-template <>
-__device__ __forceinline__ void store_rec<float>(int32_t* c, void* p, unsigned i, const Part<float>& q) {
-    c[i] = q.c;
-    reinterpret_cast<float4*>(p)[i] = make_float4(q.f, q.vx, q.vy, q.vz);
-}
-template <>
-__device__ __forceinline__ void store_rec<double>(int32_t* c, void* p, unsigned i, const Part<double>& q) {
-    c[i] = q.c;
-    double2* pp = reinterpret_cast<double2*>(p) + 2 * i;
-    pp[0] = make_double2(q.f, q.vx);
-    pp[1] = make_double2(q.vy, q.vz);
+__device__ __forceinline__ void move_rec(int32_t* c, void* p, unsigned src, unsigned dst) {
+    if (src == dst) return;
+    using R = typename Rec<T>::type;
+    R* pp = reinterpret_cast<R*>(p);
+    const int cv = c[src];
+    const R rv = pp[src];
+    c[dst] = cv;
+    pp[dst] = rv;
 }
 
-template <typename T>
-__device__ __forceinline__ void load_rec(const void* p, unsigned i, T& f, T& vx, T& vy, T& vz);
-template <>
-__device__ __forceinline__ void load_rec<float>(const void* p, unsigned i, float& f, float& vx, float& vy,
-                                                float& vz) {
-    const float4 a = __ldcs(reinterpret_cast<const float4*>(p) + i);
-    f = a.x; vx = a.y; vy = a.z; vz = a.w;
-}
-template <>
-__device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, double& f, double& vx, double& vy,
-                                                 double& vz) {
-    const double2* pp = reinterpret_cast<const double2*>(p) + 2 * i;
-    const double2 a = __ldcs(pp), b = __ldcs(pp + 1);
-    f = a.x; vx = a.y; vy = b.x; vz = b.y;
-}
-
-// Store totals after a sweep, for discharge d, by one warp of k_post: from the
-// slice sums of parity par, the new counts and segment counts, the newborn
-// segment and its first_seg entries, on a full step the per-period mean
-// counts; then the slice sums of the other parity cleared for the next sweep.
+// Store totals after a sweep, for discharge d, by one warp of k_post: from the slice sums of parity
+// par, the new counts and the layout of the output buffer (the sweep's chunks become its regions,
+// the newborns its dense part at R0); on a full step the per-period mean counts; then the slice
+// sums of the other parity cleared for the next sweep.
 __device__ __forceinline__ void store_totals(const Disc& D, int d, Ctl* ctl, int lane, int par, bool full_step,
-                                             int& err) {
-    const int TILE = D.tile, CHUNK = D.chunk;
+                                             int out_buf, int& err) {
     long long chunks[2], slices[2];
     for (int sp = 0; sp < 2; ++sp) {
-        chunks[sp] = (ctl->count_in[d][sp] + TILE - 1) / TILE * D.warps;
+        chunks[sp] = ctl->chunks_in[d][sp];
         slices[sp] = (chunks[sp] + SLICE - 1) / SLICE;
     }
     const unsigned* T0 = D.slice_tot[0] + (size_t)par * 3 * D.slice_n[0];
@@ -486,22 +448,21 @@ __device__ __forceinline__ void store_totals(const Disc& D, int d, Ctl* ctl, int
         const long long bcap = D.bcap;
         const long long nbk = nb < bcap ? nb : bcap;
         const long long ch = chunks[sp];
-        const int nseg = (int)ch + (nbk > 0 ? 1 : 0);
         long long n_new = main_total + nbk;
-        int* st = D.seg_start[sp];
         if (lane == 0) {
             if (nb > bcap) err |= ERR_CAPACITY;
-            if (nbk > 0) {
-                st[ch] = (int)main_total;
-                D.seg_src[sp][ch] = (int)D.R0[sp];
-            }
-            st[nseg] = (int)n_new;
+            // more regions than the next sweep has output regions for: a sort or a repack is overdue
+            if (ch > D.rmax[sp]) err |= ERR_CAPACITY;
+            D.start[sp][ch] = (int)main_total;
             if (n_new > D.cap[sp]) {
                 err |= ERR_CAPACITY;
                 n_new = D.cap[sp];
             }
             ctl->count[d][sp] = n_new;
-            ctl->nseg[d][sp] = nseg;
+            Lay& L = ctl->lay[d][sp][out_buf];
+            L.K = (int)ch;
+            L.M = main_total;
+            L.D0 = D.R0[sp];
             if (full_step) {  // per-period mean counts (steady-state criterion)
                 const long long n_step = ctl->step;  // this step is n; the counts belong to n+1
                 ctl->period_acc[d][sp] += (double)n_new;
@@ -512,31 +473,70 @@ __device__ __forceinline__ void store_totals(const Disc& D, int d, Ctl* ctl, int
                 }
             }
         }
-        n_new = __shfl_sync(FULL, n_new, 0);
-        // the newborn segment's share of first_seg
-        const long long jmax = (long long)D.max_tiles[sp] * D.warps;
-        for (long long j = (main_total + CHUNK - 1) / CHUNK + lane; j * CHUNK < n_new && j <= jmax; j += 32)
-            D.first_seg[sp][j] = (int)ch;
         // the next sweep adds into the other parity
         unsigned* Tn = D.slice_tot[sp] + (size_t)(par ^ 1) * 3 * D.slice_n[sp];
         for (int k = lane; k < 3 * D.slice_n[sp]; k += 32) Tn[k] = 0;
     }
 }
 
-// Dynamic shared memory of the sweep: histogram and energy moment (u64, N+1
-// each), the node field (T, N+1), then per warp its candidate queue (one entry
-// per slot of its chunk) and its newborn scratch (a pair per lane).
+// Bulk copies into shared memory (the asynchronous copy engine) with an mbarrier per buffer.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(unsigned long long* mb) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* mb, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mb))
+                 : "memory");
+}
+// Waits for phase `parity` of the barrier to complete, at most MBAR_TRIES polls (each poll may block
+// for a hardware-defined time); false if it gave up.
+constexpr int MBAR_TRIES = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parity) {
+    const unsigned a = smem_u32(mb);
+    for (int it = 0; it < MBAR_TRIES; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Dynamic shared memory of the sweep: histogram and energy moment (u64, N+1 each), the node field
+// (T, N+1); per warp two staging buffers of one chunk (records, then cells) and its candidate
+// queue; per store the layout snapshot and the tile prefix.
 template <typename T>
+__host__ __device__ constexpr size_t sweep_stage_offset(int max_N) {
+    return (((size_t)(max_N + 1) * (16 + sizeof(T)) + 127) / 128) * 128;
+}
+template <typename T, int PPT>
+__host__ __device__ constexpr size_t sweep_stage_bytes() {  // one buffer of one warp
+    return (size_t)32 * PPT * (sizeof(typename Rec<T>::type) + 4);
+}
+template <typename T, int BLOCK, int PPT>
 __host__ __device__ constexpr size_t sweep_queue_offset(int max_N) {
-    return (((size_t)(max_N + 1) * (16 + sizeof(T)) + 15) / 16) * 16;
+    return sweep_stage_offset<T>(max_N) + 2 * (BLOCK / 32) * sweep_stage_bytes<T, PPT>();
 }
 template <typename T, int BLOCK, int PPT>
-__host__ __device__ constexpr size_t sweep_born_offset(int max_N) {
-    return ((sweep_queue_offset<T>(max_N) + sizeof(QEnt<T>) * (size_t)BLOCK * PPT + 15) / 16) * 16;
+__host__ __device__ constexpr size_t sweep_store_offset(int max_N) {
+    return ((sweep_queue_offset<T, BLOCK, PPT>(max_N) + sizeof(QEnt<T>) * (size_t)BLOCK * PPT + 15) / 16) * 16;
 }
+struct StoreSnap {  // layout of one input store, for the prefetches of any tile
+    int K, chunks;
+    long long M, D0, n;
+};
 template <typename T, int BLOCK, int PPT>
-__host__ __device__ constexpr size_t sweep_smem(int max_N) {
-    return sweep_born_offset<T, BLOCK, PPT>(max_N) + sizeof(Part<T>) * 2 * (size_t)BLOCK;
+__host__ __device__ constexpr size_t sweep_smem(int max_N, int n_disc) {
+    return sweep_store_offset<T, BLOCK, PPT>(max_N) + sizeof(StoreSnap) * 2 * (size_t)n_disc +
+           sizeof(long long) * (2 * (size_t)n_disc + 1);
 }
 
 // Resident threads per SM the sweep is compiled for (the register budget is 65536 / that): the
@@ -549,19 +549,17 @@ __host__ __device__ constexpr int sweep_min_blocks() {
 }
 
 // ---------------------------------------------------------------------------
-// The sweep. Persistent CTAs take the tiles of TILE = BLOCK x PPT slots of all
-// stores (discharge, species) in a static grid-stride order; warp w of a tile
-// owns the chunk of CHUNK = 32 PPT consecutive slots at w CHUNK and works on it
-// alone, with no barrier: it loads its particles straight into registers
-// through the store's segment table, pushes them (gather, kick, energy moment,
-// candidate test), runs one collision pass over the chunk's candidates, then
-// kicks, drifts, deposits and writes the survivors in slot order to the
-// chunk's own output region [CHUNK cs, ...), cs the chunk index. Newborns go
-// in parent-slot order to the chunk's regions of the newborn buffers (same
-// species: ionization electrons; other species: ionization ions, or SEE
-// electrons of the ion sweep), and the chunk records the three counts. The
-// CTA synchronises only where its tiles move to another store (histogram
-// flush).
+// The sweep. Persistent CTAs take the tiles of NW chunks of all stores (discharge, species) in a
+// static grid-stride order; warp w of a tile owns the tile's chunk w (at most CHUNK = 32 PPT
+// slots, a region or a run of the dense part of the input layout) and works on it alone, with no
+// barrier: the chunk's records and cells arrive in the warp's staging buffer by a bulk copy issued
+// while the warp was processing its previous chunk; the warp pushes its particles (gather, kick,
+// energy moment, candidate test), runs one collision pass over the chunk's candidates, then kicks,
+// drifts, deposits and writes the survivors in slot order to the chunk's own output region
+// [CHUNK cs, ...), cs the chunk index. Newborns go in parent-slot order to the chunk's regions of
+// the newborn buffers (same species: ionization electrons; other species: ionization ions, or SEE
+// electrons of the ion sweep), and the chunk records the three counts. The CTA synchronises only
+// where its tiles move to another store (histogram flush).
 template <typename T, int BLOCK, int PPT>
 __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     k_sweep(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl, int in_buf, unsigned long long seed,
@@ -569,36 +567,57 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     using R = typename Rec<T>::type;
     constexpr int NW = BLOCK / 32;
     constexpr int CHUNK = 32 * PPT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr unsigned REC_BYTES = CHUNK * sizeof(R), CELL_BYTES = CHUNK * 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem_raw);
     unsigned long long* s_Q = s_hist + (max_N + 1);
     T* s_E = reinterpret_cast<T*>(s_Q + (max_N + 1));
-    QEnt<T>* s_q = reinterpret_cast<QEnt<T>*>(smem_raw + sweep_queue_offset<T>(max_N));
-    Part<T>* s_born = reinterpret_cast<Part<T>*>(smem_raw + sweep_born_offset<T, BLOCK, PPT>(max_N));
+    StoreSnap* s_store = reinterpret_cast<StoreSnap*>(smem_raw + sweep_store_offset<T, BLOCK, PPT>(max_N));
+    long long* s_segstart = reinterpret_cast<long long*>(s_store + 2 * n_disc);
 
-    __shared__ long long s_segstart[2 * MAXD + 1];
     __shared__ Seg<T> S;
     __shared__ long long s_step;
     __shared__ int s_par;
     __shared__ unsigned s_cnt[NCNT];
     __shared__ int s_err;
+    __shared__ unsigned long long s_mbar[NW][2];
+    // per warp: the chunk prefetched for its next tile (chunk index, first and end slot, valid), the
+    // store of the last prefetch, and the barrier phases (kept here, not in registers)
+    __shared__ int s_pf[NW][6];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned char* stage = smem_raw + sweep_stage_offset<T>(max_N) + (size_t)warp * 2 * sweep_stage_bytes<T, PPT>();
+    QEnt<T>* Q = reinterpret_cast<QEnt<T>*>(smem_raw + sweep_queue_offset<T, BLOCK, PPT>(max_N)) + warp * CHUNK;
+    if (lane == 0) {
+        mbar_init(&s_mbar[warp][0]);
+        mbar_init(&s_mbar[warp][1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     grid_dep_sync();
     if (tid == 0) {
         long long acc = 0;
+        int err0 = 0;
         for (int s = 0; s < 2 * n_disc; ++s) {
+            const int d = s >> 1, sp = s & 1;
+            const Lay L = ctl->lay[d][sp][in_buf];
+            const long long n = ctl->count[d][sp];
+            long long ch = chunks_of(L, n, CHUNK);
+            if (ch > discs[d].ralloc[sp]) {  // more chunks than output regions: reported, the rest dropped
+                ch = discs[d].ralloc[sp];
+                err0 |= ERR_CAPACITY;
+            }
+            s_store[s] = StoreSnap{L.K, (int)ch, L.M, L.D0, n};
             s_segstart[s] = acc;
-            const long long n = ctl->count[s >> 1][s & 1];
-            acc += (n + BLOCK * PPT - 1) / (BLOCK * PPT);
+            acc += (ch + NW - 1) / NW;
+            if (blockIdx.x == 0) ctl->chunks_in[d][sp] = (int)ch;  // read by the post-sweep grid
         }
         s_segstart[2 * n_disc] = acc;
         s_step = ctl->step;
         s_par = ctl->slice_par;
-        s_err = 0;
+        s_err = blockIdx.x == 0 ? err0 : 0;
     }
     __syncthreads();
-    const long long total_tiles = s_segstart[2 * n_disc];
+    const int total_tiles = (int)s_segstart[2 * n_disc];  // tiles and chunks fit in 31 bits (record offsets do)
     const long long step = s_step;
     int cur_seg = -1, cur_d = -1;
     int err = 0;
@@ -617,98 +636,139 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         __syncthreads();
     };
 
-    QEnt<T>* Q = s_q + warp * CHUNK;
-    Part<T>* born = s_born + 2 * (warp * 32 + lane);
-    const unsigned lt = (1u << lane) - 1u;
+    // Prefetch of this warp's chunk of tile gn into staging buffer b: the store of the tile, the
+    // chunk's record offset (known without any table) and its first and end slot (regions: from
+    // the start table, loaded now and used when the chunk is processed).
+    int* pf = s_pf[warp];  // [0] chunk, [1] first slot, [2] end slot, [3] valid, [4] store, [5] phases
+    auto prefetch = [&](int b, int gn) {
+        if (lane == 0) pf[3] = 0;
+        if (gn >= total_tiles) return;
+        int sg = pf[4];
+        while (sg + 1 < 2 * n_disc && s_segstart[sg + 1] <= gn) ++sg;
+        const StoreSnap ss = s_store[sg];
+        const int cs = (gn - (int)s_segstart[sg]) * NW + warp;
+        if (cs >= ss.chunks) return;
+        const int d = sg >> 1, sp = sg & 1;
+        long long src;
+        int pst0, pst1;
+        if (cs < ss.K) {
+            src = (long long)cs * CHUNK;
+            const int* st = discs[d].start[sp];
+            pst0 = __ldg(st + cs);
+            pst1 = __ldg(st + cs + 1);
+        } else {
+            const long long j = (long long)(cs - ss.K);
+            src = ss.D0 + j * CHUNK;
+            pst0 = (int)(ss.M + j * CHUNK);
+            pst1 = (int)min(ss.n, ss.M + (j + 1) * CHUNK);
+        }
+        if (lane == 0) {
+            pf[0] = (int)cs;
+            pf[1] = pst0;
+            pf[2] = pst1;
+            pf[3] = 1;
+            pf[4] = sg;
+            unsigned char* buf = stage + (size_t)b * sweep_stage_bytes<T, PPT>();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer
+            mbar_expect(&s_mbar[warp][b], REC_BYTES + CELL_BYTES);
+            bulk_g2s(buf, reinterpret_cast<const R*>(discs[d].p[in_buf][sp]) + src, REC_BYTES, &s_mbar[warp][b]);
+            bulk_g2s(buf + REC_BYTES, discs[d].c[in_buf][sp] + src, CELL_BYTES, &s_mbar[warp][b]);
+        }
+    };
 
-    // One warp's chunk of the store of species SP: load, push, collide, write (see above).
-    auto chunk = [&](unsigned cs, unsigned cbase, auto spc) {
+    const unsigned lt = (1u << lane) - 1u;
+    if (lane == 0) {
+        pf[4] = 0;
+        pf[5] = 0;  // bit b: phase of buffer b's barrier the next wait expects
+    }
+    __syncwarp();
+    prefetch(0, blockIdx.x);  // the chunk of the CTA's first tile, into buffer 0
+    __syncwarp();
+
+    // One warp's chunk of the store of species SP: push, collide, write (see above). Phase C reads
+    // each particle again from the staging buffer and repeats the gather and the first half kick
+    // (the same operations, so the same values) instead of keeping them in registers.
+    auto chunk = [&](unsigned cs, int base, int cnt, const R* srec, const int32_t* scell, auto spc) {
         constexpr int SP = decltype(spc)::value;
-        const unsigned n = (unsigned)S.n;
-        unsigned offA = cbase, offB = cbase, offS = cbase;  // output cursors of the chunk's regions
-        if (cbase < n) {
-            const int N = S.N;
-            // ---- load, through the store's segment table
-            SegCursor cur;
-            cur.init(S.seg_start, S.seg_src, S.first_seg, S.nseg, cbase, CHUNK, lane);
-            const int32_t* __restrict__ cin = S.cin;
-            const void* pin = S.pin;
-            int cc[PPT];
-            T fq[PPT], vxq[PPT], vyq[PPT], vzq[PPT];
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const unsigned s0 = cbase + 32 * k, slot = s0 + lane;
-                cc[k] = -1;
-                fq[k] = vxq[k] = vyq[k] = vzq[k] = (T)0;
-                if (s0 < n) {
-                    const unsigned off = cur.offset(s0, slot);
-                    if (slot < n) {
-                        cc[k] = __ldcs(cin + off);
-                        load_rec<T>(pin, off, fq[k], vxq[k], vyq[k], vzq[k]);
-                    }
+        const unsigned obase = cs * CHUNK;
+        unsigned offA = obase, offB = obase, offS = obase;  // output cursors of the chunk's regions
+        const int N = S.N;
+        const T Ksp = S.k.K[SP];
+        // particle i of the chunk: cell (-1 if none or out of range), offset, velocity, gathered field
+        auto particle = [&](int i, int& c, T& f, T& vx, T& vy, T& vz, T& ef) {
+            c = -1;
+            f = vx = vy = vz = ef = (T)0;
+            if (i < cnt) {
+                c = scell[i];
+                const R r = srec[i];
+                f = r.x;
+                vx = r.y;
+                vy = r.z;
+                vz = r.w;
+                if (!((unsigned)c < (unsigned)N)) c = -1;
+                else {
+                    const T E0 = s_E[c], E1 = s_E[c + 1];
+                    ef = fma_(f, sub_(E1, E0), E0);
                 }
             }
+        };
+        if (cnt > 0) {
             // candidate words: slots 4q..4q+3 take the four words of one Philox call (call 4,
-            // counter word 0 = q); lane l computes group q = (cbase + 32 k) / 4 + j for k = i / 8,
-            // j = i % 8, i = l + 32 m, and iteration k takes its word by shuffle
-            constexpr int NG = (8 * PPT + 31) / 32;
+            // counter word 0 = q); lane l computes the calls q0 + l + 32 m, q0 = base / 4, and the
+            // particle of slot s takes word s % 4 of call s / 4 by shuffle
+            constexpr int NG = (CHUNK / 4 + 1 + 31) / 32;
             const uint32_t did = S.did, thr = S.thr;
+            const unsigned q0 = (unsigned)base >> 2;
             U4 cw[NG];
 #pragma unroll
-            for (int m = 0; m < NG; ++m) {
-                const int i = lane + 32 * m;
-                const unsigned q = (cbase + 32u * (unsigned)(i >> 3)) / 4 + (unsigned)(i & 7);
-                cw[m] = draw(seed, q, step, SP, 4, did);
-            }
-            const T Ksp = S.k.K[SP];
+            for (int m = 0; m < NG; ++m) cw[m] = draw(seed, q0 + lane + 32 * m, step, SP, 4, did);
             // ---- phase A: gather, first half kick, energy moment, candidate test
-            T efq[PPT];
             int qiq[PPT];
             int qn = 0;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (cc[k] >= 0 && !((unsigned)cc[k] < (unsigned)N)) {
-                    err |= ERR_NONFINITE;  // corrupt cell index: dropped and reported
-                    cc[k] = -1;
-                }
-                const bool valid = cc[k] >= 0;
-                efq[k] = (T)0;
+                const int i = 32 * k + lane;
+                int c;
+                T f, vx, vy, vz, ef;
+                particle(i, c, f, vx, vy, vz, ef);
+                if (i < cnt && c < 0) err |= ERR_NONFINITE;  // corrupt cell index: dropped and reported
+                const bool valid = c >= 0;
                 unsigned long long qv = 0;
                 if (valid) {
-                    const int c = cc[k];
-                    const T E0 = s_E[c], E1 = s_E[c + 1];
-                    efq[k] = fma_(fq[k], sub_(E1, E0), E0);
-                    vzq[k] = fma_(Ksp, efq[k], vzq[k]);  // v_n
+                    vz = fma_(Ksp, ef, vz);  // v_n
                     if (SP == 0) {  // energy moment at (x_n, v_n), 2^-12 eV, clamped at 2^26
-                        const T e2 = fma_(vxq[k], vxq[k], fma_(vyq[k], vyq[k], mul_(vzq[k], vzq[k])));
+                        const T e2 = fma_(vx, vx, fma_(vy, vy, mul_(vz, vz)));
                         T eq = mul_(e2, S.k.kappa_E);
                         if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
                         const unsigned long long Et = rint_u32(eq);
-                        const unsigned long long Eh = rint_u32(mul_(eq, fq[k]));
+                        const unsigned long long Eh = rint_u32(mul_(eq, f));
                         qv = (Et - Eh) | (Eh << 32);
                     }
                 }
-                if (SP == 0) warp_hist<true>(s_Q, cc[k], qv, lane);
-                const int src_lane = (8 * k + (lane >> 2)) & 31;
-                const U4& g4 = cw[(8 * k) >> 5];
-                const uint32_t w0 = __shfl_sync(FULL, g4.x, src_lane), w1 = __shfl_sync(FULL, g4.y, src_lane);
-                const uint32_t w2 = __shfl_sync(FULL, g4.z, src_lane), w3 = __shfl_sync(FULL, g4.w, src_lane);
-                const int wi = lane & 3;
-                const uint32_t cword = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
+                if (SP == 0) warp_hist<true>(s_Q, c, qv, lane);
+                const unsigned slot = (unsigned)base + i;
+                const unsigned r = (slot >> 2) - q0;
+                uint32_t cword = 0;
+#pragma unroll
+                for (int m = 0; m < NG; ++m) {
+                    const uint32_t w0 = __shfl_sync(FULL, cw[m].x, r & 31), w1 = __shfl_sync(FULL, cw[m].y, r & 31);
+                    const uint32_t w2 = __shfl_sync(FULL, cw[m].z, r & 31), w3 = __shfl_sync(FULL, cw[m].w, r & 31);
+                    const int wi = slot & 3;
+                    const uint32_t wsel = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
+                    if ((int)(r >> 5) == m) cword = wsel;
+                }
                 const bool cand = valid && cword < thr;
                 const unsigned cm = __ballot_sync(FULL, cand);
                 if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + SP], (unsigned)__popc(cm));
                 qiq[k] = cand ? qn + __popc(cm & lt) : -1;
                 if (cand) {
                     QEnt<T>& e = Q[qiq[k]];
-                    e.slot = cbase + 32 * k + lane;
-                    e.c = cc[k];
+                    e.idx = i;
                     e.out = 0;
-                    e.f = fq[k];
-                    e.ef = efq[k];
-                    e.vx = vxq[k];
-                    e.vy = vyq[k];
-                    e.vz = vzq[k];
+                    e.ef = ef;
+                    e.vx = vx;
+                    e.vy = vy;
+                    e.vz = vz;
                 }
                 qn += __popc(cm);
             }
@@ -716,13 +776,17 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             __syncwarp();
             for (int r0 = 0; r0 < qn; r0 += 32) {
                 const int q = r0 + lane;
-                if (q < qn) collide<T>(S, Q[q], born, step, seed, s_hist, s_cnt, err);
+                if (q < qn) {
+                    const uint32_t i = Q[q].idx;
+                    collide<T>(S, Q[q], scell[i], srec[i].x, (uint32_t)base + i, obase + q, step, seed, s_hist,
+                               s_cnt, err);
+                }
                 __syncwarp();
-                if (SP == 0) {
+                if (SP == 0) {  // the round's newborns, from the candidates' ranks to parent-slot order (dst <= src)
                     const uint32_t o = q < qn ? Q[q].out : 0u;
                     const unsigned m1 = __ballot_sync(FULL, (o & 2u) != 0), m2 = __ballot_sync(FULL, (o & 4u) != 0);
-                    if (o & 2u) store_rec<T>(S.sc, S.sp_, offS + __popc(m1 & lt), born[0]);
-                    if (o & 4u) store_rec<T>(S.bc, S.bp, offB + __popc(m2 & lt), born[1]);
+                    if (o & 2u) move_rec<T>(S.sc, S.sp_, obase + q, offS + __popc(m1 & lt));
+                    if (o & 4u) move_rec<T>(S.bc, S.bp, obase + q, offB + __popc(m2 & lt));
                     offS += __popc(m1);
                     offB += __popc(m2);
                     __syncwarp();
@@ -734,27 +798,32 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             void* pout = S.pout;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
+                const int i = 32 * k + lane;
                 bool alive = false, see = false;
                 Part<T> P0{}, Pse{};
-                if (cc[k] >= 0) {
-                    T vx = vxq[k], vy = vyq[k], vz = vzq[k];
+                int c;
+                T f, vx, vy, vz, ef;
+                particle(i, c, f, vx, vy, vz, ef);
+                if (c >= 0) {
                     if (qiq[k] >= 0) {
                         const QEnt<T>& e = Q[qiq[k]];
                         vx = e.vx;
                         vy = e.vy;
                         vz = e.vz;
+                    } else {
+                        vz = fma_(Ksp, ef, vz);  // v_n, as in phase A
                     }
-                    vz = fma_(Ksp, efq[k], vz);
+                    vz = fma_(Ksp, ef, vz);
                     int cn;
                     T fn;
-                    const int side = drift(N, dtdx, cc[k], fq[k], vz, cn, fn, err);
+                    const int side = drift(N, dtdx, c, f, vz, cn, fn, err);
                     if (side < 0) {
                         P0 = Part<T>{cn, fn, vx, vy, vz};
                         alive = true;
                     } else {
                         atomicAdd(&s_cnt[CNT_ABS + 2 * SP + side], 1u);
                         if (SP == 1 && S.has_see)
-                            see = emit_see<T>(S, cbase + 32 * k + lane, step, seed, side, Pse, s_cnt);
+                            see = emit_see<T>(S, (uint32_t)base + i, step, seed, side, Pse, s_cnt);
                     }
                 }
                 warp_hist<false>(s_hist, alive ? P0.c : -1, alive ? (1ull << 40) + cic_F(P0.f) : 0ull, lane);
@@ -769,7 +838,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             }
         }
         if (lane == 0) {
-            const unsigned a = offA - cbase, b = offB - cbase, c = offS - cbase;
+            const unsigned a = offA - obase, b = offB - obase, c = offS - obase;
             S.cnt_main[cs] = (int)a;
             S.cnt_birth[cs] = (int)b;
             if (SP == 0) S.cnt_same[cs] = (int)c;
@@ -780,7 +849,8 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         }
     };
 
-    for (long long g = blockIdx.x; g < total_tiles; g += gridDim.x) {
+    int it = 0;
+    for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++it) {
         // the store of tile g: the CTA's tiles increase, so its store only moves forward
         int seg = cur_seg < 0 ? 0 : cur_seg;
         while (seg + 1 < 2 * n_disc && s_segstart[seg + 1] <= g) ++seg;
@@ -798,7 +868,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 S.n_exc = D.n_exc;
                 S.thr = D.thr[sp];
                 S.did = D.discharge_id;
-                S.n = ctl->count[d][sp];
+                S.n = s_store[seg].n;
                 S.cap = D.cap[sp];
                 S.bcap = D.bcap;
                 S.cin = D.c[in_buf][sp];
@@ -815,10 +885,11 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 S.Dother = D.D[1 - sp];
                 S.Qg = D.Q;
                 S.cnt = D.cnt;
-                S.seg_start = D.seg_start[sp];
-                S.seg_src = D.seg_src[sp];
-                S.first_seg = D.first_seg[sp];
-                S.nseg = ctl->nseg[d][sp];
+                S.start = D.start[sp];
+                S.K = s_store[seg].K;
+                S.M = s_store[seg].M;
+                S.D0 = s_store[seg].D0;
+                S.ralloc = D.ralloc[sp];
                 S.cnt_main = D.cnt_main[sp];
                 S.cnt_birth = D.cnt_birth[sp];
                 S.cnt_same = D.cnt_same;
@@ -839,26 +910,34 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             __syncthreads();
         }
 
-        // chunk index in the store and its first slot (slots and record offsets fit in 31 bits:
-        // the host caps every record buffer below 2^31)
-        const unsigned cs = (unsigned)(g - s_segstart[seg]) * NW + warp;
-        const unsigned cbase = cs * CHUNK;
-        if (S.sp == 0) chunk(cs, cbase, IC<0>{});
-        else chunk(cs, cbase, IC<1>{});
+        const int b = it & 1;
+        const bool mine = pf[3] != 0;
+        const unsigned cs = (unsigned)pf[0];
+        const int base = pf[1], end = pf[2];
+        if (mine) {  // this tile's chunk: its staged data, then the next tile's prefetch into the other buffer
+            if (!mbar_wait(&s_mbar[warp][b], ((unsigned)pf[5] >> b) & 1u)) err |= ERR_TIMEOUT;
+        }
+        __syncwarp();
+        if (lane == 0 && mine) pf[5] ^= 1 << b;
+        prefetch(b ^ 1, g + gridDim.x);
+        __syncwarp();
+        if (mine && !(err & ERR_TIMEOUT)) {
+            const unsigned char* buf = stage + (size_t)b * sweep_stage_bytes<T, PPT>();
+            const R* srec = reinterpret_cast<const R*>(buf);
+            const int32_t* scell = reinterpret_cast<const int32_t*>(buf + REC_BYTES);
+            // slots and record offsets fit in 31 bits: the host caps every record buffer below 2^31
+            if (S.sp == 0) chunk(cs, base, end - base, srec, scell, IC<0>{});
+            else chunk(cs, base, end - base, srec, scell, IC<1>{});
+        }
+        __syncwarp();
     }
+    // copies still in flight (a prefetch is issued only for a tile this CTA takes, so none should
+    // be): wait for them, bounded, before the CTA's shared memory goes away
+    if (pf[3] && !mbar_wait(&s_mbar[warp][it & 1], ((unsigned)pf[5] >> (it & 1)) & 1u)) err |= ERR_TIMEOUT;
     if (cur_seg >= 0) flush();
     if (err) atomicOr(&s_err, err);
     __syncthreads();
-    // the last CTA snapshots the counts the sweep read; it uses no other CTA's results (the counts
-    // do not change during the sweep), so no fence: the kernel boundary publishes everything
-    if (tid == 0) {
-        if (s_err) atomicOr(&ctl->error, s_err);
-        const unsigned prev = atomicAdd(&ctl->done, 1u);
-        if (prev == gridDim.x - 1) {
-            for (int i = 0; i < 2 * n_disc; ++i) ctl->count_in[i >> 1][i & 1] = ctl->count[i >> 1][i & 1];
-            ctl->done = 0;
-        }
-    }
+    if (tid == 0 && s_err) atomicOr(&ctl->error, s_err);
 }
 
 
@@ -939,12 +1018,12 @@ __device__ __forceinline__ double i128_to_double(__int128 x) {
 }
 
 // After a sweep (mode bit 1) and for every solve, one grid (x = slice or role,
-// y = store): CTAs x < nsl write the segment entries of slice x of store y
-// (seg_start/seg_src of its chunks, first_seg of the slots they hold) and copy
-// its newborns into the newborn regions; CTA x = nsl, y even solves the field of
-// discharge y / 2 and accumulates the moments; CTA x = nsl, y odd turns the
-// slice sums of discharge y / 2 into the new counts and clears the sums of the
-// other parity for the next sweep. mode bits: 1 segments after a sweep; 2
+// y = store): CTAs x < nsl write the region starts of the chunks of slice x of
+// store y (the first slot each chunk's survivors take in the new layout) and
+// copy its newborns into the newborn area; CTA x = nsl, y even solves the field
+// of discharge y / 2 and accumulates the moments; CTA x = nsl, y odd turns the
+// slice sums of discharge y / 2 into the new counts and layouts and clears the
+// sums of the other parity for the next sweep. mode bits: 1 layouts after a sweep; 2
 // accumulate moments and advance the step; 4 initial solve at t = n dt (load);
 // 8 segments only (no solve, deposits kept). The last CTA to finish advances
 // the step (mode bit 2) and flips the slice parity (mode bit 1).
@@ -961,14 +1040,11 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
     const int d = blockIdx.y >> 1, sp = blockIdx.y & 1;
     const Disc& D = discs[d];
     // every field is read before the first store (the stores could otherwise alias them)
-    const int TILE = D.tile, CHUNK = D.chunk, WARPS = D.warps;
+    const int CHUNK = D.chunk;
     const int* __restrict__ cnt_m = D.cnt_main[sp];
     const int* __restrict__ cnt_b = D.cnt_birth[sp];
     const int* __restrict__ cnt_s = D.cnt_same;
-    int* __restrict__ st = D.seg_start[sp];
-    int* __restrict__ sr = D.seg_src[sp];
-    int* __restrict__ fs = D.first_seg[sp];
-    const long long jmax = D.max_tiles[sp] * WARPS;
+    int* __restrict__ st = D.start[sp];
     const int q = 1 - sp;  // store of the other-species newborns
     const long long bcap = D.bcap;
     const int rw = D.rec_words;  // record size in 16-byte words
@@ -983,7 +1059,7 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
     const unsigned* __restrict__ slice0 = D.slice_tot[0];
     const unsigned* __restrict__ slice_s = D.slice_tot[sp];
     const int sn0 = D.slice_n[0], sn_s = D.slice_n[sp];
-    const long long chunks = (ctl->count_in[d][sp] + TILE - 1) / TILE * WARPS;
+    const long long chunks = ctl->chunks_in[d][sp];
     const long long t0 = (long long)blockIdx.x * SLICE;
     if (t0 >= chunks) return;
     // output offsets of this slice: the sums of the slices before it (survivors, other-species
@@ -1000,7 +1076,7 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
             c += Tp[3 * k + 2];
         }
         if (sp == 1) {
-            const long long ch0 = (ctl->count_in[d][0] + TILE - 1) / TILE * WARPS;
+            const long long ch0 = ctl->chunks_in[d][0];
             const unsigned* T0 = slice0 + (size_t)par * 3 * sn0;
             for (long long k = lane; k < (ch0 + SLICE - 1) / SLICE; k += 32) b += T0[3 * k + 2];
         }
@@ -1069,9 +1145,7 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
         const long long t = tb + i;
         const int cm = s_cnt[0][tid * K + i], cb = s_cnt[1][tid * K + i], cs = s_cnt[2][tid * K + i];
         if (t < chunks) {
-            st[t] = (int)em;
-            sr[t] = (int)(t * CHUNK);
-            for (long long j = (em + CHUNK - 1) / CHUNK; j * CHUNK < em + cm && j <= jmax; ++j) fs[j] = (int)t;
+            st[t] = (int)em;  // the first slot of region t of the new layout
             for (int k = 0; k < cb; ++k) {
                 const long long o = eb + k;
                 if (o < bcap) {
@@ -1290,7 +1364,8 @@ __global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ di
     } else if ((mode & 1) && (blockIdx.y & 1) == 1) {  // store totals of discharge y / 2
         if (warp == 0) {
             int e2 = 0;
-            store_totals(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, lane, ctl->slice_par, (mode & 2) != 0, e2);
+            store_totals(discs[blockIdx.y >> 1], blockIdx.y >> 1, ctl, lane, ctl->slice_par, (mode & 2) != 0, out_buf,
+                         e2);
             if (e2 && lane == 0) atomicOr(&s_err, e2);
         }
     } else if (!(mode & 8) && (blockIdx.y & 1) == 0) {
@@ -1467,59 +1542,85 @@ __global__ void k_tables(int n_pts, int n_proc, double de, double M, const doubl
 }
 
 // ---------------------------------------------------------------------------
-// Stable counting sort by cell. Tiles of SORT_TILE particles; inside a tile
-// warp w owns a contiguous run of SORT_R x 32 particles in input order.
-constexpr int SORT_BLOCK = 256, SORT_NW = SORT_BLOCK / 32, SORT_R = 16, SORT_TILE = SORT_BLOCK * SORT_R;
-constexpr int SORT_WARP = 32 * SORT_R;  // consecutive slots of one warp in a sort tile
+// Chunk k of a store with layout L (see Lay): first slot, slots and record offset. Regions take
+// their first and end slots from the start table.
+struct ChunkDesc {
+    long long src;
+    int base, cnt;
+};
+__device__ __forceinline__ ChunkDesc chunk_desc(const Lay& L, long long n, const int* st, long long k, int chunk) {
+    ChunkDesc c;
+    if (k < L.K) {
+        c.src = k * chunk;
+        c.base = __ldg(st + k);
+        c.cnt = __ldg(st + k + 1) - c.base;
+    } else {
+        const long long j = k - L.K;
+        c.src = L.D0 + j * chunk;
+        c.base = (int)(L.M + j * chunk);
+        c.cnt = (int)min((long long)chunk, n - c.base);
+    }
+    return c;
+}
 
-// Stable counting sort of every store by cell, over tiles of SORT_TILE slots
-// (warp w of tile t owns slots t SORT_TILE + w SORT_WARP ...):
+// Stable counting sort by cell. A sort tile is SORT_NW warps of SORT_R rows of 32 slots: warp w of
+// tile t walks the store's chunks t SORT_NW CPW + w CPW .. + CPW - 1 (CPW = SORT_R 32 / CHUNK) in
+// slot order.
+constexpr int SORT_BLOCK = 256, SORT_NW = SORT_BLOCK / 32, SORT_R = 16;
+__device__ __forceinline__ long long sort_tiles(long long chunks, int chunk) {
+    const long long per = (long long)SORT_NW * (SORT_R * 32 / chunk);
+    return (chunks + per - 1) / per;
+}
+
+// Stable counting sort of every store by cell:
 //   k_sort_count   per tile: each slot's cell and its rank among the tile's
 //                  slots of the same cell (in slot order), packed with the cell
-//                  into kr[slot], its record offset into off[slot], and the
-//                  tile's cell counts into hist[seg][t N + c]; input read
-//                  through the store's segment table;
+//                  into kr[slot], and the tile's cell counts into
+//                  hist[seg][t N + c];
 //   k_sort_rows    per cell: exclusive scan of the counts over the tiles; the
 //                  last CTA of a store scans the cell totals (first slot of
 //                  every cell);
-//   k_sort_scatter streaming, one slot per thread: destination = first slot of
-//                  its cell + the tile's offset in that cell + its rank; its
-//                  first CTA marks the sorted store as one dense segment.
+//   k_sort_scatter per tile, walking the same chunks: destination = first slot
+//                  of its cell + the tile's offset in that cell + its rank; the
+//                  sorted buffer's layout is dense.
 __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
                                                            int buf, unsigned* __restrict__ hist,
                                                            const long long* __restrict__ hoff,
-                                                           unsigned* __restrict__ kr_all, unsigned* __restrict__ off_all,
+                                                           unsigned* __restrict__ kr_all,
                                                            const long long* __restrict__ eoff, int max_N) {
     grid_dep_sync();
     extern __shared__ __align__(16) unsigned s_w[];  // [SORT_NW][max_N] per-warp counts, then prefixes
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
-    const int N = D.N;
-    const unsigned n = (unsigned)ctl->count[d][sp];
-    const int nseg = ctl->nseg[d][sp];
-    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
+    const int N = D.N, CHUNK = D.chunk, RPC = CHUNK / 32, CPW = SORT_R / RPC;
+    const long long n = ctl->count[d][sp];
+    const Lay L = ctl->lay[d][sp][buf];
+    const long long chunks = chunks_of(L, n, CHUNK);
+    const long long Ts = sort_tiles(chunks, CHUNK);
     const int32_t* __restrict__ cc = D.c[buf][sp];
+    const int* st = D.start[sp];
     unsigned* H = hist + hoff[seg];
     unsigned* KR = kr_all + eoff[seg];
-    unsigned* OF = off_all + eoff[seg];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     unsigned* Wc = s_w + warp * max_N;
-    for (unsigned t = blockIdx.x; t < Ts; t += gridDim.x) {
+    for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
         for (int j = tid; j < SORT_NW * max_N; j += SORT_BLOCK) s_w[j] = 0;
         __syncthreads();
-        const unsigned wbase = t * SORT_TILE + warp * SORT_WARP;
-        unsigned kr[SORT_R], off[SORT_R];  // cell (then | rank in the warp << 16), record offset
-        SegCursor cur;
-        if (wbase < n) cur.init(D.seg_start[sp], D.seg_src[sp], D.first_seg[sp], nseg, wbase, D.chunk, lane);
+        const long long k0 = (t * SORT_NW + warp) * CPW;
+        unsigned kr[SORT_R];
+        int slot[SORT_R];
+        ChunkDesc cd{0, 0, 0};
 #pragma unroll
         for (int r = 0; r < SORT_R; ++r) {  // all cell loads first
-            const unsigned s0 = wbase + 32 * r, slot = s0 + lane;
+            const int ci = r / RPC, row = r % RPC;
+            if (row == 0) cd = (k0 + ci < chunks) ? chunk_desc(L, n, st, k0 + ci, CHUNK) : ChunkDesc{0, 0, 0};
+            const int i = 32 * row + lane;
             kr[r] = 0xFFFFu;
-            off[r] = 0;
-            if (s0 < n) {
-                off[r] = cur.offset(s0, slot);
-                if (slot < n) kr[r] = (unsigned)__ldcs(cc + off[r]);  // checked below, after all loads are issued
+            slot[r] = -1;
+            if (i < cd.cnt) {
+                kr[r] = (unsigned)__ldcs(cc + cd.src + i);  // checked below, after all loads are issued
+                slot[r] = cd.base + i;
             }
         }
 #pragma unroll
@@ -1549,11 +1650,9 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(const Disc* __restric
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < SORT_R; ++r) {
-            const unsigned slot = wbase + 32 * r + lane;
-            if (slot < n) {
+            if (slot[r] >= 0) {
                 const int k = (int)(kr[r] & 0xFFFFu);
-                KR[slot] = k < N ? (unsigned)k | ((Wc[k] + (kr[r] >> 16)) << 16) : 0xFFFFu;
-                OF[slot] = off[r];
+                KR[slot[r]] = k < N ? (unsigned)k | ((Wc[k] + (kr[r] >> 16)) << 16) : 0xFFFFu;
             }
         }
         __syncthreads();
@@ -1600,7 +1699,7 @@ __device__ __forceinline__ void cells_scan(unsigned* a, int N) {
 
 // Per (store, group of 32 cells): exclusive scan over the tiles in place (lane = cell, each warp
 // a contiguous range of tiles, so rows are read 128 bytes at a time); row totals out.
-__global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ discs, Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int buf,
                                                     unsigned* __restrict__ hist, const long long* __restrict__ hoff,
                                                     unsigned* __restrict__ tot) {
     grid_dep_sync();
@@ -1610,8 +1709,8 @@ __global__ void __launch_bounds__(1024) k_sort_rows(const Disc* __restrict__ dis
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + lane;
     if (blockIdx.x * 32 >= N) return;
-    const unsigned n = (unsigned)ctl->count[d][sp];
-    const unsigned Ts = (n + SORT_TILE - 1) / SORT_TILE;
+    const unsigned Ts = (unsigned)sort_tiles(chunks_of(ctl->lay[d][sp][buf], ctl->count[d][sp], discs[d].chunk),
+                                             discs[d].chunk);
     unsigned* H = hist + hoff[seg];
     const unsigned per = (Ts + 31) / 32, t0 = min(Ts, warp * per), t1 = min(Ts, t0 + per);
     unsigned sum = 0;
@@ -1650,36 +1749,69 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_scatter(const Disc* __restr
                                                              const long long* __restrict__ hoff,
                                                              const unsigned* __restrict__ tot,
                                                              const unsigned* __restrict__ kr_all,
-                                                             const unsigned* __restrict__ off_all,
                                                              const long long* __restrict__ eoff) {
     grid_dep_sync();
     const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
     const Disc& D = discs[d];
-    const int N = D.N;
-    const unsigned n = (unsigned)ctl->count[d][sp];
+    const int N = D.N, CHUNK = D.chunk, RPC = CHUNK / 32, CPW = SORT_R / RPC;
+    const long long n = ctl->count[d][sp];
+    const Lay L = ctl->lay[d][sp][src];
+    const long long chunks = chunks_of(L, n, CHUNK);
+    const long long Ts = sort_tiles(chunks, CHUNK);
     using R = typename Rec<T>::type;
     const R* __restrict__ ps = reinterpret_cast<const R*>(D.p[src][sp]);
     R* __restrict__ pd = reinterpret_cast<R*>(D.p[dst][sp]);
     int32_t* __restrict__ cd = D.c[dst][sp];
+    const int* st = D.start[sp];
     const unsigned* H = hist + hoff[seg];
     const unsigned* cstart = tot + (long long)seg * MAXN;
     const unsigned* KR = kr_all + eoff[seg];
-    const unsigned* OF = off_all + eoff[seg];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the sorted store is one dense segment
-        D.seg_start[sp][0] = 0;
-        D.seg_start[sp][1] = (int)n;
-        D.seg_src[sp][0] = 0;
-        D.first_seg[sp][0] = 0;
-        ctl->nseg[d][sp] = 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->lay[d][sp][dst] = Lay{0, 0, 0, 0};  // the sorted store is dense
+    for (long long t = blockIdx.x; t < Ts; t += gridDim.x) {
+        const long long k0 = (t * SORT_NW + warp) * CPW;
+        for (int ci = 0; ci < CPW && k0 + ci < chunks; ++ci) {
+            const ChunkDesc c = chunk_desc(L, n, st, k0 + ci, CHUNK);
+            for (int row = 0; row < RPC; ++row) {
+                const int i = 32 * row + lane;
+                if (i >= c.cnt) continue;
+                const unsigned kr = __ldcs(KR + c.base + i);
+                const int k = (int)(kr & 0xFFFFu);
+                if (k >= N) continue;  // a corrupt cell index (reported by the sweep): dropped
+                const unsigned long long o = (unsigned long long)cstart[k] + H[(size_t)t * N + k] + (kr >> 16);
+                if (o < (unsigned long long)n) {
+                    cd[o] = k;
+                    pd[o] = ps[c.src + i];
+                }
+            }
+        }
     }
-    for (unsigned i = blockIdx.x * SORT_BLOCK + threadIdx.x; i < n; i += gridDim.x * SORT_BLOCK) {
-        const unsigned kr = __ldcs(KR + i);
-        const int k = (int)(kr & 0xFFFFu);
-        if (k >= N) continue;  // a corrupt cell index (reported by the sweep): dropped
-        const unsigned o = cstart[k] + H[(size_t)(i / SORT_TILE) * N + k] + (kr >> 16);
-        if (o < n) {
-            cd[o] = k;
-            pd[o] = ps[__ldcs(OF + i)];
+}
+
+// Order-preserving repack of every store into a dense buffer (the slots keep their order): bounds
+// the number of regions when the sort runs rarely or never. One warp per chunk.
+template <typename T>
+__global__ void k_repack(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int src, int dst) {
+    grid_dep_sync();
+    const int seg = blockIdx.y, d = seg >> 1, sp = seg & 1;
+    const Disc& D = discs[d];
+    const int CHUNK = D.chunk;
+    const long long n = ctl->count[d][sp];
+    const Lay L = ctl->lay[d][sp][src];
+    const long long chunks = chunks_of(L, n, CHUNK);
+    using R = typename Rec<T>::type;
+    const R* __restrict__ ps = reinterpret_cast<const R*>(D.p[src][sp]);
+    const int32_t* __restrict__ cs_ = D.c[src][sp];
+    R* __restrict__ pd = reinterpret_cast<R*>(D.p[dst][sp]);
+    int32_t* __restrict__ cd = D.c[dst][sp];
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->lay[d][sp][dst] = Lay{0, 0, 0, 0};
+    for (long long k = w0; k < chunks; k += nw) {
+        const ChunkDesc c = chunk_desc(L, n, D.start[sp], k, CHUNK);
+        for (int i = lane; i < c.cnt; i += 32) {
+            cd[c.base + i] = __ldcs(cs_ + c.src + i);
+            pd[c.base + i] = ps[c.src + i];
         }
     }
 }
@@ -1698,25 +1830,29 @@ __global__ void k_pack_state(const Disc* __restrict__ discs, int d, int sp, int 
     }
 }
 
-// State download: the store, read through its segment table (binary search per
-// slot), -> SoA staging.
+// State download: the store, read through its layout (regions: binary search of the start table;
+// the dense part by offset), -> SoA staging.
 template <typename T>
 __global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl, int d, int sp, int buf,
                                long long n, int32_t* __restrict__ c, T* __restrict__ sv) {
     const Disc& D = discs[d];
-    const int nseg = ctl->nseg[d][sp];
-    const int* st = D.seg_start[sp];
-    const int* sr = D.seg_src[sp];
+    const Lay L = ctl->lay[d][sp][buf];
+    const int* st = D.start[sp];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = nseg - 1;  // last segment with start <= i
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((long long)st[mid] <= i) lo = mid;
-            else hi = mid - 1;
+        long long o;
+        if (i < L.M) {
+            int lo = 0, hi = L.K - 1;  // last region with start <= i (empty regions share their start)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((long long)st[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            o = (long long)lo * D.chunk + (i - st[lo]);
+        } else {
+            o = L.D0 + (i - L.M);
         }
-        const unsigned o = (unsigned)sr[lo] + (unsigned)(i - st[lo]);
         T f, vx, vy, vz;
-        load_rec<T>(D.p[buf][sp], o, f, vx, vy, vz);
+        load_rec<T>(D.p[buf][sp], (unsigned)o, f, vx, vy, vz);
         c[i] = D.c[buf][sp][o];
         sv[i] = f;
         sv[n + i] = vx;
@@ -1725,31 +1861,19 @@ __global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __rest
     }
 }
 
-// Every store becomes one dense segment [0, count) (after a load, an upload or a sort).
-// End of a state upload (one thread): the store holds n particles, or none if the pack kernel
-// found a cell out of range, as one dense segment.
+// End of a state upload (one thread): the store holds n particles, or none if the pack kernel found a
+// cell out of range, dense in buffer buf.
 __global__ void k_finish_upload(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, int d, int sp, long long n,
-                                const unsigned* __restrict__ bad) {
-    const Disc& D = discs[d];
-    const long long v = *bad ? 0 : n;
-    ctl->count[d][sp] = v;
-    D.seg_start[sp][0] = 0;
-    D.seg_start[sp][1] = (int)v;
-    D.seg_src[sp][0] = 0;
-    D.first_seg[sp][0] = 0;
-    ctl->nseg[d][sp] = 1;
+                                const unsigned* __restrict__ bad, int buf) {
+    ctl->count[d][sp] = *bad ? 0 : n;
+    ctl->lay[d][sp][buf] = Lay{0, 0, 0, 0};
 }
-__global__ void k_set_dense(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl) {
+// Every store dense in buffer buf (after a load).
+__global__ void k_set_dense(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl, int buf) {
     grid_dep_sync();
     const int i = threadIdx.x;
     if (i >= 2 * n_disc) return;
-    const int d = i >> 1, sp = i & 1;
-    const Disc& D = discs[d];
-    D.seg_start[sp][0] = 0;
-    D.seg_start[sp][1] = (int)ctl->count[d][sp];
-    D.seg_src[sp][0] = 0;
-    D.first_seg[sp][0] = 0;
-    ctl->nseg[d][sp] = 1;
+    ctl->lay[i >> 1][i & 1][buf] = Lay{0, 0, 0, 0};
 }
 
 // ---------------------------------------------------------------------------
@@ -1828,7 +1952,7 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 
 template <typename T, int BLOCK, int PPT>
 static cudaError_t launch_sweep_t(const SweepLaunch& L) {
-    const size_t smem = sweep_smem<T, BLOCK, PPT>(L.max_N);
+    const size_t smem = sweep_smem<T, BLOCK, PPT>(L.max_N, L.n_disc);
     auto kern = k_sweep<T, BLOCK, PPT>;
     cudaError_t e = smem_attr(kern, smem);
     if (e != cudaSuccess) return e;
@@ -1855,26 +1979,26 @@ cudaError_t launch_sweep(const SweepLaunch& L) {
 }
 
 template <typename T, int BLOCK, int PPT>
-static int occ_t(int max_N) {
+static int occ_t(int max_N, int n_disc) {
     int nb = 0;
-    const size_t smem = sweep_smem<T, BLOCK, PPT>(max_N);
+    const size_t smem = sweep_smem<T, BLOCK, PPT>(max_N, n_disc);
     smem_attr(k_sweep<T, BLOCK, PPT>, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<T, BLOCK, PPT>, BLOCK, smem);
     return nb;
 }
 template <typename T>
-static int occ_p(int block, int ppt, int max_N) {
+static int occ_p(int block, int ppt, int max_N, int n_disc) {
     if (block == 128) {
-        if (ppt == 2) return occ_t<T, 128, 2>(max_N);
-        if (ppt == 8) return occ_t<T, 128, 8>(max_N);
-        return occ_t<T, 128, 4>(max_N);
+        if (ppt == 2) return occ_t<T, 128, 2>(max_N, n_disc);
+        if (ppt == 8) return occ_t<T, 128, 8>(max_N, n_disc);
+        return occ_t<T, 128, 4>(max_N, n_disc);
     }
-    if (ppt == 2) return occ_t<T, 256, 2>(max_N);
-    if (ppt == 8) return occ_t<T, 256, 8>(max_N);
-    return occ_t<T, 256, 4>(max_N);
+    if (ppt == 2) return occ_t<T, 256, 2>(max_N, n_disc);
+    if (ppt == 8) return occ_t<T, 256, 8>(max_N, n_disc);
+    return occ_t<T, 256, 4>(max_N, n_disc);
 }
-int sweep_occupancy(int fp64, int block, int ppt, int max_N) {
-    return fp64 ? occ_p<double>(block, ppt, max_N) : occ_p<float>(block, ppt, max_N);
+int sweep_occupancy(int fp64, int block, int ppt, int max_N, int n_disc) {
+    return fp64 ? occ_p<double>(block, ppt, max_N, n_disc) : occ_p<float>(block, ppt, max_N, n_disc);
 }
 
 cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, int max_slices,
@@ -1960,28 +2084,33 @@ cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, 
 }
 
 cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int src, int dst, unsigned* hist,
-                        const long long* hoff, unsigned* tot, unsigned* kr, unsigned* off, const long long* eoff,
-                        int max_N, int grid_x, cudaStream_t st) {
+                        const long long* hoff, unsigned* tot, unsigned* kr, const long long* eoff, int max_N,
+                        int grid_x, cudaStream_t st) {
     dim3 g(grid_x, 2 * n_disc);
     const size_t smem = sizeof(unsigned) * SORT_NW * max_N;
     cudaError_t e = smem_attr(k_sort_count, smem);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(k_sort_count, g, dim3(SORT_BLOCK), smem, st, discs, ctl, src, hist, hoff, kr, off, eoff, max_N);
+    e = launch_pdl(k_sort_count, g, dim3(SORT_BLOCK), smem, st, discs, ctl, src, hist, hoff, kr, eoff, max_N);
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_pdl(k_sort_rows, dim3((max_N + 31) / 32, 2 * n_disc), dim3(1024), 0, st, discs, ctl, hist, hoff, tot);
+    e = launch_pdl(k_sort_rows, dim3((max_N + 31) / 32, 2 * n_disc), dim3(1024), 0, st, discs, ctl, src, hist, hoff,
+                   tot);
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const dim3 gs(4 * grid_x, 2 * n_disc);
     if (fp64)
-        return launch_pdl(k_sort_scatter<double>, gs, dim3(SORT_BLOCK), 0, st, discs, ctl, src, dst, hist, hoff, tot, kr,
-                          off, eoff);
-    return launch_pdl(k_sort_scatter<float>, gs, dim3(SORT_BLOCK), 0, st, discs, ctl, src, dst, hist, hoff, tot, kr, off,
+        return launch_pdl(k_sort_scatter<double>, g, dim3(SORT_BLOCK), 0, st, discs, ctl, src, dst, hist, hoff, tot, kr,
+                          eoff);
+    return launch_pdl(k_sort_scatter<float>, g, dim3(SORT_BLOCK), 0, st, discs, ctl, src, dst, hist, hoff, tot, kr,
                       eoff);
+}
+
+cudaError_t launch_repack(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int src, int dst, int grid_x,
+                          cudaStream_t st) {
+    const dim3 g(grid_x, 2 * n_disc);
+    if (fp64) return launch_pdl(k_repack<double>, g, dim3(256), 0, st, discs, ctl, src, dst);
+    return launch_pdl(k_repack<float>, g, dim3(256), 0, st, discs, ctl, src, dst);
 }
 
 cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
@@ -1999,16 +2128,16 @@ cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int
 }
 
 
-long long sort_tile() { return SORT_TILE; }
+long long sort_tile_chunks(int chunk) { return (long long)SORT_NW * (SORT_R * 32 / chunk); }
 
 cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, long long n, const unsigned* bad,
-                                 cudaStream_t st) {
-    k_finish_upload<<<1, 1, 0, st>>>(discs, ctl, d, sp, n, bad);
+                                 int buf, cudaStream_t st) {
+    k_finish_upload<<<1, 1, 0, st>>>(discs, ctl, d, sp, n, bad, buf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st) {
-    return launch_pdl(k_set_dense, dim3(1), dim3(128), 0, st, discs, n_disc, ctl);
+cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, int buf, cudaStream_t st) {
+    return launch_pdl(k_set_dense, dim3(1), dim3(128), 0, st, discs, n_disc, ctl, buf);
 }
 
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,

@@ -13,7 +13,7 @@ struct SweepLaunch {
 };
 
 cudaError_t launch_sweep(const SweepLaunch& L);
-int sweep_occupancy(int fp64, int block, int ppt, int max_N);
+int sweep_occupancy(int fp64, int block, int ppt, int max_N, int n_disc);
 cudaError_t launch_finalize(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int out_buf, int mode, int max_slices,
                             int max_N, cudaStream_t st);
 cudaError_t launch_load(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
@@ -25,21 +25,23 @@ cudaError_t launch_backkick(int fp64, const Disc* discs, int n_disc, const Ctl* 
 cudaError_t launch_tables(int fp64, int n_pts, int n_proc, double de, double M, const double* se, const double* si,
                           void* Te, void* Ti, unsigned long long* kmax, cudaStream_t st);
 cudaError_t launch_sort(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int src, int dst, unsigned* hist,
-                        const long long* hoff, unsigned* tot, unsigned* kr, unsigned* off, const long long* eoff,
-                        int max_N, int grid_x, cudaStream_t st);
+                        const long long* hoff, unsigned* tot, unsigned* kr, const long long* eoff, int max_N,
+                        int grid_x, cudaStream_t st);
+cudaError_t launch_repack(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int src, int dst, int grid_x,
+                          cudaStream_t st);
 cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
                               const void* sv, unsigned* bad, int grid, cudaStream_t st);
 cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long n,
                                 int32_t* c, void* sv, int grid, cudaStream_t st);
-long long sort_tile();
+long long sort_tile_chunks(int chunk);
 cudaError_t launch_load_profile(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,
                                 const void* warm, int grid_x, cudaStream_t st);
 size_t warm_desc_bytes(int fp64);
 void warm_desc_fill(int fp64, void* out, const void* cdf_e, const void* cdf_i, const void* eps, int P, double scale,
                     double K23);
-cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, int buf, cudaStream_t st);
 cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, long long n, const unsigned* bad,
-                                 cudaStream_t st);
+                                 int buf, cudaStream_t st);
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_debug_math(long long n, const float* x, const float* y, float* lg, float* sn, float* cs,

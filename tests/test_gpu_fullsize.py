@@ -38,15 +38,17 @@ def _workload(name):
     return c3().scaled(n_e0=2_000_000, n_i0=2_000_000)
 
 
-CASES = [("c2", 256, 2), ("c2", 256, 4), ("c2", 128, 4), ("c3-tenth", 256, 2)]
+# workload, block, particles per thread, sort period, steps. Without a sort the library repacks the
+# stores (order-preserving) every 50 steps at 2000 steps per period; 56 steps cover one repack.
+CASES = [("c2", 256, 2, 16, 32), ("c2", 256, 4, 16, 32), ("c2", 128, 4, 16, 32), ("c3-tenth", 256, 2, 16, 32),
+         ("c2", 256, 2, 0, 56)]
 
 
-@pytest.mark.parametrize("case", CASES, ids=[f"{a}-{b}x{c}" for a, b, c in CASES])
+@pytest.mark.parametrize("case", CASES, ids=[f"{a}-{b}x{c}-sort{k}" for a, b, c, k, _ in CASES])
 def test_fullsize_steps_bit_exact(P, case):
-    name, block, ppt = case
+    name, block, ppt, K, steps = case
     d = _workload(name)
     gas = X.by_name(d.gas, eps_max_eV=d.eps_max_eV, de_eV=d.de_eV)
-    K, steps = 16, 32
     ref = O.Oracle(gas, d, "f32", sort_every=K)
     sim = P.Simulation(gas, d, seed=d.seed, precision="fp32", sort_every=K, block=block, ppt=ppt, load=False)
     for sp in (0, 1):
