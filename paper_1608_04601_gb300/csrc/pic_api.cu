@@ -411,6 +411,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.m_inv_2dx = -1.0 / (2.0 * der.dx);
         D.hdx_eps = der.dx / (2.0 * H_EPS0);
         D.inv_N = 1.0 / (double)d.n_cells;
+        D.inv_dt = 1.0 / d.dt_s;
         D.V0tab = nullptr;
         D.jtab = nullptr;
         {

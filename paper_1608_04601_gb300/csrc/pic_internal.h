@@ -69,7 +69,7 @@ struct Disc {
     // Poisson constants (host-computed, so the FP64 solve needs no device division):
     // r_j = pc_r[1] D_i,j - pc_r[0] D_e,j = rho_j dx^2 / eps0 inside; wall charge density
     // rho = pc_w[1] D_i - pc_w[0] D_e (half-cell volume); 1/dx, -1/(2 dx), dx/(2 eps0), 1/N
-    double pc_r[2], pc_w[2], inv_dx, m_inv_2dx, hdx_eps, inv_N;
+    double pc_r[2], pc_w[2], inv_dx, m_inv_2dx, hdx_eps, inv_N, inv_dt;
     const double* V0tab;      // V_rf sin(2 pi f k dt), k < steps_per_period, or null (then sin on device)
     int has_see, tile;        // sweep tile (slots) of this context
     int chunk, warps;         // compaction unit: one warp's 32 PPT slots; warps per tile

@@ -719,9 +719,14 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             constexpr int NG = (CHUNK / 4 + 1 + 31) / 32;
             const uint32_t did = S.did, thr = S.thr;
             const unsigned q0 = (unsigned)base >> 2;
+            // calls needed: q0 .. (base + cnt - 1) / 4; the last group of calls is drawn only if the
+            // chunk reaches it (an unaligned first slot needs one call beyond CHUNK / 4)
+            const int ncalls = (int)(((unsigned)base + cnt - 1) >> 2) - (int)q0 + 1;
             U4 cw[NG];
 #pragma unroll
-            for (int m = 0; m < NG; ++m) cw[m] = draw(seed, q0 + lane + 32 * m, step, SP, 4, did);
+            for (int m = 0; m < NG; ++m)
+                if (32 * m < ncalls) cw[m] = draw(seed, q0 + lane + 32 * m, step, SP, 4, did);
+                else cw[m] = U4{0, 0, 0, 0};
             // ---- phase A: gather, first half kick, energy moment, candidate test
             int qiq[PPT];
             int qn = 0;
@@ -751,6 +756,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 uint32_t cword = 0;
 #pragma unroll
                 for (int m = 0; m < NG; ++m) {
+                    if (32 * m > 8 * (k + 1)) continue;  // row k needs calls up to 8 (k + 1)
                     const uint32_t w0 = __shfl_sync(FULL, cw[m].x, r & 31), w1 = __shfl_sync(FULL, cw[m].y, r & 31);
                     const uint32_t w2 = __shfl_sync(FULL, cw[m].z, r & 31), w3 = __shfl_sync(FULL, cw[m].w, r & 31);
                     const int wi = slot & 3;
@@ -1137,41 +1143,54 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
     }
     __syncthreads();
     long long em = s_pre[0] + s_w[0][warp] + xm - rm;
-    long long eb = s_pre[1] + s_w[1][warp] + xb - rb;
-    long long es = s_pre[2] + s_w[2][warp] + xs - rs;
-    int err = 0;
+    const long long eb0 = s_pre[1] + s_w[1][warp] + xb - rb;  // this thread's first newborn of each kind
+    const long long es0 = s_pre[2] + s_w[2][warp] + xs - rs;
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {  // rolled: this code runs once per step, from a cold instruction cache
         const long long t = tb + i;
-        const int cm = s_cnt[0][tid * K + i], cb = s_cnt[1][tid * K + i], cs = s_cnt[2][tid * K + i];
-        if (t < chunks) {
-            st[t] = (int)em;  // the first slot of region t of the new layout
-            for (int k = 0; k < cb; ++k) {
-                const long long o = eb + k;
-                if (o < bcap) {
-                    oc_q[o] = bc[t * CHUNK + k];
-                    const R* src = bp + (t * CHUNK + k) * rw;
-                    R* dst = op_q + o * rw;
-                    for (int w = 0; w < rw; ++w) dst[w] = src[w];
-                } else {
-                    err = ERR_CAPACITY;
-                }
+        if (t < chunks) st[t] = (int)em;  // the first slot of region t of the new layout
+        em += s_cnt[0][tid * K + i];
+    }
+    // The newborns of the warp's chunks, copied by the whole warp: newborn j of a kind belongs to the
+    // last lane u whose first newborn is at or before j (a search over the lanes' starts), and within
+    // lane u's K chunks to the one whose running count passes j. All lanes load, then all store.
+    int err = 0;
+#pragma unroll 1
+    for (int kind = 0; kind < 2; ++kind) {
+        if (kind == 1 && sp != 0) break;  // same-species newborns: the electron sweep's only
+        const int row = kind == 0 ? 1 : 2;
+        const long long e0 = kind == 0 ? eb0 : es0;
+        const int r = kind == 0 ? rb : rs;
+        const int32_t* __restrict__ cin = kind == 0 ? bc : sc;
+        const R* __restrict__ pin = kind == 0 ? bp : spr;
+        int32_t* __restrict__ cdst = kind == 0 ? oc_q : oc_0;
+        R* __restrict__ pdst = kind == 0 ? op_q : op_0;
+        const long long w0 = __shfl_sync(FULL, e0, 0), w1 = __shfl_sync(FULL, e0 + r, 31);
+        for (long long jb = w0; jb < w1; jb += 32) {
+            const long long j = jb + lane;
+            int u = 0;  // last lane with start <= j
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long su = __shfl_sync(FULL, e0, u + o);
+                if (su <= j) u += o;
             }
-            for (int k = 0; k < cs; ++k) {
-                const long long o = es + k;
-                if (o < bcap) {
-                    oc_0[o] = sc[t * CHUNK + k];
-                    const R* src = spr + (t * CHUNK + k) * rw;
-                    R* dst = op_0 + o * rw;
-                    for (int w = 0; w < rw; ++w) dst[w] = src[w];
-                } else {
-                    err = ERR_CAPACITY;
-                }
+            const long long su = __shfl_sync(FULL, e0, u);
+            if (j >= w1) continue;
+            long long rem = j - su;
+            int ci = 0;
+            const int tw = (warp * 32 + u) * K;  // lane u's first chunk in the slice
+            while (ci < K - 1 && rem >= s_cnt[row][tw + ci]) rem -= s_cnt[row][tw + ci++];
+            const long long srcr = (t0 + tw + ci) * CHUNK + rem;
+            if (j < bcap) {
+                const int cv = cin[srcr];
+                R rv[2];
+                for (int w = 0; w < rw; ++w) rv[w] = pin[srcr * rw + w];
+                cdst[j] = cv;
+                for (int w = 0; w < rw; ++w) pdst[j * rw + w] = rv[w];
+            } else {
+                err = ERR_CAPACITY;
             }
         }
-        em += cm;
-        eb += cb;
-        es += cs;
     }
     if (err) atomicOr(&ctl->error, err);
 }
@@ -1209,11 +1228,11 @@ __device__ __noinline__ void discharge_current(const Disc& D, int d, Ctl* ctl, i
             for (int k = 0; k < 4; ++k) dA[k] = (double)(c[k] - ctl->cnt_solve[d][k]);
             dS[0] = (double)(c[4] - ctl->cnt_solve[d][4]);
             dS[1] = (double)(c[5] - ctl->cnt_solve[d][5]);
-            const double we = D.w[0], wi = D.w[1], dt = D.dt;
-            const double cond0 = E_CHARGE * (we * dA[0] - wi * dA[2] - we * dS[0]) / dt;
-            const double condN = E_CHARGE * (wi * dA[3] - we * dA[1] + we * dS[1]) / dt;
-            J0 = EPS0 * (Ew[0] - ctl->E_wall[d][0]) / dt + cond0;
-            JN = EPS0 * (Ew[1] - ctl->E_wall[d][1]) / dt + condN;
+            const double we = D.w[0], wi = D.w[1], rdt = D.inv_dt;  // FP64 division is slow on this part
+            const double cond0 = E_CHARGE * (we * dA[0] - wi * dA[2] - we * dS[0]) * rdt;
+            const double condN = E_CHARGE * (wi * dA[3] - we * dA[1] + we * dS[1]) * rdt;
+            J0 = EPS0 * (Ew[0] - ctl->E_wall[d][0]) * rdt + cond0;
+            JN = EPS0 * (Ew[1] - ctl->E_wall[d][1]) * rdt + condN;
         }
         const long long slot = step % D.jh;
         D.J_hist[2 * slot] = J0;
