@@ -362,7 +362,8 @@ def run_gpu(args, rank: int, world: int):
     if args.warm_start and not args.quick and world == 1:
         # rf periods to the steady state from the homogeneous start vs from the network's profiles
         from paper_1608_04601_gb300 import warmstart
-        warm = warmstart.experiment(n_train=args.ws_train, n_test=args.ws_test)
+        warm = warmstart.experiment(n_train=args.ws_train, n_test=args.ws_test, periods=700, train_periods=700,
+                                    avg=200)
 
     # aggregate over ranks: the job took as long as its slowest rank, and did every rank's work
     total_ms, ps = reduce_over_ranks(main["total_ms"], main["ps"], world, "cuda")
@@ -435,8 +436,8 @@ def main():
     ap.add_argument("--no-c3", dest="c3", action="store_false", help="skip the 2e7 + 2e7 particle workload")
     ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
                     help="skip the warm-start experiment (training runs, network training, cold vs warm runs)")
-    ap.add_argument("--ws-train", type=int, default=64, help="training discharges of the warm-start experiment")
-    ap.add_argument("--ws-test", type=int, default=8, help="held-out discharges of the warm-start experiment")
+    ap.add_argument("--ws-train", type=int, default=128, help="training discharges of the warm-start experiment")
+    ap.add_argument("--ws-test", type=int, default=24, help="held-out discharges of the warm-start experiment")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use --block/--ppt/--sort-every as given instead of searching")
     args = ap.parse_args()

@@ -9,8 +9,9 @@ def test_family_is_seeded_and_inside_its_box():
     a, b = W.family(20, 3), W.family(20, 3)
     assert [(d.p_Pa, d.V_rf_V, d.gap_m, d.f_rf_Hz) for d in a] == [(d.p_Pa, d.V_rf_V, d.gap_m, d.f_rf_Hz) for d in b]
     for d in a:
-        assert 16.0 <= d.p_Pa <= 28.0 and 200.0 <= d.V_rf_V <= 500.0 and 0.02 <= d.gap_m <= 0.03
-        assert 10e6 <= d.f_rf_Hz <= 16e6 and d.steps_per_period == 400
+        assert W.P_RANGE[0] <= d.p_Pa <= W.P_RANGE[1] and W.V_RANGE[0] <= d.V_rf_V <= W.V_RANGE[1]
+        assert W.GAP_RANGE[0] <= d.gap_m <= W.GAP_RANGE[1] and W.F_RANGE[0] <= d.f_rf_Hz <= W.F_RANGE[1]
+        assert d.steps_per_period == 400
         assert abs(d.dt_s * d.f_rf_Hz * d.steps_per_period - 1.0) < 1e-12
     assert len({d.discharge_id for d in W.family(5, 1, first_id=100)}) == 5
 
@@ -39,3 +40,11 @@ def test_density_floor_and_energy_floor():
     m = {k: np.zeros(d.n_cells + 1) for k in ("n_e", "n_i", "mean_eps")}
     back = W.from_target(W.to_target(m, d))
     assert np.allclose(back[0], 1e12) and np.allclose(back[1], 1e12) and np.allclose(back[2], 0.1)
+
+
+def test_sign_test_probabilities():
+    """One-sided sign test: P(at least k of n fair coin flips) -- closed forms for small n."""
+    assert W.sign_test_p(8, 8) == 1 / 256
+    assert W.sign_test_p(7, 8) == 9 / 256
+    assert W.sign_test_p(0, 5) == 1.0
+    assert abs(W.sign_test_p(10, 12) - (66 + 12 + 1) / 4096) < 1e-15
