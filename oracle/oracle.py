@@ -74,6 +74,11 @@ class OrcDerived(C.Structure):
         return out
 
 
+class OrcDiagConfig(C.Structure):
+    _fields_ = [("period_steps", C.c_int32), ("phase_step", C.c_int32), ("sample_every", C.c_int32),
+                ("eedf_bins", C.c_int32), ("eedf_de_eV", C.c_double), ("fast_eV", C.c_double)]
+
+
 class OrcMomentInfo(C.Structure):
     _fields_ = [("steps", C.c_int64), ("absorbed", (C.c_double * 2) * 2)]
 
@@ -112,6 +117,11 @@ def _lib(prec: str):
         L.orc_moments.argtypes = [vp, vp, vp, vp, C.POINTER(OrcMomentInfo)]
         L.orc_reset_moments.argtypes = [vp]
         L.orc_last_current.argtypes = [vp, vp]
+        L.orc_set_diagnostics.argtypes = [vp, C.POINTER(OrcDiagConfig)]
+        L.orc_set_diagnostics.restype = C.c_int
+        L.orc_reset_diagnostics.argtypes = [vp]
+        L.orc_diagnostics.argtypes = [vp] + [vp] * 10 + [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.orc_diagnostics.restype = C.c_int
         L.orc_load_profiles.argtypes = [vp, C.c_int, vp, vp, vp]
         L.orc_load_profiles.restype = C.c_int
         L.orc_real_bytes.restype = C.c_int
@@ -330,6 +340,27 @@ class Oracle:
 
     def reset_moments(self):
         self.L.orc_reset_moments(self.h)
+
+    def set_diagnostics(self, period_steps: int, phase_step: int, sample_every: int, eedf_bins: int,
+                        eedf_de_eV: float, fast_eV: float):
+        cfg = OrcDiagConfig(period_steps, phase_step, sample_every, eedf_bins, eedf_de_eV, fast_eV)
+        if self.L.orc_set_diagnostics(self.h, C.byref(cfg)):
+            raise ValueError("orc_set_diagnostics rejected the configuration")
+        self._eedf_bins = eedf_bins
+
+    def reset_diagnostics(self):
+        self.L.orc_reset_diagnostics(self.h)
+
+    def diagnostics(self) -> dict:
+        N1 = self.N + 1
+        keys = ("E", "n_e", "mean_eps", "gamma_e", "q_e", "heating", "ion_rate", "n_fast", "n_fast_avg")
+        out = {k: np.zeros(N1) for k in keys}
+        out["eedf"] = np.zeros(self._eedf_bins)
+        sn, sm = C.c_int64(), C.c_int64()
+        if self.L.orc_diagnostics(self.h, *[_p(out[k]) for k in keys], _p(out["eedf"]), C.byref(sn), C.byref(sm)):
+            raise RuntimeError("diagnostics not configured")
+        out["snapshots"], out["samples"] = sn.value, sm.value
+        return out
 
     def last_current(self) -> np.ndarray:
         """J(t) of the last solved step at z = 0 and at z = d, A/m^2."""

@@ -113,6 +113,12 @@ struct orc_ctx {
     double E_wall_prev[2];
     int64_t abs_prev[2][2], see_side[2], see_prev[2];
     double J_last[2];
+    /* kinetic diagnostics */
+    orc_diag_config dg;
+    int dg_on;
+    int64_t *dg_D, *dg_U, *dg_V, *dg_W, *dg_K, *dg_F, *dg_Fa, *dg_eedf;
+    double* dg_E;
+    int64_t dg_snap, dg_samples;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -436,6 +442,8 @@ void orc_destroy(orc_ctx* o) {
     free(o->Te); free(o->Ti); free(o->E); free(o->E64); free(o->phi); free(o->rho);
     free(o->D[0]); free(o->D[1]); free(o->Dprev_e); free(o->Q);
     free(o->acc_D[0]); free(o->acc_D[1]); free(o->acc_Q); free(o->acc_Dprev);
+    free(o->dg_D); free(o->dg_U); free(o->dg_V); free(o->dg_W); free(o->dg_K); free(o->dg_F); free(o->dg_Fa);
+    free(o->dg_eedf); free(o->dg_E);
     free(o);
 }
 
@@ -928,9 +936,12 @@ void orc_last_current(const orc_ctx* o, double J[2]) {
     J[1] = o->J_last[1];
 }
 
+static void diag_take(orc_ctx* o);
+
 int orc_step(orc_ctx* o, int64_t n_steps) {
     int N = o->N;
     for (int64_t it = 0; it < n_steps; ++it) {
+        if (o->dg_on) diag_take(o);
         if (orc_sweep(o)) return -1;
         int64_t n = o->step;
         if (o->p.sort_every > 0 && (n + 1) % o->p.sort_every == 0)
@@ -1043,5 +1054,135 @@ void orc_get_derived(const orc_ctx* o, orc_derived* out) { *out = o->d; }
 int orc_get_tables(const orc_ctx* o, void* Te, void* Ti) {
     if (Te) memcpy(Te, o->Te, sizeof(real) * (size_t)o->n_pts * 4);
     if (Ti) memcpy(Ti, o->Ti, sizeof(real) * (size_t)o->n_pts * 2);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kinetic diagnostics (see pic_oracle.h). The field average is of the node field the particles
+ * gather (the particle precision). Per electron at (x_n, v_n): the gathered field and the
+ * first half kick as in the sweep, the energy e2 kappa_E in 2^-12 eV clamped at 2^26 as for the
+ * energy moment, then each moment as an integer value X (rounded in the particle precision) split
+ * between the two nodes of its cell like the charge: X - Xh to node c, Xh = rn(X f) to node c+1.
+ * Units of X: density 2^32 per particle (the deposit's F split), energy 2^-12 eV, particle flux
+ * v_z 2^6 (1/64 m/s), energy flux U v_z 2^-4 (16 eV m/s, formed as eq v_z 2^-16), ionization rate
+ * coefficient sigma_iz v 2^72 (m^3/s).                                                         */
+int orc_set_diagnostics(orc_ctx* o, const orc_diag_config* cfg) {
+    if (!cfg || cfg->period_steps < 0 || cfg->eedf_bins < 1 || !(cfg->eedf_de_eV > 0)) return -1;
+    o->dg = *cfg;
+    size_t N1 = (size_t)o->N + 1;
+    int64_t** arr[7] = {&o->dg_D, &o->dg_U, &o->dg_V, &o->dg_W, &o->dg_K, &o->dg_F, &o->dg_Fa};
+    for (int k = 0; k < 7; ++k) {
+        free(*arr[k]);
+        *arr[k] = (int64_t*)calloc(N1, sizeof(int64_t));
+    }
+    free(o->dg_eedf);
+    o->dg_eedf = (int64_t*)calloc((size_t)cfg->eedf_bins, sizeof(int64_t));
+    free(o->dg_E);
+    o->dg_E = (double*)calloc(N1, sizeof(double));
+    o->dg_on = 1;
+    orc_reset_diagnostics(o);
+    return 0;
+}
+
+void orc_reset_diagnostics(orc_ctx* o) {
+    if (!o->dg_on) return;
+    size_t N1 = (size_t)o->N + 1;
+    int64_t* arr[7] = {o->dg_D, o->dg_U, o->dg_V, o->dg_W, o->dg_K, o->dg_F, o->dg_Fa};
+    for (int k = 0; k < 7; ++k) memset(arr[k], 0, sizeof(int64_t) * N1);
+    memset(o->dg_eedf, 0, sizeof(int64_t) * (size_t)o->dg.eedf_bins);
+    memset(o->dg_E, 0, sizeof(double) * N1);
+    o->dg_snap = 0;
+    o->dg_samples = 0;
+}
+
+static void split_add(int64_t* h, int32_t c, real x, real f) {
+    int64_t X = (int64_t)R_RINT(x), Xh = (int64_t)R_RINT(x * f);
+    h[c] += X - Xh;
+    h[c + 1] += Xh;
+}
+
+static void diag_take(orc_ctx* o) {
+    const int64_t n = o->step;
+    const int P = o->dg.period_steps;
+    const int phase = P > 0 && o->dg.phase_step >= 0 && n % P == o->dg.phase_step;
+    const int sample = o->dg.sample_every > 0 && n % o->dg.sample_every == 0;
+    if (!phase && !sample) return;
+    const int N = o->N, bins = o->dg.eedf_bins;
+    const real thr = (real)(o->dg.fast_eV * 4096.0);          /* 2^-12 eV */
+    const real inv_bin = (real)(1.0 / (o->dg.eedf_de_eV * 4096.0));
+    const int ciz = o->n_proc_e - 1;                          /* ionization column of the table */
+    const store* s = &o->s[SP_E];
+    if (phase) {
+        for (int j = 0; j <= N; ++j) o->dg_E[j] += (double)o->E[j];
+        o->dg_snap++;
+    }
+    if (sample) o->dg_samples++;
+    for (int64_t k = 0; k < s->n; ++k) {
+        const int32_t c = s->c[k];
+        const real f = s->f[k], vx = s->vx[k], vy = s->vy[k];
+        const real ef = gather(o, c, f);
+        const real vz = R_FMA(o->K_e, ef, s->vz[k]);           /* v_n */
+        const real e2 = R_FMA(vx, vx, R_FMA(vy, vy, vz * vz));
+        real eq = e2 * o->kappa_E;
+        if (!(eq <= (real)0x1p26)) eq = (real)0x1p26;
+        const int64_t F = (int64_t)R_RINT(f * (real)TWO32);
+        const int fast = eq > thr;
+        if (phase) {
+            o->dg_D[c] += (int64_t)4294967296LL - F;
+            o->dg_D[c + 1] += F;
+            split_add(o->dg_U, c, eq, f);
+            split_add(o->dg_V, c, vz * (real)64.0, f);
+            split_add(o->dg_W, c, (eq * vz) * (real)0x1p-16, f);
+            real C[4];
+            lookup(o->Te, 4, o->n_pts, e2 * o->kappa_e, C);
+            split_add(o->dg_K, c, (C[ciz] - C[ciz - 1]) * (real)0x1p72, f);
+            if (fast) {
+                o->dg_F[c] += (int64_t)4294967296LL - F;
+                o->dg_F[c + 1] += F;
+            }
+        }
+        if (sample) {
+            int b = (int)(eq * inv_bin);
+            if (b >= bins) b = bins - 1;
+            o->dg_eedf[b]++;
+            if (fast) {
+                o->dg_Fa[c] += (int64_t)4294967296LL - F;
+                o->dg_Fa[c + 1] += F;
+            }
+        }
+    }
+}
+
+int orc_diagnostics(const orc_ctx* o, double* E, double* n_e, double* mean_eps, double* gamma_e, double* q_e,
+                    double* heating, double* ion_rate, double* n_fast, double* n_fast_avg, double* eedf,
+                    int64_t* snapshots, int64_t* samples) {
+    if (!o->dg_on) return -1;
+    const int N = o->N;
+    const double dx = o->d.dx, w = o->p.w_e;
+    const double ns = o->dg_snap > 0 ? (double)o->dg_snap : 1.0, nm = o->dg_samples > 0 ? (double)o->dg_samples : 1.0;
+    for (int j = 0; j <= N; ++j) {
+        const double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
+        const double Ej = o->dg_E[j] / ns;
+        const double g = w * (double)o->dg_V[j] / 64.0 / (Vj * ns);
+        if (E) E[j] = Ej;
+        if (n_e) n_e[j] = w * (double)o->dg_D[j] / (TWO32 * Vj * ns);
+        if (mean_eps) mean_eps[j] = o->dg_D[j] > 0 ? ((double)o->dg_U[j] / 4096.0) / ((double)o->dg_D[j] / TWO32) : 0.0;
+        if (gamma_e) gamma_e[j] = g;
+        if (q_e) q_e[j] = w * E_CHARGE * (double)o->dg_W[j] * 16.0 / (Vj * ns);
+        if (heating) heating[j] = -E_CHARGE * Ej * g;
+        if (ion_rate) ion_rate[j] = o->d.n_gas * w * (double)o->dg_K[j] * 0x1p-72 / (Vj * ns);
+        if (n_fast) n_fast[j] = w * (double)o->dg_F[j] / (TWO32 * Vj * ns);
+        if (n_fast_avg) n_fast_avg[j] = w * (double)o->dg_Fa[j] / (TWO32 * Vj * nm);
+    }
+    if (eedf) {
+        double tot = 0.0;
+        for (int b = 0; b < o->dg.eedf_bins; ++b) tot += (double)o->dg_eedf[b];
+        for (int b = 0; b < o->dg.eedf_bins; ++b) {
+            const double U = (b + 0.5) * o->dg.eedf_de_eV;
+            eedf[b] = tot > 0 ? (double)o->dg_eedf[b] / (tot * o->dg.eedf_de_eV * sqrt(U)) : 0.0;
+        }
+    }
+    if (snapshots) *snapshots = o->dg_snap;
+    if (samples) *samples = o->dg_samples;
     return 0;
 }

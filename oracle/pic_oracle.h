@@ -136,6 +136,30 @@ void     orc_reset_moments(orc_ctx* o);
  * after the first solve of a run (no previous field).                                         */
 void     orc_last_current(const orc_ctx* o, double J[2]);
 
+/* Kinetic diagnostics of the electrons (section "Results": the EEDF figure, the fast-electron
+ * density and the profiles at t f = 0.25), taken at (x_n, v_n) before the sweep of step n:
+ *   - phase-resolved: at every step n with n % period_steps == phase_step, the node field E and
+ *     the cloud-in-cell moments density, mean energy, particle flux Gamma_e, energy flux Q_e,
+ *     ionization rate S (the rate coefficient sigma_iz v of each electron times n_gas), fast
+ *     electrons (energy above fast_eV), accumulated over such steps;
+ *   - sampled every sample_every steps: the energy histogram (eedf_bins bins of eedf_de_eV, the
+ *     last bin also takes higher energies) and the fast-electron density.
+ * Every per-particle value is formed in the particle precision and rounded to an integer, so the
+ * accumulators are exact sums. The read-out gives physical units (see orc_diagnostics).       */
+typedef struct {
+    int32_t period_steps, phase_step, sample_every, eedf_bins;
+    double eedf_de_eV, fast_eV;
+} orc_diag_config;
+int  orc_set_diagnostics(orc_ctx* o, const orc_diag_config* cfg);   /* resets the accumulators */
+void orc_reset_diagnostics(orc_ctx* o);
+/* Read-out (each array may be NULL): E [V/m], n_e [m^-3], mean_eps [eV], gamma_e [m^-2 s^-1],
+ * q_e [W m^-2], heating = -e0 E Gamma_e [W m^-3], ion_rate [m^-3 s^-1], n_fast [m^-3] averaged
+ * over the phase snapshots (N+1 nodes each); n_fast_avg [m^-3] over the samples; eedf
+ * [eedf_bins] f0(U)/n_e at the bin centres [eV^-3/2]; snapshots and samples counted.          */
+int  orc_diagnostics(const orc_ctx* o, double* E, double* n_e, double* mean_eps, double* gamma_e, double* q_e,
+                     double* heating, double* ion_rate, double* n_fast, double* n_fast_avg, double* eedf,
+                     int64_t* snapshots, int64_t* samples);
+
 /* Building blocks, exported for the pins. */
 void     orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 float    orc_uniform(uint32_t x);
