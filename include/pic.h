@@ -205,6 +205,51 @@ pic_status pic_current_amplitude(pic_ctx* ctx, int32_t discharge, int64_t first,
                                  int64_t* periods_done);
 pic_status pic_reset_moments(pic_ctx* ctx);
 
+/* ---- kinetic diagnostics of the electrons (section "Results") -------------
+ * Taken from the electron store at (x_n, v_n), before the sweep of step n of pic_step, on
+ * the device (one or two extra launches at such a step, none at other steps):
+ *   - rf-phase snapshots at every step n with period_steps > 0 and n % period_steps ==
+ *     phase_step (the paper's profiles at t f = 0.25 take period_steps = steps_per_period,
+ *     phase_step = steps_per_period / 4): the node field E and the cloud-in-cell node moments
+ *     density n_e, mean energy, particle flux Gamma_e, energy flux Q_e, ionization rate S (each
+ *     electron's sigma_iz v times n_gas), heating -e0 E Gamma_e and fast-electron density
+ *     (energy above fast_eV; the paper takes e0 V0 / 4);
+ *   - samples at every step n with sample_every > 0 and n % sample_every == 0: the energy
+ *     histogram of eedf_bins bins of eedf_de_eV (the last bin also takes higher energies) and
+ *     the fast-electron density.
+ * Per electron: the gathered field and the first half kick as in the sweep, its energy in
+ * 2^-12 eV (clamped at 2^26), and per node moment an integer (rounded in the particle
+ * precision) split between the two nodes of its cell like the charge; density 2^32 per
+ * particle, energy 2^-12 eV, v_z 2^-6 m/s, energy x v_z 2^-4 eV m/s, sigma_iz v 2^-72 m^3/s.
+ * The sums are exact, hence independent of the order of the particles.
+ * With graphs (pic_options.use_graph), rf periods run as graphs only while both schedules
+ * repeat every rf period (period_steps and sample_every divide steps_per_period, or are 0);
+ * otherwise steps are launched one by one.                                                 */
+typedef struct {
+    int32_t period_steps;   /* 0: no snapshots                                            */
+    int32_t phase_step;     /* 0 .. period_steps - 1                                      */
+    int32_t sample_every;   /* 0: no samples                                              */
+    int32_t eedf_bins;      /* 1 .. PIC_DIAG_MAX_BINS                                     */
+    double eedf_de_eV;      /* bin width, > 0                                             */
+    double fast_eV;         /* fast-electron threshold, >= 0                              */
+} pic_diag_config;
+#define PIC_DIAG_MAX_BINS 16384
+/* Configures (cfg) or switches off (cfg NULL) the diagnostics of every discharge; clears the
+ * accumulators. Allocates device memory (and so synchronises the context's stream); not
+ * allowed while the stream is being captured. PIC_ERR_ARG for a configuration out of range. */
+pic_status pic_set_diagnostics(pic_ctx* ctx, const pic_diag_config* cfg);
+/* Clears the accumulators (stream-ordered). PIC_ERR_STATE if not configured.             */
+pic_status pic_reset_diagnostics(pic_ctx* ctx);
+/* Read-out of one discharge (host arrays, each may be NULL): E [V/m], n_e [m^-3], mean_eps
+ * [eV], gamma_e [m^-2 s^-1], q_e [W m^-2], heating [W m^-3], ion_rate [m^-3 s^-1], n_fast
+ * [m^-3] averaged over the snapshots, n_fast_avg [m^-3] over the samples (N+1 nodes each; the
+ * wall nodes own half a cell); eedf [eedf_bins]: f0(U)/n_e at the bin centres U [eV^-3/2],
+ * normalised so that sum_b eedf_b sqrt(U_b) eedf_de_eV = 1; snapshots and samples taken.
+ * Synchronises the stream. PIC_ERR_STATE if not configured.                                 */
+pic_status pic_diagnostics(pic_ctx* ctx, int32_t discharge, double* E, double* n_e, double* mean_eps,
+                           double* gamma_e, double* q_e, double* heating, double* ion_rate, double* n_fast,
+                           double* n_fast_avg, double* eedf, int64_t* snapshots, int64_t* samples);
+
 void        pic_destroy(pic_ctx* ctx);         /* NULL-safe                 */
 const char* pic_last_error(const pic_ctx* ctx);
 const char* pic_status_string(pic_status s);

@@ -1142,8 +1142,8 @@ static void diag_take(orc_ctx* o) {
             }
         }
         if (sample) {
-            int b = (int)(eq * inv_bin);
-            if (b >= bins) b = bins - 1;
+            const real xb = eq * inv_bin;                     /* bin index, clamped before the conversion */
+            const int b = xb < (real)bins ? (int)xb : bins - 1;
             o->dg_eedf[b]++;
             if (fast) {
                 o->dg_Fa[c] += (int64_t)4294967296LL - F;

@@ -49,6 +49,11 @@ class PicMoments(C.Structure):
                 ("J_amp", C.c_double), ("J_last", C.c_double)]
 
 
+class PicDiagConfig(C.Structure):
+    _fields_ = [("period_steps", C.c_int32), ("phase_step", C.c_int32), ("sample_every", C.c_int32),
+                ("eedf_bins", C.c_int32), ("eedf_de_eV", C.c_double), ("fast_eV", C.c_double)]
+
+
 class PicCounters(C.Structure):
     _fields_ = [("absorbed", (C.c_int64 * 2) * 2), ("collisions_e", C.c_int64 * 4),
                 ("collisions_i", C.c_int64 * 2), ("null_inelastic", C.c_int64), ("see_emitted", C.c_int64),
@@ -117,6 +122,9 @@ PROTOTYPES = {
     "pic_current": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
     "pic_current_amplitude": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
     "pic_load_profiles": (C.c_int, [_vp, _i32, _vp]),
+    "pic_set_diagnostics": (C.c_int, [_vp, C.POINTER(PicDiagConfig)]),
+    "pic_reset_diagnostics": (C.c_int, [_vp]),
+    "pic_diagnostics": (C.c_int, [_vp, _i32] + [_vp] * 10 + [C.POINTER(_i64), C.POINTER(_i64)]),
     # include/mlp.h
     "mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _vp, _i32, _u64, _vp]),
     "mlp_param_count": (_i64, [_vp]),

@@ -70,6 +70,11 @@ struct pic_ctx {
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graphs;
+    // kinetic diagnostics (pic_set_diagnostics): configuration, device allocations, whether both
+    // schedules repeat every rf period (then periods may run as graphs)
+    bool dg_on = false, dg_periodic = true;
+    pic_diag_config dg{};
+    std::vector<void*> dg_allocs;
 };
 
 static pic_status fail(pic_ctx* c, pic_status s, const std::string& msg) {
@@ -213,6 +218,7 @@ extern "C" void pic_destroy(pic_ctx* ctx) {
         cudaEventDestroy(e.second);
     }
     for (void* p : ctx->allocs) cudaFree(p);
+    for (void* p : ctx->dg_allocs) cudaFree(p);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -666,9 +672,46 @@ static pic_status enqueue_repack(pic_ctx* ctx) {
     return PIC_OK;
 }
 
+// Diagnostics of step n = ctx->step, before its sweep, when the schedules ask for them: one k_diag
+// launch, or two when the node arrays of the snapshot do not fit the shared memory together.
+static pic_status enqueue_diag(pic_ctx* ctx) {
+    const pic_diag_config& g = ctx->dg;
+    const long long n = ctx->step;
+    const bool phase = g.period_steps > 0 && n % g.period_steps == g.phase_step;
+    const bool sample = g.sample_every > 0 && n % g.sample_every == 0;
+    if (!phase && !sample) return PIC_OK;
+    unsigned left = (phase ? DG_PHASE_MASK : 0u) | (sample ? DG_SAMPLE_MASK : 0u);
+    constexpr size_t budget = 200 * 1024;
+    bool first = true;
+    while (left) {
+        DiagArgs A{};
+        A.mode = first ? (phase ? DIAG_PHASE : 0) | (sample ? DIAG_SAMPLE : 0) | DIAG_COUNT : 0;
+        A.bins = g.eedf_bins;
+        A.thr = g.fast_eV * 4096.0;
+        A.inv_bin = 1.0 / (g.eedf_de_eV * 4096.0);
+        const int bins = (A.mode & DIAG_SAMPLE) ? g.eedf_bins : 0;
+        for (int a = 0; a < DG_ARRAYS; ++a) {
+            const unsigned bit = 1u << a;
+            if ((left & bit) && (A.mask == 0 || diag_smem(ctx->max_N, A.mask | bit, bins) <= budget)) A.mask |= bit;
+        }
+        left &= ~A.mask;
+        const size_t smem = diag_smem(ctx->max_N, A.mask, bins);
+        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (220 * 1024) / std::max<size_t>(smem, 1)));
+        CK(launch_diag(ctx->fp64, ctx->d_discs, ctx->n_disc, ctx->d_ctl, ctx->cur, A, ctx->max_N,
+                       std::max(1, ctx->num_sms * per_sm), ctx->stream),
+           "diagnostics launch");
+        first = false;
+    }
+    return PIC_OK;
+}
+
 // Sweep + births + solve: the sweep reads buffer cur and writes 1-cur; the
 // finalize appends births into 1-cur; cur flips. Then the sort, or the repack, when due.
 static pic_status enqueue_step(pic_ctx* ctx) {
+    if (ctx->dg_on) {
+        pic_status s0 = enqueue_diag(ctx);
+        if (s0 != PIC_OK) return s0;
+    }
     pic_status s = enqueue_sweep(ctx);
     if (s != PIC_OK) return s;
     s = enqueue_finalize(ctx, 3);
@@ -722,7 +765,8 @@ extern "C" pic_status pic_step(pic_ctx* ctx, int64_t n_steps) {
     if (!ctx || n_steps < 0) return PIC_ERR_ARG;
     const int P = ctx->dis[0].weights.steps_per_period;
     const int K = ctx->opt.sort_every;
-    const bool graphs = ctx->opt.use_graph && P > 0 && (K <= 0 || P % K == 0) && !ctx->timing;
+    const bool graphs = ctx->opt.use_graph && P > 0 && (K <= 0 || P % K == 0) && !ctx->timing &&
+                        (!ctx->dg_on || ctx->dg_periodic);
     int64_t left = n_steps;
     while (left > 0) {
         if (graphs && left >= P) {
@@ -1118,6 +1162,122 @@ extern "C" pic_status pic_reset_moments(pic_ctx* ctx) {
         pic_status s = read_counters(ctx, d, &ctx->cnt_at_reset[d]);
         if (s != PIC_OK) return s;
     }
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kinetic diagnostics.
+static void drop_graphs(pic_ctx* ctx) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+extern "C" pic_status pic_set_diagnostics(pic_ctx* ctx, const pic_diag_config* cfg) {
+    if (!ctx) return PIC_ERR_ARG;
+    if (cfg && (cfg->period_steps < 0 || cfg->sample_every < 0 || cfg->eedf_bins < 1 ||
+                cfg->eedf_bins > PIC_DIAG_MAX_BINS || !(cfg->eedf_de_eV > 0) || !(cfg->fast_eV >= 0) ||
+                !std::isfinite(cfg->eedf_de_eV) || !std::isfinite(cfg->fast_eV) ||
+                (cfg->period_steps > 0 && (cfg->phase_step < 0 || cfg->phase_step >= cfg->period_steps))))
+        return fail(ctx, PIC_ERR_ARG, "diagnostics configuration out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs), "capture status");
+    if (cs != cudaStreamCaptureStatusNone) return fail(ctx, PIC_ERR_STATE, "diagnostics configured during a capture");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    drop_graphs(ctx);  // their steps were captured with the old schedule
+    for (void* p : ctx->dg_allocs) cudaFree(p);
+    ctx->dg_allocs.clear();
+    ctx->dg_on = false;
+    for (auto& D : ctx->hd) D.dg = nullptr, D.dg_E = nullptr, D.dg_eedf = nullptr, D.dg_n = nullptr;
+    if (cfg) {
+        for (auto& D : ctx->hd) {
+            const size_t N1 = (size_t)D.N + 1;
+            void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+            const size_t bytes[4] = {8 * N1 * DG_ARRAYS, 8 * N1, 8 * (size_t)cfg->eedf_bins, 16};
+            for (int q = 0; q < 4; ++q) {
+                CK(cudaMalloc(&p[q], bytes[q]), "diagnostics allocation");
+                ctx->dg_allocs.push_back(p[q]);
+                CK(cudaMemsetAsync(p[q], 0, bytes[q], ctx->stream), "diagnostics clear");
+            }
+            D.dg = static_cast<unsigned long long*>(p[0]);
+            D.dg_E = static_cast<double*>(p[1]);
+            D.dg_eedf = static_cast<unsigned long long*>(p[2]);
+            D.dg_n = static_cast<unsigned long long*>(p[3]);
+        }
+        ctx->dg = *cfg;
+        const int P = ctx->dis[0].weights.steps_per_period;
+        ctx->dg_periodic = P > 0 && (cfg->period_steps == 0 || P % cfg->period_steps == 0) &&
+                           (cfg->sample_every == 0 || P % cfg->sample_every == 0);
+    }
+    CK(cudaMemcpyAsync(ctx->d_discs, ctx->hd.data(), sizeof(Disc) * ctx->n_disc, cudaMemcpyHostToDevice, ctx->stream),
+       "descriptor upload");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    ctx->dg_on = cfg != nullptr;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_reset_diagnostics(pic_ctx* ctx) {
+    if (!ctx) return PIC_ERR_ARG;
+    if (!ctx->dg_on) return fail(ctx, PIC_ERR_STATE, "diagnostics not configured");
+    for (auto& D : ctx->hd) {
+        const size_t N1 = (size_t)D.N + 1;
+        CK(cudaMemsetAsync(D.dg, 0, 8 * N1 * DG_ARRAYS, ctx->stream), "diagnostics clear");
+        CK(cudaMemsetAsync(D.dg_E, 0, 8 * N1, ctx->stream), "diagnostics clear");
+        CK(cudaMemsetAsync(D.dg_eedf, 0, 8 * (size_t)ctx->dg.eedf_bins, ctx->stream), "diagnostics clear");
+        CK(cudaMemsetAsync(D.dg_n, 0, 16, ctx->stream), "diagnostics clear");
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_diagnostics(pic_ctx* ctx, int32_t d, double* E, double* n_e, double* mean_eps,
+                                      double* gamma_e, double* q_e, double* heating, double* ion_rate,
+                                      double* n_fast, double* n_fast_avg, double* eedf, int64_t* snapshots,
+                                      int64_t* samples) {
+    if (bad_d(ctx, d)) return PIC_ERR_ARG;
+    if (!ctx->dg_on) return fail(ctx, PIC_ERR_STATE, "diagnostics not configured");
+    const Disc& D = ctx->hd[d];
+    const int N = D.N, bins = ctx->dg.eedf_bins;
+    const size_t N1 = (size_t)N + 1;
+    const size_t o_E = 8 * N1 * DG_ARRAYS, o_h = o_E + 8 * N1, o_n = o_h + 8 * (size_t)bins;
+    pic_status s = pinned(ctx, o_n + 16);
+    if (s != PIC_OK) return s;
+    unsigned char* h = static_cast<unsigned char*>(ctx->h_pin);
+    CK(cudaMemcpyAsync(h, D.dg, o_E, cudaMemcpyDeviceToHost, ctx->stream), "diagnostics");
+    CK(cudaMemcpyAsync(h + o_E, D.dg_E, 8 * N1, cudaMemcpyDeviceToHost, ctx->stream), "diagnostics");
+    CK(cudaMemcpyAsync(h + o_h, D.dg_eedf, 8 * (size_t)bins, cudaMemcpyDeviceToHost, ctx->stream), "diagnostics");
+    CK(cudaMemcpyAsync(h + o_n, D.dg_n, 16, cudaMemcpyDeviceToHost, ctx->stream), "diagnostics");
+    CK(cudaStreamSynchronize(ctx->stream), "diagnostics");
+    const long long* A = reinterpret_cast<const long long*>(h);  // exact sums, two's complement
+    const long long *aD = A + DG_D * N1, *aU = A + DG_U * N1, *aV = A + DG_V * N1, *aW = A + DG_W * N1,
+                    *aK = A + DG_K * N1, *aF = A + DG_F * N1, *aFa = A + DG_FA * N1;
+    const double* sE = reinterpret_cast<const double*>(h + o_E);
+    const unsigned long long* hb = reinterpret_cast<const unsigned long long*>(h + o_h);
+    const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(h + o_n);
+    const double dx = D.dx, w = D.w[0], n_gas = ctx->der[d].n_gas;
+    const double ns = cnt[0] > 0 ? (double)cnt[0] : 1.0, nm = cnt[1] > 0 ? (double)cnt[1] : 1.0;
+    for (int j = 0; j <= N; ++j) {
+        const double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
+        const double Ej = sE[j] / ns;
+        const double g = w * (double)aV[j] / 64.0 / (Vj * ns);
+        if (E) E[j] = Ej;
+        if (n_e) n_e[j] = w * (double)aD[j] / (H_TWO32 * Vj * ns);
+        if (mean_eps) mean_eps[j] = aD[j] > 0 ? ((double)aU[j] / 4096.0) / ((double)aD[j] / H_TWO32) : 0.0;
+        if (gamma_e) gamma_e[j] = g;
+        if (q_e) q_e[j] = w * H_E_CHARGE * (double)aW[j] * 16.0 / (Vj * ns);
+        if (heating) heating[j] = -H_E_CHARGE * Ej * g;
+        if (ion_rate) ion_rate[j] = n_gas * w * (double)aK[j] * 0x1p-72 / (Vj * ns);
+        if (n_fast) n_fast[j] = w * (double)aF[j] / (H_TWO32 * Vj * ns);
+        if (n_fast_avg) n_fast_avg[j] = w * (double)aFa[j] / (H_TWO32 * Vj * nm);
+    }
+    if (eedf) {
+        double tot = 0.0;
+        for (int b = 0; b < bins; ++b) tot += (double)hb[b];
+        for (int b = 0; b < bins; ++b) {
+            const double U = (b + 0.5) * ctx->dg.eedf_de_eV;
+            eedf[b] = tot > 0 ? (double)hb[b] / (tot * ctx->dg.eedf_de_eV * std::sqrt(U)) : 0.0;
+        }
+    }
+    if (snapshots) *snapshots = (int64_t)cnt[0];
+    if (samples) *samples = (int64_t)cnt[1];
     return PIC_OK;
 }
 

@@ -117,6 +117,30 @@ struct Disc {
     int jh;
     const double* jtab;       // sin, cos of 2 pi f (k + 1/2) dt, k < steps_per_period, or null
     double* J_amp;            // [PERIOD_HIST]
+    // kinetic diagnostics (null until configured): node accumulators [DG_ARRAYS][N+1], sum of the
+    // node field over the snapshots [N+1], EEDF counts [bins], snapshots and samples taken [2]
+    unsigned long long* dg;
+    double* dg_E;
+    unsigned long long* dg_eedf;
+    unsigned long long* dg_n;
+};
+
+// Node arrays of the kinetic diagnostics (k_diag): density, energy, particle flux, energy flux,
+// ionization rate, fast electrons (snapshots), fast electrons (samples).
+enum { DG_D = 0, DG_U, DG_V, DG_W, DG_K, DG_F, DG_FA, DG_ARRAYS };
+enum : int { DIAG_PHASE = 1, DIAG_SAMPLE = 2, DIAG_COUNT = 4 };
+constexpr unsigned DG_PHASE_MASK = 0x3Fu, DG_SAMPLE_MASK = 1u << DG_FA;
+
+// One k_diag launch: what it takes (DIAG_* bits; DIAG_COUNT: this launch also sums the field and
+// counts the snapshot or sample), the node arrays it accumulates, the EEDF bins, the fast-electron
+// threshold and the inverse bin width, both in 2^-12 eV units (rounded to the particle precision
+// on the device).
+struct DiagArgs {
+    int mode;
+    unsigned mask;
+    int bins;
+    int pad_;
+    double thr, inv_bin;
 };
 
 // Control block; one per context, in device memory.

@@ -11,13 +11,15 @@
 //               chunk's newborn regions, with no barrier inside a tile. CIC
 //               deposits go to warp-aggregated shared-memory int64 histograms,
 //               flushed with global atomics. Chunk counts are summed per slice.
-//   k_post      per slice of chunks: the segment table entries and the newborn
-//               copies; per discharge, concurrently: the store totals (new
-//               counts) and Poisson (Eq. poisson, rf Dirichlet boundary) from
-//               exact integer prefix sums of the deposits, node field,
-//               cycle-average accumulators.
+//   k_post      per slice of chunks: the region starts of the new layout and
+//               the newborn copies; per discharge, concurrently: the store
+//               totals (new counts) and Poisson (Eq. poisson, rf Dirichlet
+//               boundary) from exact integer prefix sums of the deposits, node
+//               field, cycle-average accumulators, J(t).
 //   sort        every K steps: stable counting sort of each store by cell
-//               into a dense store.
+//               into a dense store (else an order-preserving repack).
+//   k_diag      at the steps the diagnostics schedule names, before the sweep:
+//               the electrons' node moments and energy histogram.
 #include "pic_internal.h"
 #include "pic_device.cuh"
 
@@ -1582,6 +1584,180 @@ __device__ __forceinline__ ChunkDesc chunk_desc(const Lay& L, long long n, const
     return c;
 }
 
+// ---------------------------------------------------------------------------
+// Kinetic diagnostics of the electrons (section "Results": the EEDF, the fast-electron density and
+// the profiles at a fixed rf phase), taken from the store at (x_n, v_n) before the sweep of step n.
+// Per electron: the gathered field and the first half kick as in the sweep, the energy in 2^-12 eV
+// clamped at 2^26, then per node array an integer value X rounded in the particle precision and
+// split like the charge (X - rn(X f) to node c, rn(X f) to node c + 1). Units of X:
+//   DG_D  2^32 per particle (the deposit's F split)     DG_U  energy, 2^-12 eV
+//   DG_V  v_z, 2^-6 m/s                                  DG_W  energy x v_z, formed as (eq v_z) 2^-16
+//   DG_K  ionization rate coefficient, 2^-72 m^3/s       DG_F  2^32 per electron above the threshold
+//   DG_FA as DG_F, at the EEDF samples
+// Sums are exact (int64, mod 2^64); warp groups of equal cells are reduced in three 22/22/20-bit
+// parts, so no partial sum overflows 32 bits.
+template <typename T> __device__ __forceinline__ long long rint_ll(T x);
+template <> __device__ __forceinline__ long long rint_ll<float>(float x) { return __float2ll_rn(x); }
+template <> __device__ __forceinline__ long long rint_ll<double>(double x) { return __double2ll_rn(x); }
+
+__device__ __forceinline__ unsigned long long group_sum64(unsigned peers, unsigned long long v) {
+    const unsigned a = __reduce_add_sync(peers, (unsigned)(v & 0x3FFFFFu));
+    const unsigned b = __reduce_add_sync(peers, (unsigned)((v >> 22) & 0x3FFFFFu));
+    const unsigned c = __reduce_add_sync(peers, (unsigned)(v >> 44));
+    return (unsigned long long)a + ((unsigned long long)b << 22) + ((unsigned long long)c << 44);
+}
+
+// a to node key, b to node key + 1 of a shared histogram; by group (as warp_hist) unless the
+// warp's keys form more than HIST_GROUPS groups, then lane by lane.
+__device__ __forceinline__ void warp_add_pair(unsigned long long* h, int key, unsigned long long a,
+                                              unsigned long long b, unsigned peers, bool leader, bool lanewise) {
+    if (lanewise) {
+        if (key >= 0) {
+            if (a) sadd64(&h[key], a);
+            if (b) sadd64(&h[key + 1], b);
+        }
+        return;
+    }
+    const unsigned long long sa = group_sum64(peers, a), sb = group_sum64(peers, b);
+    if (leader && key >= 0) {
+        if (sa) sadd64(&h[key], sa);
+        if (sb) sadd64(&h[key + 1], sb);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void split_rint(T x, T f, unsigned long long& a, unsigned long long& b) {
+    const long long X = rint_ll<T>(x), Xh = rint_ll<T>(mul_(x, f));
+    a = (unsigned long long)(X - Xh);
+    b = (unsigned long long)Xh;
+}
+
+template <typename T4r, typename T>
+__device__ __forceinline__ T col4(const T4r& r, int j) {
+    return j == 0 ? r.x : j == 1 ? r.y : j == 2 ? r.z : r.w;
+}
+
+constexpr int DIAG_BLOCK = 256, DIAG_NW = DIAG_BLOCK / 32;
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_BLOCK) k_diag(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl,
+                                                     int buf, DiagArgs A) {
+    grid_dep_sync();
+    extern __shared__ __align__(16) unsigned long long s_dg[];  // [arrays of the mask][N + 1], EEDF [bins] u32
+    using R = typename Rec<T>::type;
+    using Row4 = typename T4<T>::type;
+    const int d = blockIdx.y;
+    const Disc& D = discs[d];
+    const int N = D.N, N1 = N + 1, CHUNK = D.chunk, RPC = CHUNK / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool phase = A.mode & DIAG_PHASE, sample = A.mode & DIAG_SAMPLE;
+    const int nar = __popc(A.mask), nb = sample ? A.bins : 0;
+    unsigned* s_eedf = reinterpret_cast<unsigned*>(s_dg + (size_t)nar * N1);
+    for (int j = tid; j < nar * N1; j += DIAG_BLOCK) s_dg[j] = 0;
+    for (int j = tid; j < nb; j += DIAG_BLOCK) s_eedf[j] = 0;
+    const T* E = reinterpret_cast<const T*>(D.E);
+    if (blockIdx.x == 0 && (A.mode & DIAG_COUNT)) {  // field sum of the snapshot, snapshot and sample counts
+        if (phase)
+            for (int j = tid; j <= N; j += DIAG_BLOCK) D.dg_E[j] += (double)E[j];
+        if (tid == 0) {
+            if (phase) D.dg_n[0] += 1;
+            if (sample) D.dg_n[1] += 1;
+        }
+    }
+    __syncthreads();
+    unsigned long long* h[DG_ARRAYS];
+#pragma unroll
+    for (int a = 0; a < DG_ARRAYS; ++a) h[a] = s_dg + (size_t)__popc(A.mask & ((1u << a) - 1u)) * N1;
+    const bool mD = A.mask & (1u << DG_D), mU = A.mask & (1u << DG_U), mV = A.mask & (1u << DG_V),
+               mW = A.mask & (1u << DG_W), mK = A.mask & (1u << DG_K), mF = A.mask & (1u << DG_F),
+               mFa = A.mask & (1u << DG_FA);
+    const Consts<T>& K = consts_of<T>(D);
+    const T thr = (T)A.thr, inv_bin = (T)A.inv_bin, top = (T)(D.n_pts - 1), binsT = (T)A.bins;
+    const int ciz = 1 + D.n_exc;  // ionization column of the cumulative electron table
+    const Row4* Te = reinterpret_cast<const Row4*>(D.Te);
+    const long long n = ctl->count[d][0];
+    const Lay L = ctl->lay[d][0][buf];
+    const long long chunks = chunks_of(L, n, CHUNK);
+    const int32_t* __restrict__ cc = D.c[buf][0];
+    const R* __restrict__ P = reinterpret_cast<const R*>(D.p[buf][0]);
+    for (long long k = (long long)blockIdx.x * DIAG_NW + warp; k < chunks; k += (long long)gridDim.x * DIAG_NW) {
+        const ChunkDesc cd = chunk_desc(L, n, D.start[0], k, CHUNK);
+        for (int r = 0; r < RPC; ++r) {
+            const int i = 32 * r + lane;
+            int c = -1;
+            T f = 0, vx = 0, vy = 0, vz = 0;
+            if (i < cd.cnt) {
+                c = cc[cd.src + i];
+                const R q = P[cd.src + i];
+                f = q.x;
+                vx = q.y;
+                vy = q.z;
+                vz = q.w;
+                if (!((unsigned)c < (unsigned)N)) c = -1;
+            }
+            unsigned long long F = 0, uA = 0, uB = 0, vA = 0, vB = 0, wA = 0, wB = 0, kA = 0, kB = 0;
+            bool fast = false;
+            int bin = 0;
+            if (c >= 0) {
+                const T E0 = E[c], E1 = E[c + 1];
+                const T ef = fma_(f, sub_(E1, E0), E0);
+                vz = fma_(K.K[0], ef, vz);  // v_n
+                const T e2 = fma_(vx, vx, fma_(vy, vy, mul_(vz, vz)));
+                T eq = mul_(e2, K.kappa_E);
+                if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
+                F = cic_F(f);
+                fast = eq > thr;
+                if (mU) split_rint<T>(eq, f, uA, uB);
+                if (mV) split_rint<T>(mul_(vz, (T)64), f, vA, vB);
+                if (mW) split_rint<T>(mul_(mul_(eq, vz), (T)0x1p-16), f, wA, wB);
+                if (mK) {
+                    const T xi = mul_(e2, K.kappa_e);
+                    T Cz, Cy;
+                    if (!(xi < top)) {
+                        const Row4 a = Te[D.n_pts - 1];
+                        Cz = col4<Row4, T>(a, ciz);
+                        Cy = col4<Row4, T>(a, ciz - 1);
+                    } else {
+                        const int ii = (int)xi;
+                        const T fr = sub_(xi, (T)ii);
+                        const Row4 a = Te[ii], b = Te[ii + 1];
+                        const T az = col4<Row4, T>(a, ciz), ay = col4<Row4, T>(a, ciz - 1);
+                        Cz = fma_(fr, sub_(col4<Row4, T>(b, ciz), az), az);
+                        Cy = fma_(fr, sub_(col4<Row4, T>(b, ciz - 1), ay), ay);
+                    }
+                    split_rint<T>(mul_(sub_(Cz, Cy), (T)0x1p72), f, kA, kB);
+                }
+                if (sample) {
+                    const T xb = mul_(eq, inv_bin);
+                    bin = xb < binsT ? (int)xb : A.bins - 1;
+                }
+            }
+            const unsigned peers = __match_any_sync(FULL, c);
+            const bool leader = lane == __ffs(peers) - 1;
+            const bool lanewise = __popc(__ballot_sync(FULL, leader)) > HIST_GROUPS;
+            const unsigned long long dA = c >= 0 ? (1ull << 32) - F : 0ull, dB = c >= 0 ? F : 0ull;
+            if (mD) warp_add_pair(h[DG_D], c, dA, dB, peers, leader, lanewise);
+            if (mU) warp_add_pair(h[DG_U], c, uA, uB, peers, leader, lanewise);
+            if (mV) warp_add_pair(h[DG_V], c, vA, vB, peers, leader, lanewise);
+            if (mW) warp_add_pair(h[DG_W], c, wA, wB, peers, leader, lanewise);
+            if (mK) warp_add_pair(h[DG_K], c, kA, kB, peers, leader, lanewise);
+            if (mF) warp_add_pair(h[DG_F], c, fast ? dA : 0ull, fast ? dB : 0ull, peers, leader, lanewise);
+            if (mFa) warp_add_pair(h[DG_FA], c, fast ? dA : 0ull, fast ? dB : 0ull, peers, leader, lanewise);
+            if (sample && c >= 0) atomicAdd(&s_eedf[bin], 1u);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < DG_ARRAYS; ++a)
+        if (A.mask & (1u << a)) {
+            unsigned long long* g = D.dg + (size_t)a * N1;
+            for (int j = tid; j < N1; j += DIAG_BLOCK)
+                if (h[a][j]) atomicAdd(&g[j], h[a][j]);
+        }
+    for (int j = tid; j < nb; j += DIAG_BLOCK)
+        if (s_eedf[j]) atomicAdd(&D.dg_eedf[j], (unsigned long long)s_eedf[j]);
+}
+
 // Stable counting sort by cell. A sort tile is SORT_NW warps of SORT_R rows of 32 slots: warp w of
 // tile t walks the store's chunks t SORT_NW CPW + w CPW .. + CPW - 1 (CPW = SORT_R 32 / CHUNK) in
 // slot order.
@@ -2153,6 +2329,25 @@ cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, lon
                                  int buf, cudaStream_t st) {
     k_finish_upload<<<1, 1, 0, st>>>(discs, ctl, d, sp, n, bad, buf);
     return cudaGetLastError();
+}
+
+// Dynamic shared memory of a k_diag launch: its node arrays and, for a sample, the EEDF (bins > 0).
+size_t diag_smem(int max_N, unsigned mask, int bins) {
+    return (size_t)__builtin_popcount(mask) * 8 * ((size_t)max_N + 1) + 4 * (size_t)bins;
+}
+
+cudaError_t launch_diag(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int buf, const DiagArgs& A,
+                        int max_N, int grid_x, cudaStream_t st) {
+    const size_t smem = diag_smem(max_N, A.mask, (A.mode & DIAG_SAMPLE) ? A.bins : 0);
+    const dim3 g(grid_x, n_disc);
+    if (fp64) {
+        cudaError_t e = smem_attr(k_diag<double>, smem);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_diag<double>, g, dim3(DIAG_BLOCK), smem, st, discs, ctl, buf, A);
+    }
+    cudaError_t e = smem_attr(k_diag<float>, smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_diag<float>, g, dim3(DIAG_BLOCK), smem, st, discs, ctl, buf, A);
 }
 
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, int buf, cudaStream_t st) {

@@ -39,6 +39,9 @@ cudaError_t launch_load_profile(int fp64, const Disc* discs, int n_disc, Ctl* ct
 size_t warm_desc_bytes(int fp64);
 void warm_desc_fill(int fp64, void* out, const void* cdf_e, const void* cdf_i, const void* eps, int P, double scale,
                     double K23);
+cudaError_t launch_diag(int fp64, const Disc* discs, int n_disc, const Ctl* ctl, int buf, const DiagArgs& A,
+                        int max_N, int grid_x, cudaStream_t st);
+size_t diag_smem(int max_N, unsigned mask, int bins);  // bins: 0 unless the launch samples the EEDF
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, int buf, cudaStream_t st);
 cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, long long n, const unsigned* bad,
                                  int buf, cudaStream_t st);

@@ -262,6 +262,36 @@ class Simulation:
             self._ck(self.L.pic_current_amplitude(self.h, d, first, n, _ptr(out), C.byref(done)))
         return out
 
+    def set_diagnostics(self, period_steps: int = 0, phase_step: int = 0, sample_every: int = 0,
+                        eedf_bins: int = 200, eedf_de_eV: float = 0.5, fast_eV: float = 0.0, off: bool = False):
+        """Kinetic diagnostics of the electrons (pic_set_diagnostics): rf-phase snapshots at the
+        steps n with n % period_steps == phase_step, EEDF and fast-electron samples every
+        sample_every steps. off=True switches them off."""
+        if off:
+            self._ck(self.L.pic_set_diagnostics(self.h, None))
+            self._eedf_bins = 0
+            return
+        cfg = NV.PicDiagConfig(period_steps, phase_step, sample_every, eedf_bins, eedf_de_eV, fast_eV)
+        self._ck(self.L.pic_set_diagnostics(self.h, C.byref(cfg)))
+        self._eedf_bins = eedf_bins
+
+    def reset_diagnostics(self):
+        self._ck(self.L.pic_reset_diagnostics(self.h))
+
+    def diagnostics(self, d: int = 0) -> dict:
+        """Read-out of pic_diagnostics: node profiles (N+1) E, n_e, mean_eps, gamma_e, q_e, heating,
+        ion_rate, n_fast (snapshot averages), n_fast_avg (sample average), the EEDF f0(U)/n_e at
+        the bin centres, and the numbers of snapshots and samples."""
+        N1 = self.N[d] + 1
+        keys = ("E", "n_e", "mean_eps", "gamma_e", "q_e", "heating", "ion_rate", "n_fast", "n_fast_avg")
+        out = {k: np.zeros(N1) for k in keys}
+        out["eedf"] = np.zeros(max(getattr(self, "_eedf_bins", 0), 1))
+        sn, sm = C.c_int64(), C.c_int64()
+        self._ck(self.L.pic_diagnostics(self.h, d, *[_ptr(out[k]) for k in keys], _ptr(out["eedf"]),
+                                        C.byref(sn), C.byref(sm)))
+        out["snapshots"], out["samples"] = sn.value, sm.value
+        return out
+
     def sweep_timing(self, enable: bool = True):
         ms = C.c_double()
         n = C.c_int64()

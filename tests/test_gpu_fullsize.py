@@ -5,7 +5,7 @@ The 1e6 + 1e6 particle Ar-like discharge (512 cells, 2000 steps per rf period) a
 steps (pic_step: sweep, post-sweep grid, the sort every 16 steps) at the benchmark's launch
 shapes. These stores span several slices of sweep chunks, so the output offsets that the
 post-sweep grid derives from the slice sums of earlier slices are exercised; between sorts the
-sweep reads aged stores through their segment tables. Each step both sides start from the same
+sweep reads aged stores chunk by chunk through their region layouts. Each step both sides start from the same
 state and the same FP32 node field (the oracle's, fed to the library after its own solve, so that
 a last-bit difference of the two FP64 Poisson solvers cannot make the paths diverge), and the
 result must be identical: event counters, particle order, cells and every FP32 value bit for bit,
