@@ -417,6 +417,52 @@ def run_cpu_baseline(args):
             "sample": f"{d.name}: full load ({n0} particles, {t_load:.1f} s), {n_steps} FP64 steps, {dt:.1f} s"}
 
 
+def _oracle_copy(name, sort_every, n_steps, did, barrier, q):
+    """One independent copy of the workload in the oracle (its own discharge id, so its own random
+    streams), timed after every copy has loaded."""
+    from oracle import oracle as O
+    d = workload(name).scaled(discharge_id=did)
+    o = O.Oracle(gas_for(d), d, "f64", sort_every=sort_every)
+    barrier.wait(timeout=600)
+    t0 = time.monotonic()
+    ps = 0
+    for _ in range(n_steps):
+        ps += o.count(0) + o.count(1)
+        o.step(1)
+    q.put((ps, t0, time.monotonic()))
+
+
+def run_cpu_baseline_all_cores(args):
+    """The FP64 oracle as it stands on every host core: one independent copy of the workload per
+    core, in processes started by spawn; throughput = all copies' particle-steps over the wall time
+    from the first copy's start to the last copy's end."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(cores), ctx.Queue()
+    n_steps = max(4, args.cpu_steps)
+    procs = [ctx.Process(target=_oracle_copy, args=(args.workload, args.sort_every, n_steps, k + 1, barrier, q))
+             for k in range(cores)]
+    for p in procs:
+        p.start()
+    try:
+        res = [q.get(timeout=900) for _ in procs]
+    except Exception as e:  # a copy failed to start or to finish: no all-core figure
+        for p in procs:
+            p.kill()
+        return {"unavailable": f"all-core oracle run failed: {type(e).__name__}"}
+    for p in procs:
+        p.join()
+    ps = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    d = workload(args.workload)
+    return {"value": ps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent copies of {d.name} (one per core), {n_steps} FP64 steps each, "
+                      f"{wall:.1f} s wall"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,6 +529,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and not args.quick:
             res["cpu_baseline"] = run_cpu_baseline(args)
+            res["cpu_baseline_all_cores"] = run_cpu_baseline_all_cores(args)
         print(json.dumps(res))
     if world > 1:
         import torch.distributed as dist

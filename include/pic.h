@@ -324,6 +324,11 @@ pic_status pic_sweep_timing(pic_ctx* ctx, int32_t enable, double* total_ms, int6
 
 /* ---- self-checks of the device building blocks (host buffers) ---------- */
 /* Philox4x32-10 (Salmon et al., SC'11) on n counters (4 words each).      */
+/* The bounded device-side wait of the sweep's bulk-copy staging, on its own: one mbarrier that
+ * expects one arrival, polled at most `tries` times (1 .. 2^20). arrive = 0: nothing arrives, the
+ * wait gives up and the call returns PIC_ERR_TIMEOUT with the device context intact (nothing is
+ * left in flight); arrive = 1: PIC_OK. Synchronous, default stream.                        */
+pic_status pic_debug_wait(int32_t arrive, int32_t tries);
 pic_status pic_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
 /* Own log, sin(pi y), cos(pi y), Box-Muller and isotropic direction as used
  * by the kernels, on n inputs.                                            */

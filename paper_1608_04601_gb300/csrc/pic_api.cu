@@ -1314,6 +1314,19 @@ extern "C" pic_status pic_debug_philox(int64_t n, const uint32_t* ctr, const uin
     return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
 
+extern "C" pic_status pic_debug_wait(int32_t arrive, int32_t tries) {
+    if (tries < 1 || tries > (1 << 20)) return PIC_ERR_ARG;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return PIC_ERR_CUDA;
+    int h = -1;
+    cudaError_t e = cudaMemset(d, 0xFF, sizeof(int));
+    if (e == cudaSuccess) e = launch_debug_wait(arrive ? 1 : 0, tries, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    return h == 0 ? PIC_OK : h == ERR_TIMEOUT ? PIC_ERR_TIMEOUT : PIC_ERR_CUDA;
+}
+
 extern "C" pic_status pic_debug_math(int64_t n, const float* x, const float* y, float* lg, float* sn, float* cs) {
     if (n < 0 || (n && (!x || !y || !lg || !sn || !cs))) return PIC_ERR_ARG;
     if (!n) return PIC_OK;

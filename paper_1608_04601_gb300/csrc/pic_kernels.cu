@@ -495,12 +495,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                  "l"(src), "r"(bytes), "r"(smem_u32(mb))
                  : "memory");
 }
-// Waits for phase `parity` of the barrier to complete, at most MBAR_TRIES polls (each poll may block
+// Waits for phase `parity` of the barrier to complete, at most `tries` polls (each poll may block
 // for a hardware-defined time); false if it gave up.
 constexpr int MBAR_TRIES = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parity, int tries = MBAR_TRIES) {
     const unsigned a = smem_u32(mb);
-    for (int it = 0; it < MBAR_TRIES; ++it) {
+    for (int it = 0; it < tries; ++it) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -2105,6 +2105,20 @@ __global__ void k_debug_math(long long n, const float* __restrict__ x, const flo
 
 namespace pic {
 
+// Bounded-wait check: one mbarrier expecting a single arrival. With arrive = 0 nothing arrives, so
+// the wait gives up after `tries` polls and the kernel reports ERR_TIMEOUT in *out; nothing is in
+// flight when it returns. With arrive = 1 the thread arrives first and the wait succeeds.
+__global__ void k_debug_wait(int arrive, int tries, int* out) {
+    __shared__ __align__(8) unsigned long long mb;
+    if (threadIdx.x == 0) mbar_init(&mb);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mb)) : "memory");
+        *out = mbar_wait(&mb, 0u, tries) ? 0 : ERR_TIMEOUT;
+    }
+}
+
 // Raises a kernel's dynamic shared-memory limit once per (kernel, size). Kernels
 // are told apart by their address (instantiations can share a type).
 template <typename K>
@@ -2352,6 +2366,11 @@ cudaError_t launch_diag(int fp64, const Disc* discs, int n_disc, const Ctl* ctl,
 
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, int buf, cudaStream_t st) {
     return launch_pdl(k_set_dense, dim3(1), dim3(128), 0, st, discs, n_disc, ctl, buf);
+}
+
+cudaError_t launch_debug_wait(int arrive, int tries, int* out, cudaStream_t st) {
+    k_debug_wait<<<1, 32, 0, st>>>(arrive, tries, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,

@@ -45,6 +45,7 @@ size_t diag_smem(int max_N, unsigned mask, int bins);  // bins: 0 unless the lau
 cudaError_t launch_set_dense(const Disc* discs, int n_disc, Ctl* ctl, int buf, cudaStream_t st);
 cudaError_t launch_finish_upload(const Disc* discs, Ctl* ctl, int d, int sp, long long n, const unsigned* bad,
                                  int buf, cudaStream_t st);
+cudaError_t launch_debug_wait(int arrive, int tries, int* out, cudaStream_t st);
 cudaError_t launch_debug_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_debug_math(long long n, const float* x, const float* y, float* lg, float* sn, float* cs,

@@ -299,6 +299,11 @@ class Simulation:
         return ms.value, n.value
 
 
+def debug_wait(arrive: bool, tries: int) -> int:
+    """Status of pic_debug_wait (PIC_OK or PIC_ERR_TIMEOUT), returned rather than raised."""
+    return int(NV.lib().pic_debug_wait(1 if arrive else 0, int(tries)))
+
+
 def debug_philox(ctr: np.ndarray, key) -> np.ndarray:
     ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
     k = np.ascontiguousarray(key, np.uint32)

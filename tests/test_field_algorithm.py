@@ -9,7 +9,13 @@ S_{j+1} = sum_{i<=j} R_i is then (j + 1) R_j - M_j exactly, and FP64 is used onc
 order (fused multiply-adds where the kernel has them). This test restates those steps in Python
 (arbitrary-precision integers; fused multiply-adds rounded once through exact fractions) and checks
 the identity and the resulting potential and field against the oracle within the GPU parity
-tolerance (1e-12 of the largest value)."""
+tolerance (1e-12 of the largest value).
+
+This checks the restated arithmetic, not the kernel itself. The kernel is tied to the same oracle
+by tests/test_gpu_parity.py::test_poisson_matches_oracle, which uploads identical deposits, runs
+the post-sweep kernel's solve and compares its potential and field with the oracle's for N = 1 to
+4096, and by the full-size step tests (tests/test_gpu_fullsize.py), which compare the FP64 field of
+every step."""
 from fractions import Fraction
 
 import numpy as np
