@@ -104,7 +104,7 @@ typedef struct {
     int32_t precision;       /* PIC_FP32 (default) or PIC_FP64                */
     int32_t sort_every;      /* 0: never sort; K > 0: stable sort by cell    */
                              /* after every step n with (n+1) % K == 0       */
-    int32_t block;           /* sweep threads per CTA: 128, 256 (default)    */
+    int32_t block;           /* sweep threads per CTA: 128, 256 (default), 512 (PPT 2 or 4) */
     int32_t ppt;             /* sweep particles per thread: 2, 4 (default), 8 */
     int32_t ctas_per_sm;     /* persistent sweep CTAs per SM (0: occupancy)  */
     int32_t use_graph;       /* 1: replay pic_step in CUDA graphs of one rf  */

@@ -239,7 +239,8 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
     if (opt) ctx->opt = *opt;
     else pic_default_options(&ctx->opt);
     pic_options& o = ctx->opt;
-    if (o.block != 128 && o.block != 256) o.block = 256;
+    if (o.block != 128 && o.block != 256 && o.block != 512) o.block = 256;
+    if (o.block == 512 && o.ppt == 8) o.ppt = 4;
     if (o.ppt != 2 && o.ppt != 4 && o.ppt != 8) o.ppt = 4;
     if (o.precision != PIC_FP32 && o.precision != PIC_FP64) {
         pic_destroy(ctx);

@@ -136,50 +136,74 @@ __device__ __forceinline__ unsigned long long cic_F(double f) {
     return __double2ull_rn(__dmul_rn(f, TWO32_D));  // may round to 2^32
 }
 
-// Warp-aggregated shared-memory histogram update. key < 0: nothing. Lanes with
-// equal keys are grouped (match_any); each group's sums are reduced in 32-bit
-// parts (redux) and its first lane applies them:
-//   deposit (PAIR = false): v = 2^40 + F  ->  node key += count 2^32 - sum F, node key+1 += sum F
-//   moment  (PAIR = true):  v = lo + hi 2^32 (lo, hi < 2^26) -> node key += sum lo, key+1 += sum hi
-// The group reductions of a warp run one after another (one per distinct member mask), so their
-// cost grows with the number of groups: a warp with more than HIST_GROUPS distinct keys adds lane by
-// lane instead (measured on C2: the sweep of an unsorted store 140 -> 55 us; two groups is the best
-// threshold within a sort period). Integer adds: the same sums either way.
+// Warp-aggregated histogram updates (warp_dep, warp_energy below; k_diag): lanes with equal keys are
+// grouped (match_any) and each group's sums reduced (redux) and added by its first lane. The group
+// reductions of a warp run one after another (one per distinct member mask), so their cost grows
+// with the number of groups: a warp with more than HIST_GROUPS distinct keys adds lane by lane
+// instead (measured on C2 with the earlier 64-bit adds: the sweep of an unsorted store 140 -> 55
+// us; two groups was the best threshold within a sort period). Integer adds: the same sums either way.
 constexpr int HIST_GROUPS = 2;
-template <bool PAIR>
-__device__ __forceinline__ void warp_hist(unsigned long long* h, int key, unsigned long long v, int lane) {
+
+// The sweep's shared-memory histograms hold exact sums in 32-bit pieces, added with atomics whose
+// result is not read (no return trip, no carry logic):
+//   deposit, per cell c: particles n_c, and the sum of F = rn(f 2^32) as low and high 16-bit parts;
+//     node j then receives 2^32 n_j - F_j + F_{j-1} (the charge split (2^32 - F, F) of every
+//     particle), formed in 64 bits when the CTA flushes;
+//   energy moment, per node: the sum of its 26-bit values as low 13-bit and high parts.
+// A piece sum stays below 2^32 while the CTA has added fewer than 2^15 particles (plus their
+// newborns) since its last flush: the sweep flushes at least that often.
+struct DepHist {
+    unsigned* n;
+    unsigned* lo;
+    unsigned* hi;
+};
+__device__ __forceinline__ void dep_add(const DepHist& h, int c, unsigned long long F) {
+    atomicAdd(&h.n[c], 1u);
+    atomicAdd(&h.lo[c], (unsigned)(F & 0xFFFFu));
+    atomicAdd(&h.hi[c], (unsigned)(F >> 16));
+}
+// Warp-aggregated deposit of one particle per lane (key = cell, < 0: none; F as above): lanes of
+// equal keys are reduced (match_any, redux) and their first lane adds the group's sums, unless the
+// warp's keys form more than HIST_GROUPS groups (then lane by lane).
+__device__ __forceinline__ void warp_dep(const DepHist& h, int key, unsigned long long F, int lane) {
+    const unsigned peers = __match_any_sync(FULL, key);
+    const bool leader = lane == __ffs(peers) - 1;
+    if (__popc(__ballot_sync(FULL, leader)) > HIST_GROUPS) {
+        if (key >= 0) dep_add(h, key, F);
+        return;
+    }
+    const unsigned lo = __reduce_add_sync(peers, (unsigned)(F & 0xFFFFu));
+    const unsigned hi = __reduce_add_sync(peers, (unsigned)(F >> 16));
+    if (leader && key >= 0) {
+        atomicAdd(&h.n[key], (unsigned)__popc(peers));
+        if (lo) atomicAdd(&h.lo[key], lo);
+        if (hi) atomicAdd(&h.hi[key], hi);
+    }
+}
+// Warp-aggregated energy moment: a (< 2^26) to node key, b (< 2^26) to node key + 1.
+__device__ __forceinline__ void warp_energy(unsigned* qlo, unsigned* qhi, int key, unsigned a, unsigned b, int lane) {
     const unsigned peers = __match_any_sync(FULL, key);
     const bool leader = lane == __ffs(peers) - 1;
     if (__popc(__ballot_sync(FULL, leader)) > HIST_GROUPS) {
         if (key >= 0) {
-            if (PAIR) {
-                const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
-                if (lo) sadd64(&h[key], lo);
-                if (hi) sadd64(&h[key + 1], hi);
-            } else {
-                const unsigned long long F = v & ((1ull << 40) - 1);  // <= 2^32
-                sadd64(&h[key], (1ull << 32) - F);
-                if (F) sadd64(&h[key + 1], F);
+            if (a) {
+                atomicAdd(&qlo[key], a & 0x1FFFu);
+                atomicAdd(&qhi[key], a >> 13);
+            }
+            if (b) {
+                atomicAdd(&qlo[key + 1], b & 0x1FFFu);
+                atomicAdd(&qhi[key + 1], b >> 13);
             }
         }
         return;
     }
-    if (PAIR) {
-        const unsigned lo = __reduce_add_sync(peers, (unsigned)v);
-        const unsigned hi = __reduce_add_sync(peers, (unsigned)(v >> 32));
-        if (leader && key >= 0) {
-            if (lo) sadd64(&h[key], lo);
-            if (hi) sadd64(&h[key + 1], hi);
-        }
-    } else {
-        const unsigned long long F = v & ((1ull << 40) - 1);  // <= 2^32
-        const unsigned fh = __reduce_add_sync(peers, (unsigned)(F >> 16));
-        const unsigned fl = __reduce_add_sync(peers, (unsigned)(F & 0xFFFFu));
-        if (leader && key >= 0) {
-            const unsigned long long sF = ((unsigned long long)fh << 16) + fl;
-            sadd64(&h[key], ((unsigned long long)__popc(peers) << 32) - sF);
-            if (sF) sadd64(&h[key + 1], sF);
-        }
+    const unsigned al = __reduce_add_sync(peers, a & 0x1FFFu), ah = __reduce_add_sync(peers, a >> 13);
+    const unsigned bl = __reduce_add_sync(peers, b & 0x1FFFu), bh = __reduce_add_sync(peers, b >> 13);
+    if (leader && key >= 0) {
+        if (al) atomicAdd(&qlo[key], al);
+        if (ah) atomicAdd(&qhi[key], ah);
+        if (bl) atomicAdd(&qlo[key + 1], bl);
+        if (bh) atomicAdd(&qhi[key + 1], bh);
     }
 }
 
@@ -214,26 +238,25 @@ __device__ __forceinline__ void load_rec<double>(const void* p, unsigned i, doub
     f = a.x; vx = a.y; vy = b.x; vz = b.y;
 }
 
-// One collision candidate, queued by its warp in shared memory: the owner writes
-// the particle's index in its chunk, the gathered field and v_n; the lane that
-// processes the collision (reading cell and offset from the chunk's staged
-// records) writes back the new velocity and flags the newborns it left after
-// their first drift, which it stores at the candidate's rank in the chunk's
-// newborn regions (the warp then compacts them into parent-slot order).
+// The collision candidates of a chunk are queued by their warp in shared memory as their indices
+// in the chunk; the lane that processes one reads the particle from the staged records, collides
+// it, writes the new velocity back into the staged record and flags the newborns it left after
+// their first drift, which it stores at the candidate's rank in the chunk's newborn regions (the
+// warp then compacts them into parent-slot order).
+// A collision candidate of a chunk: its velocity v_n and gathered field on entry; the velocity after
+// the collision on return; newborns flagged in `out` (bit 1: same species, bit 2: other species).
 template <typename T>
-struct QEnt {
-    uint32_t idx;     // index in the chunk
-    uint32_t out;     // bit 1: same-species newborn, bit 2: other-species newborn
+struct Cand {
     T ef;
-    T vx, vy, vz;     // in: v_n; out: velocity after the collision
+    T vx, vy, vz;
 };
 
 // The collision of a queued candidate (null-collision method: process
 // selection against the cumulative rate tables, then the kinematics).
 template <typename T>
-__device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, int qc, T qf, uint32_t slot, uint32_t ridx,
-                                     long long step, unsigned long long seed, unsigned long long* sH, unsigned* sC,
-                                     int& err) {
+__device__ __forceinline__ uint32_t collide(const Seg<T>& S, Cand<T>& q, int qc, T qf, uint32_t slot, uint32_t ridx,
+                                         long long step, unsigned long long seed, const DepHist& sH, unsigned* sC,
+                                         int& err) {
     using Row4 = typename T4<T>::type;
     using Row2 = typename T4<T>::two;
     const Consts<T>& K = S.k;
@@ -319,7 +342,7 @@ __device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, int qc, T q
             int side = drift(N, K.dtdx, qc, qf, cvz, cn, fn, err);
             if (side < 0) {
                 store_rec<T>(S.sc, S.sp_, ridx, Part<T>{cn, fn, cvx, cvy, cvz});
-                shist_add(sH, cn, cic_F(fn));
+                dep_add(sH, cn, cic_F(fn));
                 out |= 2u;
             } else {
                 atomicAdd(&sC[CNT_ABS + side], 1u);
@@ -376,7 +399,7 @@ __device__ __forceinline__ void collide(const Seg<T>& S, QEnt<T>& q, int qc, T q
     q.vx = vx;
     q.vy = vy;
     q.vz = vz;
-    q.out = out;
+    return out;
 }
 
 // Secondary electron of an ion absorbed at electrode `side` (added option).
@@ -512,12 +535,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parit
     return false;
 }
 
-// Dynamic shared memory of the sweep: histogram and energy moment (u64, N+1 each), the node field
-// (T, N+1); per warp two staging buffers of one chunk (records, then cells) and its candidate
+// Dynamic shared memory of the sweep: the node field (T, N+1), the deposit histogram (u32 n, lo, hi
+// per cell) and the energy moment (u32 lo, hi per node); per warp two staging buffers of one chunk (records, then cells) and its candidate
 // queue; per store the layout snapshot and the tile prefix.
 template <typename T>
+__host__ __device__ constexpr size_t sweep_hist_offset(int max_N) {  // after the node field
+    return (((size_t)(max_N + 1) * sizeof(T) + 15) / 16) * 16;
+}
+template <typename T>
 __host__ __device__ constexpr size_t sweep_stage_offset(int max_N) {
-    return (((size_t)(max_N + 1) * (16 + sizeof(T)) + 127) / 128) * 128;
+    return ((sweep_hist_offset<T>(max_N) + 4 * (3 * (size_t)max_N + 2 * ((size_t)max_N + 1)) + 127) / 128) * 128;
 }
 template <typename T, int PPT>
 __host__ __device__ constexpr size_t sweep_stage_bytes() {  // one buffer of one warp
@@ -529,7 +556,7 @@ __host__ __device__ constexpr size_t sweep_queue_offset(int max_N) {
 }
 template <typename T, int BLOCK, int PPT>
 __host__ __device__ constexpr size_t sweep_store_offset(int max_N) {
-    return ((sweep_queue_offset<T, BLOCK, PPT>(max_N) + sizeof(QEnt<T>) * (size_t)BLOCK * PPT + 15) / 16) * 16;
+    return ((sweep_queue_offset<T, BLOCK, PPT>(max_N) + (size_t)BLOCK * PPT + 15) / 16) * 16;
 }
 struct StoreSnap {  // layout of one input store, for the prefetches of any tile
     int K, chunks;
@@ -542,12 +569,15 @@ __host__ __device__ constexpr size_t sweep_smem(int max_N, int n_disc) {
 }
 
 // Resident threads per SM the sweep is compiled for (the register budget is 65536 / that): the
-// FP32 chunk state (7 PPT registers per lane) fits 64 registers at PPT <= 2 and 80 at PPT = 4.
+// FP32 chunk state fits 64 registers at PPT <= 2 and 80 at PPT = 4; 512-thread CTAs at PPT = 4 are
+// held to 64 registers so that two of them fit an SM.
+template <typename T, int BLOCK, int PPT>
+__host__ __device__ constexpr int sweep_threads_per_sm() {
+    return sizeof(T) == 4 ? (PPT <= 2 ? 1024 : PPT == 4 ? (BLOCK >= 512 ? 1024 : 768) : 512) : 256;
+}
 template <typename T, int BLOCK, int PPT>
 __host__ __device__ constexpr int sweep_min_blocks() {
-    return (sizeof(T) == 4 ? (PPT <= 2 ? 1024 : PPT == 4 ? 768 : 512) : 256) / BLOCK > 0
-               ? (sizeof(T) == 4 ? (PPT <= 2 ? 1024 : PPT == 4 ? 768 : 512) : 256) / BLOCK
-               : 1;
+    return sweep_threads_per_sm<T, BLOCK, PPT>() / BLOCK > 0 ? sweep_threads_per_sm<T, BLOCK, PPT>() / BLOCK : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -571,9 +601,12 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     constexpr int CHUNK = 32 * PPT;
     constexpr unsigned REC_BYTES = CHUNK * sizeof(R), CELL_BYTES = CHUNK * 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem_raw);
-    unsigned long long* s_Q = s_hist + (max_N + 1);
-    T* s_E = reinterpret_cast<T*>(s_Q + (max_N + 1));
+    T* s_E = reinterpret_cast<T*>(smem_raw);
+    unsigned* s_h32 = reinterpret_cast<unsigned*>(smem_raw + sweep_hist_offset<T>(max_N));
+    const DepHist s_dep{s_h32, s_h32 + max_N, s_h32 + 2 * max_N};
+    unsigned* s_qlo = s_h32 + 3 * max_N;
+    unsigned* s_qhi = s_qlo + (max_N + 1);
+    const int h32_words = 3 * max_N + 2 * (max_N + 1);
     StoreSnap* s_store = reinterpret_cast<StoreSnap*>(smem_raw + sweep_store_offset<T, BLOCK, PPT>(max_N));
     long long* s_segstart = reinterpret_cast<long long*>(s_store + 2 * n_disc);
 
@@ -589,7 +622,8 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned char* stage = smem_raw + sweep_stage_offset<T>(max_N) + (size_t)warp * 2 * sweep_stage_bytes<T, PPT>();
-    QEnt<T>* Q = reinterpret_cast<QEnt<T>*>(smem_raw + sweep_queue_offset<T, BLOCK, PPT>(max_N)) + warp * CHUNK;
+    // per warp: the chunk indices of its candidates, in slot order (CHUNK <= 256)
+    uint8_t* Q = reinterpret_cast<uint8_t*>(smem_raw + sweep_queue_offset<T, BLOCK, PPT>(max_N)) + warp * CHUNK;
     if (lane == 0) {
         mbar_init(&s_mbar[warp][0]);
         mbar_init(&s_mbar[warp][1]);
@@ -624,17 +658,26 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     int cur_seg = -1, cur_d = -1;
     int err = 0;
 
+    // Adds the CTA's histograms and counters of the current store to the global ones and clears them.
     auto flush = [&]() {
         __syncthreads();
-        for (int j = tid; j <= S.N; j += BLOCK) {
-            const unsigned long long h = s_hist[j];
+        const int N = S.N;
+        for (int j = tid; j <= N; j += BLOCK) {
+            unsigned long long h = 0;
+            if (j < N)
+                h = ((unsigned long long)s_dep.n[j] << 32) -
+                    ((unsigned long long)s_dep.lo[j] + ((unsigned long long)s_dep.hi[j] << 16));
+            if (j > 0) h += (unsigned long long)s_dep.lo[j - 1] + ((unsigned long long)s_dep.hi[j - 1] << 16);
             if (h) atomicAdd(&S.Dg[j], h);
             if (S.sp == 0) {
-                const unsigned long long q = s_Q[j];
+                const unsigned long long q = (unsigned long long)s_qlo[j] + ((unsigned long long)s_qhi[j] << 13);
                 if (q) atomicAdd(&S.Qg[j], q);
             }
         }
         if (tid < NCNT && s_cnt[tid]) atomicAdd(&S.cnt[tid], (unsigned long long)s_cnt[tid]);
+        __syncthreads();
+        for (int j = tid; j < h32_words; j += BLOCK) s_h32[j] = 0;
+        if (tid < NCNT) s_cnt[tid] = 0;
         __syncthreads();
     };
 
@@ -671,7 +714,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             pf[3] = 1;
             pf[4] = sg;
             unsigned char* buf = stage + (size_t)b * sweep_stage_bytes<T, PPT>();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads and writes of the buffer
             mbar_expect(&s_mbar[warp][b], REC_BYTES + CELL_BYTES);
             bulk_g2s(buf, reinterpret_cast<const R*>(discs[d].p[in_buf][sp]) + src, REC_BYTES, &s_mbar[warp][b]);
             bulk_g2s(buf + REC_BYTES, discs[d].c[in_buf][sp] + src, CELL_BYTES, &s_mbar[warp][b]);
@@ -687,10 +730,12 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
     prefetch(0, blockIdx.x);  // the chunk of the CTA's first tile, into buffer 0
     __syncwarp();
 
-    // One warp's chunk of the store of species SP: push, collide, write (see above). Phase C reads
-    // each particle again from the staging buffer and repeats the gather and the first half kick
-    // (the same operations, so the same values) instead of keeping them in registers.
-    auto chunk = [&](unsigned cs, int base, int cnt, const R* srec, const int32_t* scell, auto spc) {
+    // One warp's chunk of the store of species SP: push, collide, write (see above). Phases B and C
+    // read each particle again from the staging buffer and repeat the gather and the first half kick
+    // (the same operations, so the same values) instead of keeping them in registers or in the
+    // queue; a collision writes the velocity after it back into the staged record, and phase C then
+    // takes that velocity as v_n.
+    auto chunk = [&](unsigned cs, int base, int cnt, R* srec, const int32_t* scell, auto spc) {
         constexpr int SP = decltype(spc)::value;
         const unsigned obase = cs * CHUNK;
         unsigned offA = obase, offB = obase, offS = obase;  // output cursors of the chunk's regions
@@ -716,21 +761,26 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         };
         if (cnt > 0) {
             // candidate words: slots 4q..4q+3 take the four words of one Philox call (call 4,
-            // counter word 0 = q); lane l computes the calls q0 + l + 32 m, q0 = base / 4, and the
-            // particle of slot s takes word s % 4 of call s / 4 by shuffle
+            // counter word 0 = q); lane l computes the calls q0 + l + 32 m, q0 = base / 4, compares
+            // their words with the threshold and keeps the results as bits 4 m + w (word w); the
+            // particle of slot s takes bit s % 4 of call s / 4 by one shuffle
             constexpr int NG = (CHUNK / 4 + 1 + 31) / 32;
             const uint32_t did = S.did, thr = S.thr;
             const unsigned q0 = (unsigned)base >> 2;
             // calls needed: q0 .. (base + cnt - 1) / 4; the last group of calls is drawn only if the
             // chunk reaches it (an unaligned first slot needs one call beyond CHUNK / 4)
             const int ncalls = (int)(((unsigned)base + cnt - 1) >> 2) - (int)q0 + 1;
-            U4 cw[NG];
+            unsigned cbits = 0;
 #pragma unroll
             for (int m = 0; m < NG; ++m)
-                if (32 * m < ncalls) cw[m] = draw(seed, q0 + lane + 32 * m, step, SP, 4, did);
-                else cw[m] = U4{0, 0, 0, 0};
+                if (32 * m < ncalls) {
+                    const U4 w = draw(seed, q0 + lane + 32 * m, step, SP, 4, did);
+                    cbits |= ((w.x < thr ? 1u : 0u) | (w.y < thr ? 2u : 0u) | (w.z < thr ? 4u : 0u) |
+                              (w.w < thr ? 8u : 0u))
+                             << (4 * m);
+                }
             // ---- phase A: gather, first half kick, energy moment, candidate test
-            int qiq[PPT];
+            unsigned candm = 0;  // bit k: this lane's particle of row k is a candidate
             int qn = 0;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -740,7 +790,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 particle(i, c, f, vx, vy, vz, ef);
                 if (i < cnt && c < 0) err |= ERR_NONFINITE;  // corrupt cell index: dropped and reported
                 const bool valid = c >= 0;
-                unsigned long long qv = 0;
+                unsigned qa = 0, qb = 0;
                 if (valid) {
                     vz = fma_(Ksp, ef, vz);  // v_n
                     if (SP == 0) {  // energy moment at (x_n, v_n), 2^-12 eV, clamped at 2^26
@@ -749,34 +799,20 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                         if (!(eq <= (T)0x1p26)) eq = (T)0x1p26;
                         const unsigned long long Et = rint_u32(eq);
                         const unsigned long long Eh = rint_u32(mul_(eq, f));
-                        qv = (Et - Eh) | (Eh << 32);
+                        qa = (unsigned)(Et - Eh);
+                        qb = (unsigned)Eh;
                     }
                 }
-                if (SP == 0) warp_hist<true>(s_Q, c, qv, lane);
+                if (SP == 0) warp_energy(s_qlo, s_qhi, c, qa, qb, lane);
                 const unsigned slot = (unsigned)base + i;
                 const unsigned r = (slot >> 2) - q0;
-                uint32_t cword = 0;
-#pragma unroll
-                for (int m = 0; m < NG; ++m) {
-                    if (32 * m > 8 * (k + 1)) continue;  // row k needs calls up to 8 (k + 1)
-                    const uint32_t w0 = __shfl_sync(FULL, cw[m].x, r & 31), w1 = __shfl_sync(FULL, cw[m].y, r & 31);
-                    const uint32_t w2 = __shfl_sync(FULL, cw[m].z, r & 31), w3 = __shfl_sync(FULL, cw[m].w, r & 31);
-                    const int wi = slot & 3;
-                    const uint32_t wsel = wi == 0 ? w0 : wi == 1 ? w1 : wi == 2 ? w2 : w3;
-                    if ((int)(r >> 5) == m) cword = wsel;
-                }
-                const bool cand = valid && cword < thr;
+                const unsigned cb = __shfl_sync(FULL, cbits, r & 31);
+                const bool cand = valid && ((cb >> (4 * (r >> 5) + (slot & 3))) & 1u);
                 const unsigned cm = __ballot_sync(FULL, cand);
                 if (lane == 0 && cm) atomicAdd(&s_cnt[CNT_CAND + SP], (unsigned)__popc(cm));
-                qiq[k] = cand ? qn + __popc(cm & lt) : -1;
                 if (cand) {
-                    QEnt<T>& e = Q[qiq[k]];
-                    e.idx = i;
-                    e.out = 0;
-                    e.ef = ef;
-                    e.vx = vx;
-                    e.vy = vy;
-                    e.vz = vz;
+                    candm |= 1u << k;
+                    Q[qn + __popc(cm & lt)] = (uint8_t)i;
                 }
                 qn += __popc(cm);
             }
@@ -784,14 +820,21 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             __syncwarp();
             for (int r0 = 0; r0 < qn; r0 += 32) {
                 const int q = r0 + lane;
+                uint32_t o = 0;
                 if (q < qn) {
-                    const uint32_t i = Q[q].idx;
-                    collide<T>(S, Q[q], scell[i], srec[i].x, (uint32_t)base + i, obase + q, step, seed, s_hist,
-                               s_cnt, err);
+                    const int i = Q[q];
+                    int c;
+                    T f, vx, vy, vz, ef;
+                    particle(i, c, f, vx, vy, vz, ef);  // a candidate has a valid cell
+                    Cand<T> e{ef, vx, vy, fma_(Ksp, ef, vz)};
+                    o = collide<T>(S, e, c, f, (uint32_t)base + i, obase + q, step, seed, s_dep, s_cnt, err);
+                    R& rec = srec[i];
+                    rec.y = e.vx;
+                    rec.z = e.vy;
+                    rec.w = e.vz;
                 }
                 __syncwarp();
                 if (SP == 0) {  // the round's newborns, from the candidates' ranks to parent-slot order (dst <= src)
-                    const uint32_t o = q < qn ? Q[q].out : 0u;
                     const unsigned m1 = __ballot_sync(FULL, (o & 2u) != 0), m2 = __ballot_sync(FULL, (o & 4u) != 0);
                     if (o & 2u) move_rec<T>(S.sc, S.sp_, obase + q, offS + __popc(m1 & lt));
                     if (o & 4u) move_rec<T>(S.bc, S.bp, obase + q, offB + __popc(m2 & lt));
@@ -813,14 +856,9 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 T f, vx, vy, vz, ef;
                 particle(i, c, f, vx, vy, vz, ef);
                 if (c >= 0) {
-                    if (qiq[k] >= 0) {
-                        const QEnt<T>& e = Q[qiq[k]];
-                        vx = e.vx;
-                        vy = e.vy;
-                        vz = e.vz;
-                    } else {
-                        vz = fma_(Ksp, ef, vz);  // v_n, as in phase A
-                    }
+                    // v_n as in phase A; a candidate's staged record already holds its velocity after
+                    // the collision at t_n
+                    if (!((candm >> k) & 1u)) vz = fma_(Ksp, ef, vz);
                     vz = fma_(Ksp, ef, vz);
                     int cn;
                     T fn;
@@ -834,7 +872,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                             see = emit_see<T>(S, (uint32_t)base + i, step, seed, side, Pse, s_cnt);
                     }
                 }
-                warp_hist<false>(s_hist, alive ? P0.c : -1, alive ? (1ull << 40) + cic_F(P0.f) : 0ull, lane);
+                warp_dep(s_dep, alive ? P0.c : -1, alive ? cic_F(P0.f) : 0ull, lane);
                 const unsigned mA = __ballot_sync(FULL, alive);
                 if (alive) store_rec<T>(cout, pout, offA + __popc(mA & lt), P0);
                 offA += __popc(mA);
@@ -857,12 +895,20 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         }
     };
 
-    int it = 0;
-    for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++it) {
+    // tiles between flushes: at most 2^14 particles (and as many newborns) per flush, which keeps
+    // every histogram piece below 2^32
+    constexpr int FLUSH_TILES = (16384 / (BLOCK * PPT)) > 0 ? 16384 / (BLOCK * PPT) : 1;
+    int it = 0, since = 0;
+    for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++it, ++since) {
         // the store of tile g: the CTA's tiles increase, so its store only moves forward
         int seg = cur_seg < 0 ? 0 : cur_seg;
         while (seg + 1 < 2 * n_disc && s_segstart[seg + 1] <= g) ++seg;
+        if (seg == cur_seg && since >= FLUSH_TILES) {
+            flush();
+            since = 0;
+        }
         if (seg != cur_seg) {
+            since = 0;
             if (cur_seg >= 0) flush();
             const int d = seg >> 1, sp = seg & 1;
             if (tid == 0) {
@@ -905,10 +951,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
             }
             if (tid < NCNT) s_cnt[tid] = 0;
             __syncthreads();
-            for (int j = tid; j <= S.N; j += BLOCK) {
-                s_hist[j] = 0;
-                s_Q[j] = 0;
-            }
+            for (int j = tid; j < h32_words; j += BLOCK) s_h32[j] = 0;
             if (d != cur_d) {
                 const T* E = reinterpret_cast<const T*>(discs[d].E);
                 for (int j = tid; j <= S.N; j += BLOCK) s_E[j] = E[j];
@@ -930,8 +973,8 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
         prefetch(b ^ 1, g + gridDim.x);
         __syncwarp();
         if (mine && !(err & ERR_TIMEOUT)) {
-            const unsigned char* buf = stage + (size_t)b * sweep_stage_bytes<T, PPT>();
-            const R* srec = reinterpret_cast<const R*>(buf);
+            unsigned char* buf = stage + (size_t)b * sweep_stage_bytes<T, PPT>();
+            R* srec = reinterpret_cast<R*>(buf);
             const int32_t* scell = reinterpret_cast<const int32_t*>(buf + REC_BYTES);
             // slots and record offsets fit in 31 bits: the host caps every record buffer below 2^31
             if (S.sp == 0) chunk(cs, base, end - base, srec, scell, IC<0>{});
@@ -1607,7 +1650,7 @@ __device__ __forceinline__ unsigned long long group_sum64(unsigned peers, unsign
     return (unsigned long long)a + ((unsigned long long)b << 22) + ((unsigned long long)c << 44);
 }
 
-// a to node key, b to node key + 1 of a shared histogram; by group (as warp_hist) unless the
+// a to node key, b to node key + 1 of a shared histogram; by group (as warp_dep) unless the
 // warp's keys form more than HIST_GROUPS groups, then lane by lane.
 __device__ __forceinline__ void warp_add_pair(unsigned long long* h, int key, unsigned long long a,
                                               unsigned long long b, unsigned peers, bool leader, bool lanewise) {
@@ -2173,6 +2216,10 @@ static cudaError_t launch_sweep_t(const SweepLaunch& L) {
 
 template <typename T>
 static cudaError_t launch_sweep_p(const SweepLaunch& L) {
+    if (L.block == 512) {
+        if (L.ppt == 2) return launch_sweep_t<T, 512, 2>(L);
+        return launch_sweep_t<T, 512, 4>(L);
+    }
     if (L.block == 128) {
         if (L.ppt == 2) return launch_sweep_t<T, 128, 2>(L);
         if (L.ppt == 8) return launch_sweep_t<T, 128, 8>(L);
@@ -2197,6 +2244,10 @@ static int occ_t(int max_N, int n_disc) {
 }
 template <typename T>
 static int occ_p(int block, int ppt, int max_N, int n_disc) {
+    if (block == 512) {
+        if (ppt == 2) return occ_t<T, 512, 2>(max_N, n_disc);
+        return occ_t<T, 512, 4>(max_N, n_disc);
+    }
     if (block == 128) {
         if (ppt == 2) return occ_t<T, 128, 2>(max_N, n_disc);
         if (ppt == 8) return occ_t<T, 128, 8>(max_N, n_disc);
