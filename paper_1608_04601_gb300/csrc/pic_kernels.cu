@@ -166,25 +166,25 @@ __device__ __forceinline__ void dep_add(const DepHist& h, int c, unsigned long l
 // equal keys are reduced (match_any, redux) and their first lane adds the group's sums, unless the
 // warp's keys form more than HIST_GROUPS groups (then lane by lane).
 __device__ __forceinline__ void warp_dep(const DepHist& h, int key, unsigned long long F, int lane) {
-    const unsigned peers = __match_any_sync(FULL, key);
-    const bool leader = lane == __ffs(peers) - 1;
-    if (__popc(__ballot_sync(FULL, leader)) > HIST_GROUPS) {
+    const int k0 = __shfl_sync(FULL, key, 0);
+    if (!__all_sync(FULL, key == k0)) {  // several cells (or empty lanes): lane by lane
         if (key >= 0) dep_add(h, key, F);
         return;
     }
-    const unsigned lo = __reduce_add_sync(peers, (unsigned)(F & 0xFFFFu));
-    const unsigned hi = __reduce_add_sync(peers, (unsigned)(F >> 16));
-    if (leader && key >= 0) {
-        atomicAdd(&h.n[key], (unsigned)__popc(peers));
+    const unsigned lo = __reduce_add_sync(FULL, (unsigned)(F & 0xFFFFu));
+    const unsigned hi = __reduce_add_sync(FULL, (unsigned)(F >> 16));
+    if (lane == 0 && key >= 0) {
+        atomicAdd(&h.n[key], 32u);
         if (lo) atomicAdd(&h.lo[key], lo);
         if (hi) atomicAdd(&h.hi[key], hi);
     }
 }
 // Warp-aggregated energy moment: a (< 2^26) to node key, b (< 2^26) to node key + 1.
 __device__ __forceinline__ void warp_energy(unsigned* qlo, unsigned* qhi, int key, unsigned a, unsigned b, int lane) {
-    const unsigned peers = __match_any_sync(FULL, key);
-    const bool leader = lane == __ffs(peers) - 1;
-    if (__popc(__ballot_sync(FULL, leader)) > HIST_GROUPS) {
+    const int k0 = __shfl_sync(FULL, key, 0);
+    const unsigned peers = FULL;
+    const bool leader = lane == 0;
+    if (!__all_sync(FULL, key == k0)) {
         if (key >= 0) {
             if (a) {
                 atomicAdd(&qlo[key], a & 0x1FFFu);
