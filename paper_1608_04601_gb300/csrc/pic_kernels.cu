@@ -1226,12 +1226,13 @@ __device__ __forceinline__ void seg_apply(const Disc* __restrict__ discs, Ctl* _
             const int tw = (warp * 32 + u) * K;  // lane u's first chunk in the slice
             while (ci < K - 1 && rem >= s_cnt[row][tw + ci]) rem -= s_cnt[row][tw + ci++];
             const long long srcr = (t0 + tw + ci) * CHUNK + rem;
-            if (j < bcap) {
+            if (j < bcap) {  // records of one (FP32) or two (FP64) 16-byte words; no runtime-indexed array
                 const int cv = cin[srcr];
-                R rv[2];
-                for (int w = 0; w < rw; ++w) rv[w] = pin[srcr * rw + w];
+                const R r0 = pin[srcr * rw];
+                const R r1 = rw == 2 ? pin[srcr * rw + 1] : r0;
                 cdst[j] = cv;
-                for (int w = 0; w < rw; ++w) pdst[j * rw + w] = rv[w];
+                pdst[j * rw] = r0;
+                if (rw == 2) pdst[j * rw + 1] = r1;
             } else {
                 err = ERR_CAPACITY;
             }
@@ -1260,22 +1261,22 @@ constexpr int FIELD_SCAN = 256;  // threads of the integer scan
 // solve of a load (mode bit 4) only records the fields and counters. On a full step the current at
 // z = 0 is also projected onto the rf period's first harmonic (sin and cos at the step midpoint);
 // at the end of a period the amplitude is stored.
-__device__ __noinline__ void discharge_current(const Disc& D, int d, Ctl* ctl, int mode, long long step,
+__device__ __forceinline__ void discharge_current(const Disc& D, int d, Ctl* ctl, int mode, long long step,
                                                const double* Ew) {
-    unsigned long long c[6];
-    for (int k = 0; k < 4; ++k) c[k] = D.cnt[CNT_ABS + k];  // [species][electrode]
-    c[4] = D.cnt[CNT_SEE_SIDE];
-    c[5] = D.cnt[CNT_SEE_SIDE + 1];
+    // counters as scalars (an array here would live in local memory, cold at every step)
+    const unsigned long long c0 = D.cnt[CNT_ABS + 0], c1 = D.cnt[CNT_ABS + 1], c2 = D.cnt[CNT_ABS + 2],
+                             c3 = D.cnt[CNT_ABS + 3];  // [species][electrode]
+    const unsigned long long c4 = D.cnt[CNT_SEE_SIDE], c5 = D.cnt[CNT_SEE_SIDE + 1];
     if (!(mode & 4)) {  // a solve after a sweep (or a stand-alone solve): the current of step n
         double J0 = 0.0, JN = 0.0;  // no earlier solve: no current
         if (ctl->have_solve[d]) {
-            double dA[4], dS[2];
-            for (int k = 0; k < 4; ++k) dA[k] = (double)(c[k] - ctl->cnt_solve[d][k]);
-            dS[0] = (double)(c[4] - ctl->cnt_solve[d][4]);
-            dS[1] = (double)(c[5] - ctl->cnt_solve[d][5]);
+            const unsigned long long* cs = ctl->cnt_solve[d];
+            const double dA0 = (double)(c0 - cs[0]), dA1 = (double)(c1 - cs[1]), dA2 = (double)(c2 - cs[2]),
+                         dA3 = (double)(c3 - cs[3]);
+            const double dS0 = (double)(c4 - cs[4]), dS1 = (double)(c5 - cs[5]);
             const double we = D.w[0], wi = D.w[1], rdt = D.inv_dt;  // FP64 division is slow on this part
-            const double cond0 = E_CHARGE * (we * dA[0] - wi * dA[2] - we * dS[0]) * rdt;
-            const double condN = E_CHARGE * (wi * dA[3] - we * dA[1] + we * dS[1]) * rdt;
+            const double cond0 = E_CHARGE * (we * dA0 - wi * dA2 - we * dS0) * rdt;
+            const double condN = E_CHARGE * (wi * dA3 - we * dA1 + we * dS1) * rdt;
             J0 = EPS0 * (Ew[0] - ctl->E_wall[d][0]) * rdt + cond0;
             JN = EPS0 * (Ew[1] - ctl->E_wall[d][1]) * rdt + condN;
         }
@@ -1298,7 +1299,13 @@ __device__ __noinline__ void discharge_current(const Disc& D, int d, Ctl* ctl, i
     ctl->have_solve[d] = 1;
     ctl->E_wall[d][0] = Ew[0];
     ctl->E_wall[d][1] = Ew[1];
-    for (int k = 0; k < 6; ++k) ctl->cnt_solve[d][k] = c[k];
+    unsigned long long* cs = ctl->cnt_solve[d];
+    cs[0] = c0;
+    cs[1] = c1;
+    cs[2] = c2;
+    cs[3] = c3;
+    cs[4] = c4;
+    cs[5] = c5;
 }
 template <typename T>
 __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restrict__ ctl, int mode, int tid, int lane,
@@ -1412,7 +1419,7 @@ __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restric
 }
 
 template <typename T>
-__global__ void __launch_bounds__(POST_BLOCK) k_post(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(POST_BLOCK, 1) k_post(const Disc* __restrict__ discs, int n_disc, Ctl* __restrict__ ctl,
                                                      int out_buf, int mode, int nsl, int max_N) {
     constexpr int BLOCK = POST_BLOCK;
     extern __shared__ __align__(16) double s_f[];
