@@ -117,6 +117,10 @@ def _lib(prec: str):
         L.orc_moments.argtypes = [vp, vp, vp, vp, C.POINTER(OrcMomentInfo)]
         L.orc_reset_moments.argtypes = [vp]
         L.orc_last_current.argtypes = [vp, vp]
+        L.orc_set_current_drive.argtypes = [vp, C.c_int, C.c_double]
+        L.orc_set_current_drive.restype = C.c_int
+        L.orc_period_history.argtypes = [vp, vp, vp, C.c_int64, vp]
+        L.orc_period_history.restype = C.c_int64
         L.orc_set_diagnostics.argtypes = [vp, C.POINTER(OrcDiagConfig)]
         L.orc_set_diagnostics.restype = C.c_int
         L.orc_reset_diagnostics.argtypes = [vp]
@@ -361,6 +365,19 @@ class Oracle:
             raise RuntimeError("diagnostics not configured")
         out["snapshots"], out["samples"] = sn.value, sm.value
         return out
+
+    def set_current_drive(self, period_steps: int, J_target: float = 0.0):
+        """First-harmonic amplitude of J(0,t) per rf period; J_target > 0: adapt V0 after every period."""
+        if self.L.orc_set_current_drive(self.h, int(period_steps), float(J_target)):
+            raise ValueError("orc_set_current_drive rejected the arguments")
+
+    def period_history(self):
+        """(J_calc per completed period, V0 applied in it, V0 now)."""
+        Vn = C.c_double()
+        n = self.L.orc_period_history(self.h, None, None, 0, None)
+        amp, V0 = np.zeros(n), np.zeros(n)
+        self.L.orc_period_history(self.h, _p(amp), _p(V0), n, C.byref(Vn))
+        return amp, V0, Vn.value
 
     def last_current(self) -> np.ndarray:
         """J(t) of the last solved step at z = 0 and at z = d, A/m^2."""

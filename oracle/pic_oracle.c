@@ -113,6 +113,12 @@ struct orc_ctx {
     double E_wall_prev[2];
     int64_t abs_prev[2][2], see_side[2], see_prev[2];
     double J_last[2];
+    /* current-driven mode (Eq. adaptivevoltage): amplitude in effect, target (0: fixed voltage),
+     * first-harmonic projections of J(0,t) over the current rf period, per-period history       */
+    double V_amp, J_target, proj_a, proj_b;
+    int period_steps;
+    double *amp_hist, *V_hist;
+    int64_t hist_n, hist_cap;
     /* kinetic diagnostics */
     orc_diag_config dg;
     int dg_on;
@@ -408,6 +414,7 @@ orc_ctx* orc_create(const orc_gas* gas, const orc_params* p) {
     orc_ctx* o = (orc_ctx*)calloc(1, sizeof(orc_ctx));
     if (!o) return NULL;
     o->p = *p;
+    o->V_amp = p->V_rf_V;
     o->gas = *gas;
     o->N = p->n_cells;
     o->n_pts = gas->n_pts;
@@ -444,6 +451,7 @@ void orc_destroy(orc_ctx* o) {
     free(o->acc_D[0]); free(o->acc_D[1]); free(o->acc_Q); free(o->acc_Dprev);
     free(o->dg_D); free(o->dg_U); free(o->dg_V); free(o->dg_W); free(o->dg_K); free(o->dg_F); free(o->dg_Fa);
     free(o->dg_eedf); free(o->dg_E);
+    free(o->amp_hist); free(o->V_hist);
     free(o);
 }
 
@@ -898,7 +906,7 @@ int orc_solve(orc_ctx* o) {
         double Vj = (j == 0 || j == N) ? 0.5 * dx : dx;
         o->rho[j] = E_CHARGE * (o->p.w_i * (double)o->D[SP_I][j] - o->p.w_e * (double)o->D[SP_E][j]) / (TWO32 * Vj);
     }
-    double V0 = o->p.V_rf_V * sin(2.0 * PI_D * o->p.f_rf_Hz * t);
+    double V0 = o->V_amp * sin(2.0 * PI_D * o->p.f_rf_Hz * t);
     orc_poisson(N, dx, V0, 0.0, o->rho, o->phi, o->E64);
     for (int j = 0; j <= N; ++j) o->E[j] = (real)o->E64[j];
     /* Discharge current density over the step just solved for (from the previous solve to this
@@ -936,6 +944,47 @@ void orc_last_current(const orc_ctx* o, double J[2]) {
     J[1] = o->J_last[1];
 }
 
+/* End of step n (its solve done, J_last = J of step n): first-harmonic projections of J(0,t) over
+ * the rf period at the step midpoints t_{n+1/2}; at the period's last step its amplitude
+ * J_calc = sqrt(a^2 + b^2), a = (2/P) sum J sin(w t), b = (2/P) sum J cos(w t), and in the
+ * current-driven mode V0 <- V0 J0 / J_calc for the next period (Eq. adaptivevoltage).           */
+static void period_current(orc_ctx* o, int64_t n) {
+    const int P = o->period_steps;
+    if (P <= 0) return;
+    const double w = 2.0 * PI_D * o->p.f_rf_Hz, th = w * ((double)(n % P) + 0.5) * o->p.dt_s;
+    o->proj_a += o->J_last[0] * sin(th);
+    o->proj_b += o->J_last[0] * cos(th);
+    if (n % P != P - 1) return;
+    const double a = 2.0 * o->proj_a / P, b = 2.0 * o->proj_b / P;
+    const double amp = sqrt(a * a + b * b);
+    if (o->hist_n == o->hist_cap) {
+        o->hist_cap = o->hist_cap ? 2 * o->hist_cap : 64;
+        o->amp_hist = (double*)realloc(o->amp_hist, sizeof(double) * (size_t)o->hist_cap);
+        o->V_hist = (double*)realloc(o->V_hist, sizeof(double) * (size_t)o->hist_cap);
+    }
+    o->amp_hist[o->hist_n] = amp;
+    o->V_hist[o->hist_n] = o->V_amp;  /* the amplitude applied during this period */
+    o->hist_n++;
+    if (o->J_target > 0.0 && amp > 0.0) o->V_amp = o->V_amp * (o->J_target / amp);
+    o->proj_a = o->proj_b = 0.0;
+}
+
+int orc_set_current_drive(orc_ctx* o, int period_steps, double J_target) {
+    if (period_steps < 0 || !(J_target >= 0.0)) return -1;
+    o->period_steps = period_steps;
+    o->J_target = J_target;
+    o->proj_a = o->proj_b = 0.0;
+    return 0;
+}
+
+int64_t orc_period_history(const orc_ctx* o, double* amp, double* V0, int64_t cap, double* V_now) {
+    const int64_t n = o->hist_n < cap ? o->hist_n : cap;
+    if (amp) memcpy(amp, o->amp_hist, sizeof(double) * (size_t)n);
+    if (V0) memcpy(V0, o->V_hist, sizeof(double) * (size_t)n);
+    if (V_now) *V_now = o->V_amp;
+    return o->hist_n;
+}
+
 static void diag_take(orc_ctx* o);
 
 int orc_step(orc_ctx* o, int64_t n_steps) {
@@ -947,6 +996,7 @@ int orc_step(orc_ctx* o, int64_t n_steps) {
         if (o->p.sort_every > 0 && (n + 1) % o->p.sort_every == 0)
             if (orc_sort(o)) return -1;
         orc_solve(o);
+        period_current(o, n);
         for (int j = 0; j <= N; ++j) {
             o->acc_D[0][j] += (double)o->D[0][j];
             o->acc_D[1][j] += (double)o->D[1][j];

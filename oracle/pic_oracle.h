@@ -135,6 +135,13 @@ void     orc_reset_moments(orc_ctx* o);
  * powered electrode, the paper's definition), J[1] the same expression at z = d. Both are zero
  * after the first solve of a run (no previous field).                                         */
 void     orc_last_current(const orc_ctx* o, double J[2]);
+/* Per rf period of period_steps steps (counted from step 0; 0: off): the first-harmonic amplitude
+ * J_calc of J(0,t) at the step midpoints, and with J_target > 0 the current-driven mode of Eq.
+ * (adaptivevoltage): after every period V0 <- V0 J_target / J_calc (section "Boundary
+ * conditions"; the paper applies it to its fluid models, here it drives the particle model).  */
+int      orc_set_current_drive(orc_ctx* o, int period_steps, double J_target);
+/* Completed periods; their amplitudes J_calc and applied V0 (up to cap of each), V0 in effect. */
+int64_t  orc_period_history(const orc_ctx* o, double* amp, double* V0, int64_t cap, double* V_now);
 
 /* Kinetic diagnostics of the electrons (section "Results": the EEDF figure, the fast-electron
  * density and the profiles at t f = 0.25), taken at (x_n, v_n) before the sweep of step n:
