@@ -203,6 +203,17 @@ pic_status pic_current(pic_ctx* ctx, int32_t discharge, int64_t first, int64_t n
  * adaptivevoltage). Requires a time step that divides the period (PIC_ERR_STATE). */
 pic_status pic_current_amplitude(pic_ctx* ctx, int32_t discharge, int64_t first, int64_t n, double* out,
                                  int64_t* periods_done);
+/* Current-driven mode (Eq. adaptivevoltage, section "Boundary conditions"): with J0 > 0 (A/m^2),
+ * after every rf period of discharge d the amplitude of the applied voltage is multiplied by
+ * J0 / J_calc, J_calc the period's first-harmonic amplitude of J(0,t) (pic_current_amplitude);
+ * J0 = 0 keeps the amplitude in effect fixed. The paper adapts the voltage of its fluid models
+ * this way; here it drives the particle model. Requires a time step that divides the rf period
+ * (PIC_ERR_STATE). Synchronises the stream; takes effect from the next completed period.     */
+pic_status pic_set_current_drive(pic_ctx* ctx, int32_t discharge, double J0);
+/* Voltage amplitude V0 applied in rf periods first .. first+n-1 into host out[k] (the last
+ * PERIOD_HIST periods are kept); *V0_now the amplitude in effect now (either may be NULL).   */
+pic_status pic_voltage_amplitude(pic_ctx* ctx, int32_t discharge, int64_t first, int64_t n, double* out,
+                                 int64_t* periods_done, double* V0_now);
 pic_status pic_reset_moments(pic_ctx* ctx);
 
 /* ---- kinetic diagnostics of the electrons (section "Results") -------------

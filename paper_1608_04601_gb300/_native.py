@@ -123,6 +123,8 @@ PROTOTYPES = {
     "pic_current_amplitude": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64)]),
     "pic_load_profiles": (C.c_int, [_vp, _i32, _vp]),
     "pic_debug_wait": (C.c_int, [_i32, _i32]),
+    "pic_set_current_drive": (C.c_int, [_vp, _i32, C.c_double]),
+    "pic_voltage_amplitude": (C.c_int, [_vp, _i32, _i64, _i64, _vp, C.POINTER(_i64), C.POINTER(C.c_double)]),
     "pic_set_diagnostics": (C.c_int, [_vp, C.POINTER(PicDiagConfig)]),
     "pic_reset_diagnostics": (C.c_int, [_vp]),
     "pic_diagnostics": (C.c_int, [_vp, _i32] + [_vp] * 10 + [C.POINTER(_i64), C.POINTER(_i64)]),

@@ -457,6 +457,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         D.jh = d.weights.steps_per_period > 0 ? 4 * d.weights.steps_per_period : 4096;
         ALLOC(D.J_hist, double*, sizeof(double) * 2 * (size_t)D.jh);
         ALLOC(D.J_amp, double*, sizeof(double) * PERIOD_HIST);
+        ALLOC(D.V_hist, double*, sizeof(double) * PERIOD_HIST);
         D.has_see = d.weights.gamma_see > 0.0;
         D.tile = (int)tile;
         D.chunk = 32 * o.ppt;
@@ -536,6 +537,8 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         for (int i = 0; i < n_dis; ++i) {
             h.count[i][0] = o.load ? ctx->dis[i].weights.n_e0 : 0;
             h.count[i][1] = o.load ? ctx->dis[i].weights.n_i0 : 0;
+            h.V_scale[i] = 1.0;
+            h.J_drive[i] = 0.0;
         }
         cudaMemcpyAsync(ctx->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream);
         ce = launch_set_dense(ctx->d_discs, n_dis, ctx->d_ctl, 0, ctx->stream);
@@ -1020,6 +1023,17 @@ extern "C" pic_status pic_get_tables(pic_ctx* ctx, int32_t g, void* Te, void* Ti
     return PIC_OK;
 }
 
+// Copies ring entries first .. first+n-1 (ring of len entries of bytes each) to host memory, in at
+// most two contiguous copies.
+static cudaError_t ring_copy(void* dst, const void* ring, long long first, long long n, long long len, size_t bytes) {
+    const long long a = first % len, n1 = std::min(n, len - a);
+    const unsigned char* r = static_cast<const unsigned char*>(ring);
+    unsigned char* o = static_cast<unsigned char*>(dst);
+    cudaError_t e = n1 > 0 ? cudaMemcpy(o, r + a * bytes, (size_t)n1 * bytes, cudaMemcpyDeviceToHost) : cudaSuccess;
+    if (e == cudaSuccess && n > n1) e = cudaMemcpy(o + n1 * bytes, r, (size_t)(n - n1) * bytes, cudaMemcpyDeviceToHost);
+    return e;
+}
+
 extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
     if (bad_d(ctx, d) || !out) return PIC_ERR_ARG;
     const Disc& D = ctx->hd[d];
@@ -1078,12 +1092,8 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
     const long long keep = std::min(done, (long long)PERIOD_HIST);
     if (keep >= 2 * PIC_STEADY_BLOCK) {
         std::vector<double> pm(2 * (size_t)keep);
-        for (long long k = 0; k < keep; ++k) {  // oldest kept period first
-            const long long per = done - keep + k;
-            CK(cudaMemcpyAsync(&pm[2 * k], D.period_mean + 2 * (per % PERIOD_HIST), 2 * sizeof(double),
-                               cudaMemcpyDeviceToHost, ctx->stream), "period counts");
-        }
-        CK(cudaStreamSynchronize(ctx->stream), "period counts");
+        CK(ring_copy(pm.data(), D.period_mean, done - keep, keep, PERIOD_HIST, 2 * sizeof(double)),
+           "period counts");  // oldest kept period first
         std::vector<double> cum(2 * (size_t)(keep + 1), 0.0);
         for (long long k = 0; k < keep; ++k)
             for (int sp = 0; sp < 2; ++sp) cum[2 * (k + 1) + sp] = cum[2 * k + sp] + pm[2 * k + sp];
@@ -1125,10 +1135,7 @@ extern "C" pic_status pic_current(pic_ctx* ctx, int32_t d, int64_t first, int64_
     const Disc& D = ctx->hd[d];
     if (steps_done) *steps_done = ctx->step;
     if (first + n > ctx->step || ctx->step - first > D.jh) return fail(ctx, PIC_ERR_ARG, "steps not available");
-    for (long long k = 0; k < n; ++k) {
-        const long long slot = (first + k) % D.jh;
-        CK(cudaMemcpy(out + 2 * k, D.J_hist + 2 * slot, 2 * sizeof(double), cudaMemcpyDeviceToHost), "current");
-    }
+    CK(ring_copy(out, D.J_hist, first, n, D.jh, 2 * sizeof(double)), "current");
     return PIC_OK;
 }
 
@@ -1142,9 +1149,34 @@ extern "C" pic_status pic_current_amplitude(pic_ctx* ctx, int32_t d, int64_t fir
     if (periods_done) *periods_done = done;
     if (!D.jtab && n > 0) return fail(ctx, PIC_ERR_STATE, "the time step does not divide the rf period");
     if (first + n > done || done - first > PERIOD_HIST) return fail(ctx, PIC_ERR_ARG, "periods not available");
-    for (long long k = 0; k < n; ++k)
-        CK(cudaMemcpy(out + k, D.J_amp + (first + k) % PERIOD_HIST, sizeof(double), cudaMemcpyDeviceToHost),
-           "current amplitude");
+    CK(ring_copy(out, D.J_amp, first, n, PERIOD_HIST, sizeof(double)), "current amplitude");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_current_drive(pic_ctx* ctx, int32_t d, double J0) {
+    if (bad_d(ctx, d) || !(J0 >= 0.0) || !std::isfinite(J0)) return PIC_ERR_ARG;
+    if (!ctx->hd[d].jtab) return fail(ctx, PIC_ERR_STATE, "the time step does not divide the rf period");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    CK(cudaMemcpy(&ctx->d_ctl->J_drive[d], &J0, sizeof(double), cudaMemcpyHostToDevice), "current drive");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_voltage_amplitude(pic_ctx* ctx, int32_t d, int64_t first, int64_t n, double* out,
+                                            int64_t* periods_done, double* V0_now) {
+    if (bad_d(ctx, d) || first < 0 || n < 0 || (n && !out)) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    const Disc& D = ctx->hd[d];
+    const int spp = ctx->dis[d].weights.steps_per_period;
+    const long long done = spp > 0 ? ctx->step / spp : 0;
+    if (periods_done) *periods_done = done;
+    if (V0_now) {
+        double s = 1.0;
+        CK(cudaMemcpy(&s, &ctx->d_ctl->V_scale[d], sizeof(double), cudaMemcpyDeviceToHost), "voltage");
+        *V0_now = D.V_rf * s;
+    }
+    if (!D.jtab && n > 0) return fail(ctx, PIC_ERR_STATE, "the time step does not divide the rf period");
+    if (first + n > done || done - first > PERIOD_HIST) return fail(ctx, PIC_ERR_ARG, "periods not available");
+    CK(ring_copy(out, D.V_hist, first, n, PERIOD_HIST, sizeof(double)), "voltage amplitude");
     return PIC_OK;
 }
 

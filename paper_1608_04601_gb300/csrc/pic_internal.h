@@ -117,6 +117,7 @@ struct Disc {
     int jh;
     const double* jtab;       // sin, cos of 2 pi f (k + 1/2) dt, k < steps_per_period, or null
     double* J_amp;            // [PERIOD_HIST]
+    double* V_hist;           // [PERIOD_HIST] rf voltage amplitude applied in every period
     // kinetic diagnostics (null until configured): node accumulators [DG_ARRAYS][N+1], sum of the
     // node field over the snapshots [N+1], EEDF counts [bins], snapshots and samples taken [2]
     unsigned long long* dg;
@@ -162,6 +163,10 @@ struct Ctl {
     double E_wall[MAXD][2];
     unsigned long long cnt_solve[MAXD][6];
     double J_sum[MAXD][2];
+    // current-driven mode (Eq. adaptivevoltage): the applied amplitude is V_rf V_scale, and with
+    // J_drive > 0 V_scale <- V_scale J_drive / J_calc after every rf period
+    double V_scale[MAXD];
+    double J_drive[MAXD];
     double period_acc[MAXD][2];   // sum of the counts over the steps of the current rf period
     unsigned sort_rows_done[MAXD][2];  // k_sort_rows CTAs finished, per store (reset by the last)
 };

@@ -1290,7 +1290,11 @@ __device__ __forceinline__ void discharge_current(const Disc& D, int d, Ctl* ctl
             ctl->J_sum[d][1] += J0 * D.jtab[2 * k + 1];
             if (k == spp - 1) {
                 const double a = 2.0 * ctl->J_sum[d][0] / spp, b = 2.0 * ctl->J_sum[d][1] / spp;
-                D.J_amp[(step / spp) % PERIOD_HIST] = sqrt(a * a + b * b);
+                const double amp = sqrt(a * a + b * b);
+                D.J_amp[(step / spp) % PERIOD_HIST] = amp;
+                D.V_hist[(step / spp) % PERIOD_HIST] = D.V_rf * ctl->V_scale[d];
+                const double J0 = ctl->J_drive[d];
+                if (J0 > 0.0 && amp > 0.0) ctl->V_scale[d] = ctl->V_scale[d] * (J0 / amp);  // Eq. (adaptivevoltage)
                 ctl->J_sum[d][0] = 0.0;
                 ctl->J_sum[d][1] = 0.0;
             }
@@ -1328,8 +1332,9 @@ __device__ __forceinline__ void field_solve(const Disc& D, int d, Ctl* __restric
     const double inv_dx = D.inv_dx, m_inv_2dx = D.m_inv_2dx, hdx_eps = D.hdx_eps, inv_N = D.inv_N;
     const long long step = ctl->step;
     const long long ns = (mode & 4) ? step : step + 1;  // time level of the solve
-    const double V0 = D.V0tab ? D.V0tab[ns % D.steps_per_period]
-                              : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt));
+    const double V0 = (D.V0tab ? D.V0tab[ns % D.steps_per_period]
+                               : D.V_rf * sin(2.0 * PI_D * D.f_rf * ((double)ns * D.dt))) *
+                      ctl->V_scale[d];
     // one pass over the nodes: stage the deposits in shared memory, accumulate the moments (mode
     // bit 2) and hand the next sweep zeroed deposit arrays
     unsigned long long* sde = reinterpret_cast<unsigned long long*>(s_f);

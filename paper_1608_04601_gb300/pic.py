@@ -262,6 +262,21 @@ class Simulation:
             self._ck(self.L.pic_current_amplitude(self.h, d, first, n, _ptr(out), C.byref(done)))
         return out
 
+    def set_current_drive(self, d: int = 0, J0: float = 0.0):
+        """Current-driven mode (pic_set_current_drive): V0 <- V0 J0 / J_calc after every rf period."""
+        self._ck(self.L.pic_set_current_drive(self.h, d, float(J0)))
+
+    def voltage_amplitude(self, d: int = 0, first: int = 0, n=None):
+        """(V0 applied in each completed rf period, V0 in effect now)."""
+        done, vn = C.c_int64(), C.c_double()
+        self._ck(self.L.pic_voltage_amplitude(self.h, d, 0, 0, None, C.byref(done), C.byref(vn)))
+        if n is None:
+            n = done.value - first
+        out = np.zeros(max(n, 0))
+        if n > 0:
+            self._ck(self.L.pic_voltage_amplitude(self.h, d, first, n, _ptr(out), C.byref(done), None))
+        return out, vn.value
+
     def set_diagnostics(self, period_steps: int = 0, phase_step: int = 0, sample_every: int = 0,
                         eedf_bins: int = 200, eedf_de_eV: float = 0.5, fast_eV: float = 0.0, off: bool = False):
         """Kinetic diagnostics of the electrons (pic_set_diagnostics): rf-phase snapshots at the
