@@ -119,6 +119,8 @@ def _lib(prec: str):
         L.orc_last_current.argtypes = [vp, vp]
         L.orc_set_current_drive.argtypes = [vp, C.c_int, C.c_double]
         L.orc_set_current_drive.restype = C.c_int
+        L.orc_set_scheme.argtypes = [vp, C.c_int]
+        L.orc_set_scheme.restype = C.c_int
         L.orc_period_history.argtypes = [vp, vp, vp, C.c_int64, vp]
         L.orc_period_history.restype = C.c_int64
         L.orc_set_diagnostics.argtypes = [vp, C.POINTER(OrcDiagConfig)]
@@ -370,6 +372,11 @@ class Oracle:
         """First-harmonic amplitude of J(0,t) per rf period; J_target > 0: adapt V0 after every period."""
         if self.L.orc_set_current_drive(self.h, int(period_steps), float(J_target)):
             raise ValueError("orc_set_current_drive rejected the arguments")
+
+    def set_scheme(self, leapfrog: bool):
+        """Velocity Verlet (collisions at v_n, default) or the leapfrog variant (at v_{n+1/2})."""
+        if self.L.orc_set_scheme(self.h, 1 if leapfrog else 0):
+            raise ValueError("orc_set_scheme rejected the argument")
 
     def period_history(self):
         """(J_calc per completed period, V0 applied in it, V0 now)."""

@@ -116,6 +116,7 @@ struct orc_ctx {
     /* current-driven mode (Eq. adaptivevoltage): amplitude in effect, target (0: fixed voltage),
      * first-harmonic projections of J(0,t) over the current rf period, per-period history       */
     double V_amp, J_target, proj_a, proj_b;
+    int leapfrog;  /* 1: collisions at v_{n+1/2} (leapfrog variant); 0: at v_n (velocity Verlet) */
     int period_steps;
     double *amp_hist, *V_hist;
     int64_t hist_n, hist_cap;
@@ -690,6 +691,10 @@ int orc_sweep(orc_ctx* o) {
                 o->Q[c] += Et - Eh;
                 o->Q[c + 1] += Eh;
             }
+            if (o->leapfrog) {  /* both half kicks first: the collision acts on v_{n+1/2} */
+                vz = R_FMA(o->K_e, ef, vz);
+                e2 = R_FMA(vx, vx, R_FMA(vy, vy, vz * vz));
+            }
             int have_child = 0;
             real ce_vx = 0, ce_vy = 0, ce_vz = 0, ci_vx = 0, ci_vy = 0, ci_vz = 0;
             if (candidate_word(o, slot, SP_E) < o->d.thr_e) {
@@ -754,7 +759,7 @@ int orc_sweep(orc_ctx* o) {
                     }
                 }
             }
-            vz = R_FMA(o->K_e, ef, vz);
+            if (!o->leapfrog) vz = R_FMA(o->K_e, ef, vz);  /* second half kick after the collision */
             int32_t cn;
             real fn;
             int side = drift(o, c, f, vz, &cn, &fn);
@@ -765,7 +770,7 @@ int orc_sweep(orc_ctx* o) {
                 o->cnt.absorbed[SP_E][side]++;
             }
             if (have_child) {
-                ce_vz = R_FMA(o->K_e, ef, ce_vz);
+                if (!o->leapfrog) ce_vz = R_FMA(o->K_e, ef, ce_vz);  /* newborns born at t_n: half kick */
                 side = drift(o, c, f, ce_vz, &cn, &fn);
                 if (side < 0) {
                     store_push(&sec, cn, fn, ce_vx, ce_vy, ce_vz);
@@ -773,7 +778,7 @@ int orc_sweep(orc_ctx* o) {
                 } else {
                     o->cnt.absorbed[SP_E][side]++;
                 }
-                ci_vz = R_FMA(o->K_i, ef, ci_vz);
+                if (!o->leapfrog) ci_vz = R_FMA(o->K_i, ef, ci_vz);
                 side = drift(o, c, f, ci_vz, &cn, &fn);
                 if (side < 0) {
                     store_push(&birth[SP_I], cn, fn, ci_vx, ci_vy, ci_vz);
@@ -794,6 +799,7 @@ int orc_sweep(orc_ctx* o) {
             real f = s->f[k], vx = s->vx[k], vy = s->vy[k], vz = s->vz[k];
             real ef = gather(o, c, f);
             vz = R_FMA(o->K_i, ef, vz);
+            if (o->leapfrog) vz = R_FMA(o->K_i, ef, vz);  /* collision at v_{n+1/2} */
             if (candidate_word(o, slot, SP_I) < o->d.thr_i) {
                 uint32_t r[4];
                 draw(o, slot, SP_I, CALL_MAIN, r);
@@ -827,7 +833,7 @@ int orc_sweep(orc_ctx* o) {
                     o->cnt.collisions_i[1]++;
                 }
             }
-            vz = R_FMA(o->K_i, ef, vz);
+            if (!o->leapfrog) vz = R_FMA(o->K_i, ef, vz);
             int32_t cn;
             real fn;
             int side = drift(o, c, f, vz, &cn, &fn);
@@ -967,6 +973,12 @@ static void period_current(orc_ctx* o, int64_t n) {
     o->hist_n++;
     if (o->J_target > 0.0 && amp > 0.0) o->V_amp = o->V_amp * (o->J_target / amp);
     o->proj_a = o->proj_b = 0.0;
+}
+
+int orc_set_scheme(orc_ctx* o, int leapfrog) {
+    if (leapfrog != 0 && leapfrog != 1) return -1;
+    o->leapfrog = leapfrog;
+    return 0;
 }
 
 int orc_set_current_drive(orc_ctx* o, int period_steps, double J_target) {

@@ -140,6 +140,12 @@ void     orc_last_current(const orc_ctx* o, double J[2]);
  * (adaptivevoltage): after every period V0 <- V0 J_target / J_calc (section "Boundary
  * conditions"; the paper applies it to its fluid models, here it drives the particle model).  */
 int      orc_set_current_drive(orc_ctx* o, int period_steps, double J_target);
+/* Push scheme (section "PIC/MCC simulation procedure": the method uses velocity Verlet and notes
+ * that it converges faster in dt than leapfrog). 0 (default): velocity Verlet, the collision acts
+ * on v_n between the two half kicks; 1: leapfrog variant, both half kicks first (v_{n+1/2} =
+ * v_{n-1/2} + a_n dt, the same two operations) and the collision acts on v_{n+1/2}, newborns
+ * drift with their birth velocity. Diagnostics at v_n in both.                                */
+int      orc_set_scheme(orc_ctx* o, int leapfrog);
 /* Completed periods; their amplitudes J_calc and applied V0 (up to cap of each), V0 in effect. */
 int64_t  orc_period_history(const orc_ctx* o, double* amp, double* V0, int64_t cap, double* V_now);
 
