@@ -111,7 +111,11 @@ typedef struct {
                              /* period (requires sort_every | steps/period)  */
     void* cuda_stream;       /* cudaStream_t to enqueue on; NULL = own stream */
     int32_t load;            /* 1 (default): load n_e0 / n_i0 at create      */
-    int32_t reserved;
+    int32_t leapfrog;        /* 0 (default): velocity Verlet, collisions at  */
+                             /* v_n between the two half kicks (the paper's  */
+                             /* scheme); 1: leapfrog variant, collisions at  */
+                             /* v_{n+1/2} after both kicks, newborns drift   */
+                             /* with their birth velocity                    */
 } pic_options;
 
 /* Fills *opt with the defaults documented above. */

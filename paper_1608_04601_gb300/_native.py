@@ -38,7 +38,7 @@ class PicDischarge(C.Structure):
 class PicOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sort_every", C.c_int32), ("block", C.c_int32), ("ppt", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("load", C.c_int32), ("reserved", C.c_int32)]
+                ("load", C.c_int32), ("leapfrog", C.c_int32)]
 
 
 class PicMoments(C.Structure):

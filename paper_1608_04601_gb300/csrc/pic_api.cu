@@ -459,6 +459,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ALLOC(D.J_amp, double*, sizeof(double) * PERIOD_HIST);
         ALLOC(D.V_hist, double*, sizeof(double) * PERIOD_HIST);
         D.has_see = d.weights.gamma_see > 0.0;
+        D.leapfrog = o.leapfrog != 0;
         D.tile = (int)tile;
         D.chunk = 32 * o.ppt;
         D.warps = o.block / 32;

@@ -72,6 +72,7 @@ struct Disc {
     double pc_r[2], pc_w[2], inv_dx, m_inv_2dx, hdx_eps, inv_N, inv_dt;
     const double* V0tab;      // V_rf sin(2 pi f k dt), k < steps_per_period, or null (then sin on device)
     int has_see, tile;        // sweep tile (slots) of this context
+    int leapfrog, pad_lf;     // push scheme: 0 velocity Verlet (collisions at v_n), 1 leapfrog (at v_{n+1/2})
     int chunk, warps;         // compaction unit: one warp's 32 PPT slots; warps per tile
     int rec_words;            // particle record size in 16-byte words (1: FP32, 2: FP64)
     Consts<float> cf;

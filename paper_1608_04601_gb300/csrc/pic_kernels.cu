@@ -56,7 +56,7 @@ struct Part {
 template <typename T>
 struct Seg {
     Consts<T> k;
-    int d, sp, N, n_pts, has_see, n_exc;
+    int d, sp, N, n_pts, has_see, n_exc, leapfrog;
     uint32_t thr, did;
     long long n, cap, bcap, tile0, ntiles;
     const int32_t* cin;
@@ -338,7 +338,7 @@ __device__ __forceinline__ uint32_t collide(const Seg<T>& S, Cand<T>& q, int qc,
         if (child) {  // newborns: second half kick and drift from the parent's position
             int cn;
             T fn;
-            cvz = fma_(K.K[0], q.ef, cvz);
+            if (!S.leapfrog) cvz = fma_(K.K[0], q.ef, cvz);  // born at t_n (Verlet): the second half kick
             int side = drift(N, K.dtdx, qc, qf, cvz, cn, fn, err);
             if (side < 0) {
                 store_rec<T>(S.sc, S.sp_, ridx, Part<T>{cn, fn, cvx, cvy, cvz});
@@ -347,7 +347,7 @@ __device__ __forceinline__ uint32_t collide(const Seg<T>& S, Cand<T>& q, int qc,
             } else {
                 atomicAdd(&sC[CNT_ABS + side], 1u);
             }
-            ivz = fma_(K.K[1], q.ef, ivz);
+            if (!S.leapfrog) ivz = fma_(K.K[1], q.ef, ivz);
             side = drift(N, K.dtdx, qc, qf, ivz, cn, fn, err);
             if (side < 0) {
                 store_rec<T>(S.bc, S.bp, ridx, Part<T>{cn, fn, ivx, ivy, ivz});
@@ -826,7 +826,9 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                     int c;
                     T f, vx, vy, vz, ef;
                     particle(i, c, f, vx, vy, vz, ef);  // a candidate has a valid cell
-                    Cand<T> e{ef, vx, vy, fma_(Ksp, ef, vz)};
+                    T vzc = fma_(Ksp, ef, vz);                 // v_n
+                    if (S.leapfrog) vzc = fma_(Ksp, ef, vzc);  // leapfrog: the collision acts on v_{n+1/2}
+                    Cand<T> e{ef, vx, vy, vzc};
                     o = collide<T>(S, e, c, f, (uint32_t)base + i, obase + q, step, seed, s_dep, s_cnt, err);
                     R& rec = srec[i];
                     rec.y = e.vx;
@@ -857,9 +859,10 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 particle(i, c, f, vx, vy, vz, ef);
                 if (c >= 0) {
                     // v_n as in phase A; a candidate's staged record already holds its velocity after
-                    // the collision at t_n
-                    if (!((candm >> k) & 1u)) vz = fma_(Ksp, ef, vz);
-                    vz = fma_(Ksp, ef, vz);
+                    // the collision (at v_n, or at v_{n+1/2} in the leapfrog scheme, then final)
+                    const bool coll = (candm >> k) & 1u;
+                    if (!coll) vz = fma_(Ksp, ef, vz);
+                    if (!(coll && S.leapfrog)) vz = fma_(Ksp, ef, vz);
                     int cn;
                     T fn;
                     const int side = drift(N, dtdx, c, f, vz, cn, fn, err);
@@ -919,6 +922,7 @@ __global__ void __launch_bounds__(BLOCK, sweep_min_blocks<T, BLOCK, PPT>())
                 S.N = D.N;
                 S.n_pts = D.n_pts;
                 S.has_see = D.has_see;
+                S.leapfrog = D.leapfrog;
                 S.n_exc = D.n_exc;
                 S.thr = D.thr[sp];
                 S.did = D.discharge_id;

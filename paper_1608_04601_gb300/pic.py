@@ -46,7 +46,7 @@ class Simulation:
 
     def __init__(self, gases, discharges, seed=None, precision: str = "fp32", sort_every: int = 0,
                  block: int = 256, ppt: int = 4, ctas_per_sm: int = 0, use_graph: bool = False,
-                 stream=None, load: bool = True, capacity=None):
+                 stream=None, load: bool = True, capacity=None, leapfrog: bool = False):
         self.L = NV.lib()
         if isinstance(gases, GasTables):
             gases = [gases]
@@ -74,6 +74,7 @@ class Simulation:
         opt.ctas_per_sm = ctas_per_sm
         opt.use_graph = 1 if use_graph else 0
         opt.load = 1 if load else 0
+        opt.leapfrog = 1 if leapfrog else 0
         if stream == "torch":
             import torch
             opt.cuda_stream = torch.cuda.current_stream().cuda_stream
