@@ -242,9 +242,9 @@ def run_gpu(args, rank: int, world: int):
         ps = float(sum(counts))
         out = {"ps": ps, "total_ms": total_ms, "sweep_ms": sweep_ms, "sweep_launches": launches,
                "clocks": clk.summary(), "counts": (counts[0], counts[-1])}
-        # kernels launched per step: the sweep and the post-sweep kernel (segment tables, newborn
-        # copies, store totals, field, moments); when a sort is due its count, row-scan (with the
-        # cell scan in its last CTA per store) and scatter (with the dense reset) kernels
+        # kernels launched per step: the sweep and the post-sweep kernel (region starts, newborn
+        # copies, store totals, field, moments, J(t)); when a sort is due its count, row-scan (with
+        # the cell scan in its last CTA per store) and scatter (with the dense reset) kernels
         step0 = sim.step_index - steps
         sorts = sum(1 for n in range(step0 + 1, step0 + steps + 1) if sort_every > 0 and n % sort_every == 0)
         out["gpu_launches"] = 2 * steps + 3 * sorts

@@ -480,7 +480,7 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
             D.R0[sp] = rs.R0;
             D.rcap[sp] = rs.rcap;
             if (D.rcap[sp] > 0x7FFFFFF0ll) {
-                pic_status s_ = fail(ctx, PIC_ERR_ARG, "capacity too large for 32-bit segment offsets");
+                pic_status s_ = fail(ctx, PIC_ERR_ARG, "capacity too large for 32-bit record offsets");
                 pic_destroy(ctx);
                 return s_;
             }
@@ -909,7 +909,7 @@ extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
         CK(launch_pack_state(ctx->fp64, ctx->d_discs, d, sp, ctx->cur, n, sc, sv, bad, grid, ctx->stream),
            "state pack");
     }
-    // count and segment table on the device (a rejected upload leaves an empty store), then one
+    // count and dense layout on the device (a rejected upload leaves an empty store), then one
     // synchronisation for the check word
     CK(launch_finish_upload(ctx->d_discs, ctx->d_ctl, d, sp, n, bad, ctx->cur, ctx->stream), "state finish");
     s = pinned(ctx, 64);
