@@ -210,10 +210,14 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def measure(prec: str, steps: int, warmup: int, sort_every: int, disc=None, disc_gas=None):
+    def measure(prec: str, steps: int, warmup: int, sort_every: int, disc=None, disc_gas=None, leapfrog=False,
+                setup=None):
         dd = disc if disc is not None else d
         sim = pic.Simulation(disc_gas if disc_gas is not None else gas, dd, seed=dd.seed, precision=prec,
-                             sort_every=sort_every, stream="torch", block=args.block, ppt=args.ppt)
+                             sort_every=sort_every, stream="torch", block=args.block, ppt=args.ppt,
+                             leapfrog=leapfrog)
+        if setup is not None:
+            setup(sim)
         if sort_every > 0:
             # the load draws positions in slot order, so the loaded store is unsorted; a long run spends
             # all but its first sort period on cell-sorted stores, so the store is sorted once here,
@@ -221,6 +225,7 @@ def run_gpu(args, rank: int, world: int):
             sim.sort()
         sim.step(warmup)
         sim.sync()
+        electrons0 = sim.count(0, 0)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         counts = []
         sim.sweep_timing(True)
@@ -241,7 +246,7 @@ def run_gpu(args, rank: int, world: int):
         total_ms = sum(step_ms)
         ps = float(sum(counts))
         out = {"ps": ps, "total_ms": total_ms, "sweep_ms": sweep_ms, "sweep_launches": launches,
-               "clocks": clk.summary(), "counts": (counts[0], counts[-1])}
+               "clocks": clk.summary(), "counts": (counts[0], counts[-1]), "electrons0": electrons0}
         # kernels launched per step: the sweep and the post-sweep kernel (region starts, newborn
         # copies, store totals, field, moments, J(t)); when a sort is due its count, row-scan (with
         # the cell scan in its last CTA per store) and scatter (with the dense reset) kernels
@@ -359,6 +364,39 @@ def run_gpu(args, rank: int, world: int):
               "ms_per_step": r3["total_ms"] / 20, "steps": 20, "warmup": 6,
               "particles": int(r3["ps"] / max(1, r3["sweep_launches"])), "clocks": r3["clocks"],
               "roofline": sweep_roofline(r3, "fp32", args.block, args.ppt, dc.name)}
+    rows_f = None
+    if not args.quick and not args.no_rows_f:
+        # the widened rows on the same workload and launch shape: the leapfrog variant (f2); the
+        # kinetic diagnostics (f1) taken at every step, whose extra step time is the diagnostics
+        # kernel's (20 B read per electron: cell and record); the current-driven mode (f3)
+        n_f = max(4, args.steps // 2)
+        lf = measure("fp32", n_f, args.warmup, sort_every, leapfrog=True)
+        base = measure("fp32", n_f, args.warmup, sort_every)
+        dg = measure("fp32", n_f, args.warmup, sort_every,
+                     setup=lambda sim: sim.set_diagnostics(period_steps=1, phase_step=0, sample_every=1,
+                                                           eedf_bins=400, eedf_de_eV=0.25, fast_eV=d.V_rf_V / 4))
+        dr = measure("fp32", n_f, args.warmup, sort_every, setup=lambda sim: sim.set_current_drive(0, 10.0))
+        peak, peak_note = peaks()
+        extra_ms = (dg["total_ms"] - base["total_ms"]) / n_f
+        electrons = float(dg["electrons0"])  # electrons at the first timed step
+        diag_gbs = 20.0 * electrons / (extra_ms * 1e-3) / 1e9 if extra_ms > 0 else None
+        P = d.steps_per_period
+        rows_f = {
+            "leapfrog": {"value": lf["ps"] / (lf["total_ms"] * 1e-3), "unit": UNIT, "ms_per_step": lf["total_ms"] / n_f,
+                         "roofline": sweep_roofline(lf, "fp32", args.block, args.ppt, d0.name)},
+            "verlet_same_run": {"value": base["ps"] / (base["total_ms"] * 1e-3), "unit": UNIT,
+                                "ms_per_step": base["total_ms"] / n_f},
+            "diagnostics_every_step": {
+                "value": dg["ps"] / (dg["total_ms"] * 1e-3), "unit": UNIT, "ms_per_step": dg["total_ms"] / n_f,
+                "kernel_ms_per_launch": extra_ms, "electrons_per_launch": electrons,
+                "achieved_gbs": diag_gbs, "frac": (diag_gbs / peak) if diag_gbs else None, "peak": peak,
+                "peak_source": peak_note,
+                "kernel_timing": "step-time difference against the same steps without diagnostics (CUDA events)",
+                "overhead_at_paper_schedule": (extra_ms * (1.0 / P + 1.0 / 16)) / (base["total_ms"] / n_f),
+                "schedule_note": "snapshot once per rf period and an EEDF sample every 16 steps"},
+            "current_drive": {"value": dr["ps"] / (dr["total_ms"] * 1e-3), "unit": UNIT,
+                              "ms_per_step": dr["total_ms"] / n_f, "J0_A_m2": 10.0},
+        }
     if args.warm_start and not args.quick and world == 1:
         # rf periods to the steady state from the homogeneous start vs from the network's profiles
         from paper_1608_04601_gb300 import warmstart
@@ -394,6 +432,8 @@ def run_gpu(args, rank: int, world: int):
         res["c3"] = c3
     if warm:
         res["warm_start"] = warm
+    if rows_f:
+        res["rows_f"] = rows_f
     return res
 
 
@@ -479,6 +519,8 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="main measurement only (no FP64 path, end-to-end, batch, large workload, warm start)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-rows-f", action="store_true",
+                    help="skip the leapfrog, diagnostics and current-drive measurements")
     ap.add_argument("--no-c3", dest="c3", action="store_false", help="skip the 2e7 + 2e7 particle workload")
     ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
                     help="skip the warm-start experiment (training runs, network training, cold vs warm runs)")

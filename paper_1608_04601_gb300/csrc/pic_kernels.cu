@@ -1666,8 +1666,8 @@ __device__ __forceinline__ unsigned long long group_sum64(unsigned peers, unsign
     return (unsigned long long)a + ((unsigned long long)b << 22) + ((unsigned long long)c << 44);
 }
 
-// a to node key, b to node key + 1 of a shared histogram; by group (as warp_dep) unless the
-// warp's keys form more than HIST_GROUPS groups, then lane by lane.
+// a to node key, b to node key + 1 of a shared histogram: reduced over the lanes of `peers` and
+// added by the leader, or (lanewise) added lane by lane.
 __device__ __forceinline__ void warp_add_pair(unsigned long long* h, int key, unsigned long long a,
                                               unsigned long long b, unsigned peers, bool leader, bool lanewise) {
     if (lanewise) {
@@ -1791,9 +1791,12 @@ __global__ void __launch_bounds__(DIAG_BLOCK) k_diag(const Disc* __restrict__ di
                     bin = xb < binsT ? (int)xb : A.bins - 1;
                 }
             }
-            const unsigned peers = __match_any_sync(FULL, c);
-            const bool leader = lane == __ffs(peers) - 1;
-            const bool lanewise = __popc(__ballot_sync(FULL, leader)) > HIST_GROUPS;
+            // a row of one cell (common on a cell-sorted store) is reduced across the warp, any other
+            // row added lane by lane (grouping by match_any cost more than it saved in the sweep)
+            const int c0 = __shfl_sync(FULL, c, 0);
+            const bool lanewise = !__all_sync(FULL, c == c0);
+            const unsigned peers = FULL;
+            const bool leader = lane == 0;
             const unsigned long long dA = c >= 0 ? (1ull << 32) - F : 0ull, dB = c >= 0 ? F : 0ull;
             if (mD) warp_add_pair(h[DG_D], c, dA, dB, peers, leader, lanewise);
             if (mU) warp_add_pair(h[DG_U], c, uA, uB, peers, leader, lanewise);
