@@ -294,9 +294,30 @@ def run_gpu(args, rank: int, world: int):
             d2h += sum(x["c"].size * (4 + 4 * rb) for x in st) + 3 * 8 * m["n_e"].size
         dt = time.perf_counter() - t0
         sim.close()
+        # the host link on its own: one plain pinned copy of a step's upload size in each direction
+        nb = int(h2d / steps)
+        hbuf = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        dbuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        link = {}
+        for name, (dst, src) in (("h2d", (dbuf, hbuf)), ("d2h", (hbuf, dbuf))):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(10):
+                dst.copy_(src, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            link[name] = 10 * nb / (a.elapsed_time(b) * 1e-3) / 1e9
+        del hbuf, dbuf
+        floor_ms = (h2d / steps / link["h2d"] + d2h / steps / link["d2h"]) / 1e6
         return {"value": ps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d / steps),
                 "d2h_bytes_per_step": int(d2h / steps), "host_memory": "pinned",
-                "per_step": "upload of the whole state, one step, download of the state and the moments"}
+                "per_step": "upload of the whole state, one step, download of the state and the moments",
+                "ms_per_step": dt * 1e3 / steps,
+                "link_gbs": {"h2d": link["h2d"], "d2h": link["d2h"],
+                             "note": "one plain pinned copy of the step's upload size, 10 repetitions"},
+                "copy_floor_ms": floor_ms}
 
     def measure_batch(steps: int, warmup: int, sort_every: int):
         """32 discharges of uneven counts (He/Ar-like x 4 pressures x 4 voltages, 1e5..4e6 each) in one
