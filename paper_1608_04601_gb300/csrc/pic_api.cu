@@ -849,9 +849,13 @@ extern "C" pic_status pic_get_count(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
 }
 
 // Device staging for state transfers (cells, then four real arrays), grown on demand.
+static size_t pad16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Device staging of a state transfer: the cells and the four real arrays, each starting on a
+// 16-byte boundary (the pack / unpack kernels then move whole 16-byte groups), and an error word.
 static pic_status staging(pic_ctx* ctx, long long n) {
     const size_t r = ctx->fp64 ? 8 : 4;
-    const size_t need = (((size_t)n * 4 + 15) / 16) * 16 + (size_t)n * 4 * r + 64;  // cells, reals, error word
+    const size_t need = pad16((size_t)n * 4) + 4 * pad16((size_t)n * r) + 64;
     if (ctx->stage_bytes >= need) return PIC_OK;
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     if (ctx->stage) cudaFree(ctx->stage);
@@ -862,6 +866,21 @@ static pic_status staging(pic_ctx* ctx, long long n) {
     return PIC_OK;
 }
 
+// The device address of host memory the GPU can reach directly (pinned and mapped, e.g. from
+// cudaHostAlloc or a registered buffer), or null (pageable memory, or a null pointer). State
+// transfers with such buffers let the pack / unpack kernels read or write them over the host link
+// instead of going through device staging and copies (measured: the link runs at the same rate
+// either way, so this saves the staging pass and the per-array copies).
+static void* mapped(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not a CUDA pointer: clear the error, take the staged path
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t cap, int32_t* c, void* f,
                                     void* vx, void* vy, void* vz, int64_t* n_out) {
     int64_t n = 0;
@@ -870,18 +889,39 @@ extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     if (n_out) *n_out = n;
     if (n > cap) return fail(ctx, PIC_ERR_ARG, "host buffer too small");
     if (n == 0) return PIC_OK;
+    const int grid = std::max(1, std::min(ctx->num_sms * 8, (int)((n + 255) / 256)));
+    {  // every requested array mapped: the unpack kernel writes the caller's arrays directly
+        void* hm[5] = {c, f, vx, vy, vz};
+        bool direct = true;
+        for (int q = 0; q < 5; ++q)
+            if (hm[q]) {
+                hm[q] = mapped(hm[q]);
+                direct = direct && hm[q] != nullptr;
+            }
+        if (direct) {
+            void* const v[4] = {hm[1], hm[2], hm[3], hm[4]};
+            CK(launch_unpack_state(ctx->fp64, ctx->d_discs, ctx->d_ctl, d, sp, ctx->cur, n,
+                                   static_cast<int32_t*>(hm[0]), v, grid, ctx->stream),
+               "state gather");
+            CK(cudaStreamSynchronize(ctx->stream), "state copy");
+            return PIC_OK;
+        }
+    }
     s = staging(ctx, n);
     if (s != PIC_OK) return s;
     const size_t r = ctx->fp64 ? 8 : 4;
     int32_t* sc = static_cast<int32_t*>(ctx->stage);
-    unsigned char* sv = static_cast<unsigned char*>(ctx->stage) + (((size_t)n * 4 + 15) / 16) * 16;
-    const int grid = std::max(1, std::min(ctx->num_sms * 8, (int)((n + 255) / 256)));
-    CK(launch_unpack_state(ctx->fp64, ctx->d_discs, ctx->d_ctl, d, sp, ctx->cur, n, sc, sv, grid, ctx->stream),
-       "state gather");
+    unsigned char* sv = static_cast<unsigned char*>(ctx->stage) + pad16((size_t)n * 4);
+    const size_t sr = pad16((size_t)n * r);
+    {
+        void* const v[4] = {sv, sv + sr, sv + 2 * sr, sv + 3 * sr};
+        CK(launch_unpack_state(ctx->fp64, ctx->d_discs, ctx->d_ctl, d, sp, ctx->cur, n, sc, v, grid, ctx->stream),
+           "state gather");
+    }
     if (c) CK(cudaMemcpyAsync(c, sc, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream), "state c");
     void* outs[4] = {f, vx, vy, vz};
     for (int q = 0; q < 4; ++q)
-        if (outs[q]) CK(cudaMemcpyAsync(outs[q], sv + (size_t)q * n * r, r * (size_t)n, cudaMemcpyDeviceToHost,
+        if (outs[q]) CK(cudaMemcpyAsync(outs[q], sv + q * sr, r * (size_t)n, cudaMemcpyDeviceToHost,
                                         ctx->stream), "state p");
     CK(cudaStreamSynchronize(ctx->stream), "state copy");
     return PIC_OK;
@@ -896,18 +936,29 @@ extern "C" pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     pic_status s = staging(ctx, n > 0 ? n : 1);
     if (s != PIC_OK) return s;
     int32_t* sc = static_cast<int32_t*>(ctx->stage);
-    unsigned char* sv = static_cast<unsigned char*>(ctx->stage) + (((size_t)n * 4 + 15) / 16) * 16;
+    unsigned char* sv = static_cast<unsigned char*>(ctx->stage) + pad16((size_t)n * 4);
+    const size_t sr = pad16((size_t)n * r);
     unsigned* bad = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ctx->stage) + ctx->stage_bytes - 64);
     CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), ctx->stream), "state check");
     if (n) {
-        CK(cudaMemcpyAsync(sc, c, 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream), "state c");
-        const void* ins[4] = {f, vx, vy, vz};
-        for (int q = 0; q < 4; ++q)
-            CK(cudaMemcpyAsync(sv + (size_t)q * n * r, ins[q], r * (size_t)n, cudaMemcpyHostToDevice, ctx->stream),
-               "state p");
         const int grid = std::max(1, std::min(ctx->num_sms * 8, (int)((n + 255) / 256)));
-        CK(launch_pack_state(ctx->fp64, ctx->d_discs, d, sp, ctx->cur, n, sc, sv, bad, grid, ctx->stream),
-           "state pack");
+        const void* hm[5] = {mapped(c), mapped(f), mapped(vx), mapped(vy), mapped(vz)};
+        if (hm[0] && hm[1] && hm[2] && hm[3] && hm[4]) {  // mapped: the pack kernel reads them directly
+            const void* const v[4] = {hm[1], hm[2], hm[3], hm[4]};
+            CK(launch_pack_state(ctx->fp64, ctx->d_discs, d, sp, ctx->cur, n, static_cast<const int32_t*>(hm[0]), v,
+                                 bad, grid, ctx->stream),
+               "state pack");
+        } else {
+            CK(cudaMemcpyAsync(sc, c, 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream), "state c");
+            const void* ins[4] = {f, vx, vy, vz};
+            for (int q = 0; q < 4; ++q)
+                CK(cudaMemcpyAsync(sv + q * sr, ins[q], r * (size_t)n, cudaMemcpyHostToDevice,
+                                   ctx->stream),
+                   "state p");
+            const void* const v[4] = {sv, sv + sr, sv + 2 * sr, sv + 3 * sr};
+            CK(launch_pack_state(ctx->fp64, ctx->d_discs, d, sp, ctx->cur, n, sc, v, bad, grid, ctx->stream),
+               "state pack");
+        }
     }
     // count and dense layout on the device (a rejected upload leaves an empty store), then one
     // synchronisation for the check word

@@ -2073,48 +2073,118 @@ __global__ void k_repack(const Disc* __restrict__ discs, Ctl* __restrict__ ctl, 
     }
 }
 
-// State upload: SoA staging (cells, then f, vx, vy, vz arrays of n reals) ->
-// the store's records; cells outside [0, N) are counted in *bad.
+// 16-byte groups of the SoA arrays of a state transfer: W consecutive particles, their cells in
+// one W-wide integer vector and each real array in one 16-byte vector.
 template <typename T>
-__global__ void k_pack_state(const Disc* __restrict__ discs, int d, int sp, int buf, long long n,
-                             const int32_t* __restrict__ c, const T* __restrict__ sv, unsigned* __restrict__ bad) {
-    const Disc& D = discs[d];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int ci = c[i];
-        if ((unsigned)ci >= (unsigned)D.N) atomicAdd(bad, 1u);
-        store_rec<T>(D.c[buf][sp], D.p[buf][sp], (unsigned)i,
-                     Part<T>{ci, sv[i], sv[n + i], sv[2 * n + i], sv[3 * n + i]});
-    }
+struct XferVec;
+template <>
+struct XferVec<float> {
+    typedef int4 CV;
+    typedef float4 RV;
+    static constexpr int W = 4;
+};
+template <>
+struct XferVec<double> {
+    typedef int2 CV;
+    typedef double2 RV;
+    static constexpr int W = 2;
+};
+
+__device__ __forceinline__ bool aligned16(const void* a, const void* b, const void* c, const void* d,
+                                          const void* e) {
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c) |
+             reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(e)) & 15) == 0;
 }
 
-// State download: the store, read through its layout (regions: binary search of the start table;
-// the dense part by offset), -> SoA staging.
+// State upload: SoA arrays (device staging, or the caller's mapped pinned host arrays) -> the
+// store's records; cells outside [0, N) are counted in *bad. With 16-byte aligned arrays each
+// thread reads whole 16-byte groups (over the host link, wide loads keep more bytes in flight
+// per thread), the ragged tail one by one.
+template <typename T>
+__global__ void k_pack_state(const Disc* __restrict__ discs, int d, int sp, int buf, long long n,
+                             const int32_t* __restrict__ c, const T* __restrict__ f, const T* __restrict__ vx,
+                             const T* __restrict__ vy, const T* __restrict__ vz, unsigned* __restrict__ bad) {
+    typedef XferVec<T> X;
+    const Disc& D = discs[d];
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    const long long groups = aligned16(c, f, vx, vy, vz) ? n / X::W : 0;
+    unsigned nbad = 0;
+    for (long long g = t0; g < groups; g += nt) {
+        const typename X::CV cv = reinterpret_cast<const typename X::CV*>(c)[g];
+        const typename X::RV a = reinterpret_cast<const typename X::RV*>(f)[g];
+        const typename X::RV b = reinterpret_cast<const typename X::RV*>(vx)[g];
+        const typename X::RV e = reinterpret_cast<const typename X::RV*>(vy)[g];
+        const typename X::RV h = reinterpret_cast<const typename X::RV*>(vz)[g];
+        const int* cs = reinterpret_cast<const int*>(&cv);
+        const T *as = reinterpret_cast<const T*>(&a), *bs = reinterpret_cast<const T*>(&b);
+        const T *es = reinterpret_cast<const T*>(&e), *hs = reinterpret_cast<const T*>(&h);
+#pragma unroll
+        for (int k = 0; k < X::W; ++k) {
+            nbad += (unsigned)cs[k] >= (unsigned)D.N;
+            store_rec<T>(D.c[buf][sp], D.p[buf][sp], (unsigned)(g * X::W + k), Part<T>{cs[k], as[k], bs[k], es[k], hs[k]});
+        }
+    }
+    for (long long i = groups * X::W + t0; i < n; i += nt) {
+        const int ci = c[i];
+        nbad += (unsigned)ci >= (unsigned)D.N;
+        store_rec<T>(D.c[buf][sp], D.p[buf][sp], (unsigned)i, Part<T>{ci, f[i], vx[i], vy[i], vz[i]});
+    }
+    if (nbad) atomicAdd(bad, nbad);
+}
+
+// Position i of the state in the store: regions (binary search of the start table; empty regions
+// share their start) and then the dense part by offset.
+__device__ __forceinline__ long long state_slot(const Lay& L, const int* st, int chunk, long long i) {
+    if (i >= L.M) return L.D0 + (i - L.M);
+    int lo = 0, hi = L.K - 1;  // last region with start <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)st[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return (long long)lo * chunk + (i - st[lo]);
+}
+
+// State download: the store, read through its layout -> SoA arrays (device staging, or the
+// caller's mapped pinned host arrays; null outputs are skipped). With 16-byte aligned outputs each
+// thread writes whole 16-byte groups.
 template <typename T>
 __global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl, int d, int sp, int buf,
-                               long long n, int32_t* __restrict__ c, T* __restrict__ sv) {
+                               long long n, int32_t* __restrict__ c, T* __restrict__ f, T* __restrict__ vx,
+                               T* __restrict__ vy, T* __restrict__ vz) {
+    typedef XferVec<T> X;
     const Disc& D = discs[d];
     const Lay L = ctl->lay[d][sp][buf];
     const int* st = D.start[sp];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        long long o;
-        if (i < L.M) {
-            int lo = 0, hi = L.K - 1;  // last region with start <= i (empty regions share their start)
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((long long)st[mid] <= i) lo = mid;
-                else hi = mid - 1;
-            }
-            o = (long long)lo * D.chunk + (i - st[lo]);
-        } else {
-            o = L.D0 + (i - L.M);
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    const long long groups = aligned16(c, f, vx, vy, vz) ? n / X::W : 0;  // null is aligned
+    for (long long g = t0; g < groups; g += nt) {
+        typename X::CV cv;
+        typename X::RV a, b, e, h;
+        int* cs = reinterpret_cast<int*>(&cv);
+        T *as = reinterpret_cast<T*>(&a), *bs = reinterpret_cast<T*>(&b);
+        T *es = reinterpret_cast<T*>(&e), *hs = reinterpret_cast<T*>(&h);
+#pragma unroll
+        for (int k = 0; k < X::W; ++k) {
+            const long long o = state_slot(L, st, D.chunk, g * X::W + k);
+            load_rec<T>(D.p[buf][sp], (unsigned)o, as[k], bs[k], es[k], hs[k]);
+            cs[k] = D.c[buf][sp][o];
         }
-        T f, vx, vy, vz;
-        load_rec<T>(D.p[buf][sp], (unsigned)o, f, vx, vy, vz);
-        c[i] = D.c[buf][sp][o];
-        sv[i] = f;
-        sv[n + i] = vx;
-        sv[2 * n + i] = vy;
-        sv[3 * n + i] = vz;
+        if (c) reinterpret_cast<typename X::CV*>(c)[g] = cv;
+        if (f) reinterpret_cast<typename X::RV*>(f)[g] = a;
+        if (vx) reinterpret_cast<typename X::RV*>(vx)[g] = b;
+        if (vy) reinterpret_cast<typename X::RV*>(vy)[g] = e;
+        if (vz) reinterpret_cast<typename X::RV*>(vz)[g] = h;
+    }
+    for (long long i = groups * X::W + t0; i < n; i += nt) {
+        const long long o = state_slot(L, st, D.chunk, i);
+        T a, b, e, g;
+        load_rec<T>(D.p[buf][sp], (unsigned)o, a, b, e, g);
+        if (c) c[i] = D.c[buf][sp][o];
+        if (f) f[i] = a;
+        if (vx) vx[i] = b;
+        if (vy) vy[i] = e;
+        if (vz) vz[i] = g;
     }
 }
 
@@ -2393,16 +2463,24 @@ cudaError_t launch_repack(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int
 }
 
 cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
-                              const void* sv, unsigned* bad, int grid, cudaStream_t st) {
-    if (fp64) k_pack_state<double><<<grid, 256, 0, st>>>(discs, d, sp, buf, n, c, (const double*)sv, bad);
-    else k_pack_state<float><<<grid, 256, 0, st>>>(discs, d, sp, buf, n, c, (const float*)sv, bad);
+                              const void* const v[4], unsigned* bad, int grid, cudaStream_t st) {
+    if (fp64)
+        k_pack_state<double><<<grid, 256, 0, st>>>(discs, d, sp, buf, n, c, (const double*)v[0], (const double*)v[1],
+                                                   (const double*)v[2], (const double*)v[3], bad);
+    else
+        k_pack_state<float><<<grid, 256, 0, st>>>(discs, d, sp, buf, n, c, (const float*)v[0], (const float*)v[1],
+                                                  (const float*)v[2], (const float*)v[3], bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long n,
-                                int32_t* c, void* sv, int grid, cudaStream_t st) {
-    if (fp64) k_unpack_state<double><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (double*)sv);
-    else k_unpack_state<float><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (float*)sv);
+                                int32_t* c, void* const v[4], int grid, cudaStream_t st) {
+    if (fp64)
+        k_unpack_state<double><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (double*)v[0], (double*)v[1],
+                                                     (double*)v[2], (double*)v[3]);
+    else
+        k_unpack_state<float><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (float*)v[0], (float*)v[1],
+                                                    (float*)v[2], (float*)v[3]);
     return cudaGetLastError();
 }
 
