@@ -272,7 +272,16 @@ const char* pic_status_string(pic_status s);
 /* ---- state access (host buffers; synchronous) --------------------------- */
 pic_status pic_get_count(pic_ctx* ctx, int32_t d, int32_t species, int64_t* n);
 /* Copies the store of (d, species) into host arrays of at least `cap`
- * entries; *n receives the count. Real arrays per the context precision. */
+ * entries (any of them may be null: not copied); *n receives the count.
+ * Real arrays per the context precision. A count above cap returns
+ * PIC_ERR_ARG with the arrays untouched. pic_set_state replaces the store by
+ * n particles (cells c in [0, N), else PIC_ERR_ARG and an empty store; above
+ * the store's capacity PIC_ERR_CAPACITY). Both synchronise the context's
+ * stream before they return. Host arrays in pinned, mapped memory
+ * (cudaHostAlloc, cudaHostRegister, a pinned torch tensor) are read or
+ * written by the device directly over the host link, fastest when each
+ * starts on a 16-byte boundary; pageable arrays go through device staging
+ * and copies. Both ways give the same store, bit for bit.               */
 pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t species, int64_t cap, int32_t* c,
                          void* f, void* vx, void* vy, void* vz, int64_t* n);
 pic_status pic_set_state(pic_ctx* ctx, int32_t d, int32_t species, int64_t n, const int32_t* c,

@@ -520,10 +520,11 @@ extern "C" pic_status pic_batch_create(pic_ctx** out, const pic_gas* gases, int3
         ALLOC(D.D[1], unsigned long long*, 8 * N1);
         ALLOC(D.Q, unsigned long long*, 8 * N1);
         ALLOC(D.Dprev, unsigned long long*, 8 * N1);
-        ALLOC(D.acc_D[0], unsigned __int128*, 16 * N1);
-        ALLOC(D.acc_D[1], unsigned __int128*, 16 * N1);
-        ALLOC(D.acc_Q, unsigned __int128*, 16 * N1);
-        ALLOC(D.acc_Dprev, unsigned __int128*, 16 * N1);
+        // the four exact accumulators in one block (read back by one copy)
+        ALLOC(D.acc_D[0], unsigned __int128*, 4 * 16 * N1);
+        D.acc_D[1] = D.acc_D[0] + N1;
+        D.acc_Q = D.acc_D[0] + 2 * N1;
+        D.acc_Dprev = D.acc_D[0] + 3 * N1;
         ALLOC(D.cnt, unsigned long long*, 8 * NCNT);
         ALLOC(D.period_mean, double*, sizeof(double) * 2 * PERIOD_HIST);
         ctx->hd.push_back(D);
@@ -883,6 +884,30 @@ static void* mapped(const void* p) {
 
 extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t cap, int32_t* c, void* f,
                                     void* vx, void* vy, void* vz, int64_t* n_out) {
+    if (bad_d(ctx, d) || (sp & ~1) || cap < 0) return PIC_ERR_ARG;
+    void* hm[5] = {c, f, vx, vy, vz};
+    bool direct = true;
+    for (int q = 0; q < 5; ++q)
+        if (hm[q]) {
+            hm[q] = mapped(hm[q]);
+            direct = direct && hm[q] != nullptr;
+        }
+    if (direct) {  // every requested array mapped: the unpack kernel writes the caller's arrays
+        // directly, taking the count on the device; one synchronisation for the count
+        pic_status s = pinned(ctx, 64);
+        if (s != PIC_OK) return s;
+        long long* hn = static_cast<long long*>(ctx->h_pin);
+        const int grid = std::max(1, (int)std::min<long long>(ctx->num_sms * 8, (cap + 255) / 256));
+        void* const v[4] = {hm[1], hm[2], hm[3], hm[4]};
+        CK(launch_unpack_state(ctx->fp64, ctx->d_discs, ctx->d_ctl, d, sp, ctx->cur, cap,
+                               static_cast<int32_t*>(hm[0]), v, grid, ctx->stream),
+           "state gather");
+        CK(cudaMemcpyAsync(hn, &ctx->d_ctl->count[d][sp], 8, cudaMemcpyDeviceToHost, ctx->stream), "count");
+        CK(cudaStreamSynchronize(ctx->stream), "state copy");
+        if (n_out) *n_out = *hn;
+        if (*hn > cap) return fail(ctx, PIC_ERR_ARG, "host buffer too small");
+        return PIC_OK;
+    }
     int64_t n = 0;
     pic_status s = pic_get_count(ctx, d, sp, &n);
     if (s != PIC_OK) return s;
@@ -890,23 +915,6 @@ extern "C" pic_status pic_get_state(pic_ctx* ctx, int32_t d, int32_t sp, int64_t
     if (n > cap) return fail(ctx, PIC_ERR_ARG, "host buffer too small");
     if (n == 0) return PIC_OK;
     const int grid = std::max(1, std::min(ctx->num_sms * 8, (int)((n + 255) / 256)));
-    {  // every requested array mapped: the unpack kernel writes the caller's arrays directly
-        void* hm[5] = {c, f, vx, vy, vz};
-        bool direct = true;
-        for (int q = 0; q < 5; ++q)
-            if (hm[q]) {
-                hm[q] = mapped(hm[q]);
-                direct = direct && hm[q] != nullptr;
-            }
-        if (direct) {
-            void* const v[4] = {hm[1], hm[2], hm[3], hm[4]};
-            CK(launch_unpack_state(ctx->fp64, ctx->d_discs, ctx->d_ctl, d, sp, ctx->cur, n,
-                                   static_cast<int32_t*>(hm[0]), v, grid, ctx->stream),
-               "state gather");
-            CK(cudaStreamSynchronize(ctx->stream), "state copy");
-            return PIC_OK;
-        }
-    }
     s = staging(ctx, n);
     if (s != PIC_OK) return s;
     const size_t r = ctx->fp64 ? 8 : 4;
@@ -1092,16 +1100,27 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
     const int N = D.N;
     const size_t N1 = (size_t)N + 1;
     // every read-back of the call into pinned memory, one synchronisation: the four exact
-    // accumulators, the control block and the counters
+    // accumulators (one block), the control block, the counters, the last J(t) and the last
+    // period's current amplitude
     const size_t acc = 16 * N1, o_ctl = 4 * acc, o_cnt = o_ctl + ((sizeof(Ctl) + 15) / 16) * 16;
-    pic_status s = pinned(ctx, o_cnt + 8 * NCNT);
+    const size_t o_j = o_cnt + 8 * NCNT;
+    pic_status s = pinned(ctx, o_j + 3 * sizeof(double));
     if (s != PIC_OK) return s;
     unsigned char* h = static_cast<unsigned char*>(ctx->h_pin);
-    const void* src[4] = {D.acc_D[0], D.acc_D[1], D.acc_Q, D.acc_Dprev};
-    for (int q = 0; q < 4; ++q)
-        CK(cudaMemcpyAsync(h + q * acc, src[q], acc, cudaMemcpyDeviceToHost, ctx->stream), "moments");
+    const int spp = ctx->dis[d].weights.steps_per_period;
+    const long long done = spp > 0 ? ctx->step / spp : 0;
+    double* hj = reinterpret_cast<double*>(h + o_j);
+    hj[0] = hj[1] = hj[2] = 0.0;
+    CK(cudaMemcpyAsync(h, D.acc_D[0], 4 * acc, cudaMemcpyDeviceToHost, ctx->stream), "moments");
     CK(cudaMemcpyAsync(h + o_ctl, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream), "moments");
     CK(cudaMemcpyAsync(h + o_cnt, D.cnt, 8 * NCNT, cudaMemcpyDeviceToHost, ctx->stream), "moments");
+    if (ctx->step > 0) {
+        CK(cudaMemcpyAsync(hj, D.J_hist + 2 * ((ctx->step - 1) % D.jh), 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream), "current");
+        if (done > 0 && D.jtab)
+            CK(cudaMemcpyAsync(hj + 2, D.J_amp + (done - 1) % PERIOD_HIST, sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream), "current amplitude");
+    }
     CK(cudaStreamSynchronize(ctx->stream), "moments");
     const Ctl& hc = *reinterpret_cast<const Ctl*>(h + o_ctl);
     if (hc.error & ERR_TIMEOUT) return fail(ctx, PIC_ERR_TIMEOUT, "a bounded device-side wait timed out");
@@ -1132,15 +1151,13 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
         }
     out->surface_charge = 8.8541878128e-12 * hc.E0_last[d];
     // rf periods, the steady-state criterion on the per-period mean counts, J(t)
-    const int spp = ctx->dis[d].weights.steps_per_period;
-    const long long done = spp > 0 ? ctx->step / spp : 0;
     out->periods_done = done;
     out->steady_period = -1;
     out->steady_metric = -1.0;
     out->steady = 0;
     out->reserved = 0;
-    out->J_amp = 0.0;
-    out->J_last = 0.0;
+    out->J_last = hj[0];
+    out->J_amp = hj[2];
     const long long keep = std::min(done, (long long)PERIOD_HIST);
     if (keep >= 2 * PIC_STEADY_BLOCK) {
         std::vector<double> pm(2 * (size_t)keep);
@@ -1164,18 +1181,6 @@ extern "C" pic_status pic_moments(pic_ctx* ctx, int32_t d, pic_moments_t* out) {
             if (out->steady_period < 0 && metric < PIC_STEADY_TOL) out->steady_period = done - keep + k;
         }
         out->steady = out->steady_period >= 0;
-    }
-    if (ctx->step > 0) {
-        double jl[2] = {0.0, 0.0}, ja = 0.0;
-        const long long n = ctx->step - 1;
-        CK(cudaMemcpyAsync(jl, D.J_hist + 2 * (n % D.jh), 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
-           "current");
-        if (done > 0 && D.jtab)
-            CK(cudaMemcpyAsync(&ja, D.J_amp + (done - 1) % PERIOD_HIST, sizeof(double), cudaMemcpyDeviceToHost,
-                               ctx->stream), "current amplitude");
-        CK(cudaStreamSynchronize(ctx->stream), "current");
-        out->J_last = jl[0];
-        out->J_amp = ja;
     }
     return PIC_OK;
 }
@@ -1238,10 +1243,7 @@ extern "C" pic_status pic_reset_moments(pic_ctx* ctx) {
     for (int d = 0; d < ctx->n_disc; ++d) {
         const Disc& D = ctx->hd[d];
         const size_t b = 16 * ((size_t)D.N + 1);
-        CK(cudaMemset(D.acc_D[0], 0, b), "reset");
-        CK(cudaMemset(D.acc_D[1], 0, b), "reset");
-        CK(cudaMemset(D.acc_Q, 0, b), "reset");
-        CK(cudaMemset(D.acc_Dprev, 0, b), "reset");
+        CK(cudaMemset(D.acc_D[0], 0, 4 * b), "reset");  // the four accumulators, one block
         long long z = 0;
         CK(cudaMemcpy(&ctx->d_ctl->acc_steps[d], &z, 8, cudaMemcpyHostToDevice), "reset");
         pic_status s = read_counters(ctx, d, &ctx->cnt_at_reset[d]);

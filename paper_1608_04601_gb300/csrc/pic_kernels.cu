@@ -2146,14 +2146,17 @@ __device__ __forceinline__ long long state_slot(const Lay& L, const int* st, int
 }
 
 // State download: the store, read through its layout -> SoA arrays (device staging, or the
-// caller's mapped pinned host arrays; null outputs are skipped). With 16-byte aligned outputs each
-// thread writes whole 16-byte groups.
+// caller's mapped pinned host arrays; null outputs are skipped). The count comes from the control
+// block; above cap nothing is written. With 16-byte aligned outputs each thread writes whole
+// 16-byte groups.
 template <typename T>
 __global__ void k_unpack_state(const Disc* __restrict__ discs, const Ctl* __restrict__ ctl, int d, int sp, int buf,
-                               long long n, int32_t* __restrict__ c, T* __restrict__ f, T* __restrict__ vx,
+                               long long cap, int32_t* __restrict__ c, T* __restrict__ f, T* __restrict__ vx,
                                T* __restrict__ vy, T* __restrict__ vz) {
     typedef XferVec<T> X;
     const Disc& D = discs[d];
+    const long long n = ctl->count[d][sp];
+    if (n > cap) return;
     const Lay L = ctl->lay[d][sp][buf];
     const int* st = D.start[sp];
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
@@ -2473,13 +2476,13 @@ cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int bu
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long n,
+cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long cap,
                                 int32_t* c, void* const v[4], int grid, cudaStream_t st) {
     if (fp64)
-        k_unpack_state<double><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (double*)v[0], (double*)v[1],
+        k_unpack_state<double><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, cap, c, (double*)v[0], (double*)v[1],
                                                      (double*)v[2], (double*)v[3]);
     else
-        k_unpack_state<float><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, n, c, (float*)v[0], (float*)v[1],
+        k_unpack_state<float><<<grid, 256, 0, st>>>(discs, ctl, d, sp, buf, cap, c, (float*)v[0], (float*)v[1],
                                                     (float*)v[2], (float*)v[3]);
     return cudaGetLastError();
 }

@@ -33,7 +33,7 @@ cudaError_t launch_repack(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int
 // pinned host memory; a null output array of the unpack is skipped
 cudaError_t launch_pack_state(int fp64, const Disc* discs, int d, int sp, int buf, long long n, const int32_t* c,
                               const void* const v[4], unsigned* bad, int grid, cudaStream_t st);
-cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long n,
+cudaError_t launch_unpack_state(int fp64, const Disc* discs, const Ctl* ctl, int d, int sp, int buf, long long cap,
                                 int32_t* c, void* const v[4], int grid, cudaStream_t st);
 long long sort_tile_chunks(int chunk);
 cudaError_t launch_load_profile(int fp64, const Disc* discs, int n_disc, Ctl* ctl, int buf, unsigned long long seed,

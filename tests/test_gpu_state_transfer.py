@@ -62,3 +62,22 @@ def test_pinned_and_pageable_transfers_agree(P, prec, off):
     sim.step(3)  # and the context steps on
     assert sim.count(0, 0) > 0
     sim.close()
+
+
+def test_pinned_download_too_small_leaves_arrays_untouched(P):
+    from paper_1608_04601_gb300 import _native as NV
+    d = I.discharge(n_cells=64, gap_m=0.025, p_Pa=60.0, V_rf_V=300.0, n_e0=3000, n_i0=3000, n_init_m3=4e14)
+    sim = P.Simulation(X.he_like(eps_max_eV=600.0, de_eV=1e-2), d, precision="fp32", sort_every=0)
+    n = sim.count(0, 0)
+    keep, out = [], {}
+    for k, t in (("c", np.int32), ("f", np.float32), ("vx", np.float32), ("vy", np.float32), ("vz", np.float32)):
+        tt, a = _pinned(n - 1, t)
+        keep.append(tt)
+        a[:] = 7
+        out[k] = a
+    with pytest.raises(NV.PicError):
+        sim.get_state(0, 0, out=out)
+    assert all(np.all(a == 7) for a in out.values())
+    # and the context is still usable
+    assert sim.get_state(0, 0)["c"].size == n
+    sim.close()
