@@ -1,6 +1,6 @@
-// mlp.cu -- the warm-start network: BF16 tensor-core products with FP32
-// accumulation (mma.sync m16n8k16), fused epilogues (bias, tanh, tanh'),
-// MSE loss, Adam; C ABI in include/mlp.h.
+// mlp.cu -- the warm-start network: BF16 products on the tcgen05 tensor cores
+// with FP32 accumulation in tensor memory, fused epilogues (bias, tanh,
+// tanh'), MSE loss, Adam; C ABI in include/mlp.h.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -17,14 +17,24 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 // ---------------------------------------------------------------------------
-// C[M x N] = A(M x K) B(K x N) on the tensor cores. A(m, k) = A[m lda + k]
-// (a_t = 0) or A[k lda + m] (a_t = 1); B(k, n) = B[n ldb + k] (b_t = 0) or
-// B[k ldb + n] (b_t = 1). Tiles of 64 x 64 x 32: four warps of 32 x 32, each
-// 2 x 4 products of 16 x 8 x 16. Operands are staged K-contiguous in shared
-// memory (rows padded by 8 elements against bank conflicts) and read as the
-// documented per-lane fragments: lane (g = lane / 4, t = lane % 4) holds A rows
-// g and g + 8, columns 2t, 2t + 1 (+ 8); B columns n = g, rows 2t, 2t + 1
-// (+ 8); accumulator rows g, g + 8, columns 2t, 2t + 1.
+// C[M x N] = A(M x K) B(K x N) on the 5th-generation tensor cores (tcgen05).
+// A(m, k) = A[m lda + k] (a_t = 0) or A[k lda + m] (a_t = 1); B(k, n) =
+// B[n ldb + k] (b_t = 0) or B[k ldb + n] (b_t = 1).
+//
+// One CTA of 128 threads per 128 x 64 tile of C, K in chunks of 64. The
+// operands of a chunk sit in shared memory K-major without swizzle: 8 x 8 core
+// matrices of 128 contiguous bytes (row r of a core matrix at 16 r bytes),
+// core matrices adjacent in K 128 bytes apart (the descriptor's leading-
+// dimension offset), 8-row groups 1024 bytes apart (its stride offset), zero
+// outside the matrices. Two buffers: while the tensor core multiplies chunk i
+// (one thread issues four tcgen05.mma kind::f16, M 128, N 64, K 16, BF16
+// operands, FP32 accumulator in 64 columns of tensor memory, and commits them
+// to the buffer's mbarrier), the threads already load chunk i + 1 into
+// registers; a buffer is overwritten only after its mbarrier says the products
+// that read it are done (bounded waits). The epilogue reads the accumulator
+// with tcgen05.ld (warp w owns lanes 32 w .. 32 w + 31, the tile's rows),
+// parks it in shared memory and writes C row by row, coalesced, applying the
+// fused bias / tanh / tanh' step.
 enum Epilogue {
     EP_STORE = 0,     // C32 = acc
     EP_BIAS_TANH = 1, // z = acc + bias; C32 = tanh z; C16 = bf16(C32)
@@ -43,110 +53,240 @@ struct GemmArgs {
     float* C32;
     bf16* C16;
     int ldc;
+    unsigned* err;       // set to MLP_ERR_TIMEOUT if a bounded wait gave up
 };
 
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8, GTHREADS = 128;
+constexpr int TBM = 128, TBN = 64, TBK = 64, TTHREADS = 128, TMEM_COLS = 64;
+constexpr unsigned CM_BYTES = 128;                    // one 8 x 8 BF16 core matrix
+constexpr unsigned LBO = CM_BYTES;                    // next core matrix along K
+constexpr unsigned SBO = (TBK / 8) * CM_BYTES;        // next 8-row group
+constexpr unsigned A_BYTES = TBM * TBK * 2, B_BYTES = TBN * TBK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr unsigned GEMM_SMEM = 2 * STAGE_BYTES;       // dynamic shared memory: two operand buffers
+constexpr int UA = TBM * TBK / 8 / TTHREADS, UB = TBN * TBK / 8 / TTHREADS;  // 8-element units per thread
+constexpr int TC_TRIES = 1 << 20;                     // polls of a bounded mbarrier wait
+constexpr unsigned MLP_ERR_TIMEOUT = 1u;
+static_assert((TBN + 1) * TBM * 4 <= GEMM_SMEM, "epilogue tile must fit in the operand buffers");
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                           ((uint32_t)(TBM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t s_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__global__ void __launch_bounds__(GTHREADS) k_gemm(GemmArgs g) {
-    __shared__ __align__(16) bf16 sA[GBM][GBK + GPAD];
-    __shared__ __align__(16) bf16 sB[GBN][GBK + GPAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;  // warp tile (32 x 32) inside the block tile
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    const int gq = lane >> 2, tq = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-    const bf16 zero = __float2bfloat16_rn(0.0f);
+// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading-dimension byte offset
+// / 16 (16-29), stride byte offset / 16 (32-45), the fixed version field 0b001 (46-48), base
+// offset 0, no swizzle (61-63 = 0).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+           (1ull << 46);
+}
 
-    for (int k0 = 0; k0 < g.K; k0 += GBK) {
-        // stage A (GBM x GBK) and B (GBN x GBK), K-contiguous, zero outside the matrices
-        for (int e = tid; e < GBM * GBK; e += GTHREADS) {
-            int r, c;
-            if (g.a_t) {  // consecutive threads walk m (contiguous in memory)
-                r = e % GBM;
-                c = e / GBM;
-            } else {
-                r = e / GBK;
-                c = e % GBK;
-            }
-            const int m = m0 + r, k = k0 + c;
-            bf16 v = zero;
-            if (m < g.M && k < g.K) v = g.a_t ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
-            sA[r][c] = v;
-        }
-        for (int e = tid; e < GBN * GBK; e += GTHREADS) {
-            int r, c;
-            if (g.b_t) {
-                r = e % GBN;
-                c = e / GBN;
-            } else {
-                r = e / GBK;
-                c = e % GBK;
-            }
-            const int n = n0 + r, k = k0 + c;
-            bf16 v = zero;
-            if (n < g.N && k < g.K) v = g.b_t ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
-            sB[r][c] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GBK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm * 32 + i * 16 + gq;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&sA[r][kk + 2 * tq]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][kk + 2 * tq]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&sA[r][kk + 2 * tq + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][kk + 2 * tq + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn * 32 + j * 8 + gq;
-                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&sB[c][kk + 2 * tq]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&sB[c][kk + 2 * tq + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
+// Byte offset of element (row r, k) of a staged operand tile.
+__device__ __forceinline__ unsigned cm_off(int r, int k) {
+    return (unsigned)(((r >> 3) * (TBK / 8) + (k >> 3)) * CM_BYTES + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mb, unsigned parity) {
+    for (int it = 0; it < TC_TRIES; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
-    // epilogue
+    return false;
+}
+
+__device__ __forceinline__ bool vec_ok(const bf16* X, int ld, int t) {
+    return !t && (ld % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
+// Unit u of a tile (8 consecutive k of one row): its row and 8-column group. 16-byte loads
+// (vec): the eight lanes of a quarter warp take the eight rows of one core matrix (its 128 bytes
+// in one conflict-free store), the next eight lanes the next 8 k of the same rows. Element
+// gathers: consecutive lanes take consecutive rows (contiguous in memory when transposed).
+template <int R>
+__device__ __forceinline__ void unit_rk(int u, bool vec, int& r, int& kc) {
+    if (vec) {
+        r = (u >> 6) * 8 + (u & 7);
+        kc = (u >> 3) & 7;
+    } else {
+        r = u % R;
+        kc = u / R;
+    }
+}
+
+// Loads this thread's units of the chunk at k0 of an operand X (rows x K; element (r, k) at
+// X[r ld + k], or X[k ld + r] if t) into registers, 8 BF16 per uint4, zero outside.
+template <int R, int U>
+__device__ __forceinline__ void load_units(uint4 (&v)[U], const bf16* __restrict__ X, int ld, int t, int rows, int K,
+                                           int r0, int k0, bool vec) {
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int q = 0; q < U; ++q) {
+        int r, kc;
+        unit_rk<R>((int)threadIdx.x + q * TTHREADS, vec, r, kc);
+        const int m = r0 + r, k = k0 + 8 * kc;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (m < rows) {
+            if (vec && k + 8 <= K) {
+                const uint4 x = *reinterpret_cast<const uint4*>(X + (size_t)m * ld + k);
+                w[0] = x.x;
+                w[1] = x.y;
+                w[2] = x.z;
+                w[3] = x.w;
+            } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 8; ++j)
+                    if (k + j < K) {
+                        const bf16 e = t ? X[(size_t)(k + j) * ld + m] : X[(size_t)m * ld + k + j];
+                        w[j >> 1] |= (uint32_t)__bfloat16_as_ushort(e) << (16 * (j & 1));
+                    }
+            }
+        }
+        v[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+template <int R, int U>
+__device__ __forceinline__ void store_units(unsigned char* s, const uint4 (&v)[U], bool vec) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm * 32 + i * 16 + gq + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + j * 8 + 2 * tq + (r & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[i][j][r];
+    for (int q = 0; q < U; ++q) {
+        int r, kc;
+        unit_rk<R>((int)threadIdx.x + q * TTHREADS, vec, r, kc);
+        *reinterpret_cast<uint4*>(s + cm_off(r, 8 * kc)) = v[q];
+    }
+}
+
+__global__ void __launch_bounds__(TTHREADS) k_gemm(GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem[];  // two buffers of A (128 x 64) then B (64 x 64)
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    const uint32_t mb0 = s_addr(&mbar[0]);  // buffer b's barrier at mb0 + 8 b
+    if (warp == 0) {  // tensor memory for the accumulator: one warp allocates, the same warp frees
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const bool va = vec_ok(g.A, g.lda, g.a_t), vb = vec_ok(g.B, g.ldb, g.b_t);
+    const int nk = (g.K + TBK - 1) / TBK;
+    uint4 ra[UA], rb[UB];
+    load_units<TBM, UA>(ra, g.A, g.lda, g.a_t, g.M, g.K, m0, 0, va);
+    load_units<TBN, UB>(rb, g.B, g.ldb, g.b_t, g.N, g.K, n0, 0, vb);
+    bool ok = true;
+    int last = -1;  // last chunk whose products were committed
+    for (int i = 0; i < nk; ++i) {
+        const int b = i & 1;
+        // buffer b last held chunk i - 2: its products must be done before it is overwritten
+        const bool done = i < 2 || tc_wait(mb0 + 8u * b, (((unsigned)i >> 1) & 1u) ^ 1u);
+        if (__syncthreads_or(!done)) {  // one decision for the whole CTA
+            ok = false;
+            break;
+        }
+        unsigned char* sa = smem + b * STAGE_BYTES;
+        store_units<TBM, UA>(sa, ra, va);
+        store_units<TBN, UB>(sa + A_BYTES, rb, vb);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, to the tensor core's proxy
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = s_addr(sa), b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int s = 0; s < TBK / 16; ++s) {  // K 16 per instruction: two core matrices along K
+                const uint64_t ad = sdesc(a0 + 2 * s * CM_BYTES), bd = sdesc(b0 + 2 * s * CM_BYTES);
+                const uint32_t accumulate = (i > 0 || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb0 + 8u * b)
+                         : "memory");
+        }
+        last = i;
+        if (i + 1 < nk) {  // the next chunk's loads overlap the products just issued
+            load_units<TBM, UA>(ra, g.A, g.lda, g.a_t, g.M, g.K, m0, (i + 1) * TBK, va);
+            load_units<TBN, UB>(rb, g.B, g.ldb, g.b_t, g.N, g.K, n0, (i + 1) * TBK, vb);
+        }
+    }
+    if (ok) {  // the last commit covers every product issued before it
+        const bool done = tc_wait(mb0 + 8u * (last & 1), ((unsigned)last >> 1) & 1u);
+        if (__syncthreads_or(!done)) ok = false;
+    }
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // accumulator -> shared tile T[128][65] (thread = row: conflict-free with the odd stride)
+        float* T = reinterpret_cast<float*>(smem);
+        const int row = warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < TBN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) T[row * (TBN + 1) + c0 + j] = __uint_as_float(r[j]);
+        }
+        __syncthreads();
+        // row by row: a warp writes 32 consecutive columns of one row. Each thread keeps one column
+        // (its bias loaded once) and takes every second row; the loads of a batch of rows (yprev)
+        // are all issued before its stores, which the compiler could not reorder (aliasing).
+        const int cc = tid % TBN, rb = tid / TBN, n = n0 + cc;
+        const bool nin = n < g.N;
+        const float bn = (nin && (g.ep == EP_BIAS_TANH || g.ep == EP_BIAS)) ? g.bias[n] : 0.0f;
+        constexpr int RSTEP = TTHREADS / TBN, BATCH = 16;
+#pragma unroll 1
+        for (int r0 = rb; r0 < TBM; r0 += RSTEP * BATCH) {
+            float y[BATCH];
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                const int m = m0 + r0 + RSTEP * j;
+                y[j] = (g.ep == EP_DTANH && nin && m < g.M) ? g.yprev[(size_t)m * g.ldc + n] : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                const int rr = r0 + RSTEP * j, m = m0 + rr;
+                if (!nin || m >= g.M) continue;
+                float v = T[rr * (TBN + 1) + cc];
+                if (g.ep == EP_BIAS_TANH) v = tanhf(v + bn);
+                else if (g.ep == EP_BIAS) v = v + bn;
+                else if (g.ep == EP_DTANH) v = v * (1.0f - y[j] * y[j]);
                 const size_t o = (size_t)m * g.ldc + n;
-                if (g.ep == EP_BIAS_TANH) v = tanhf(v + g.bias[n]);
-                else if (g.ep == EP_BIAS) v = v + g.bias[n];
-                else if (g.ep == EP_DTANH) {
-                    const float y = g.yprev[o];
-                    v = v * (1.0f - y * y);
-                }
                 g.C32[o] = v;
                 if (g.C16) g.C16[o] = __float2bfloat16_rn(v);
             }
+        }
+    } else if (tid == 0) {
+        atomicOr(g.err, MLP_ERR_TIMEOUT);
+        if (last >= 0) tc_wait(mb0 + 8u * (last & 1), ((unsigned)last >> 1) & 1u);  // a last bounded chance for the products in flight
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // Column sums of g[rows x cols] (bias gradients), fixed order per column.
@@ -241,6 +381,7 @@ struct mlp_ctx {
     float* g32[2] = {};
     bf16* g16[2] = {};
     float* loss = nullptr;
+    unsigned* d_err = nullptr;  // device word: a product's bounded wait gave up
     long long step = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -270,12 +411,22 @@ bool dalloc(mlp_ctx* c, T** p, size_t n) {
     return true;
 }
 
-cudaError_t gemm(cudaStream_t st, const bf16* A, int lda, int a_t, const bf16* B, int ldb, int b_t, int M, int N, int K,
+cudaError_t gemm(mlp_ctx* c, const bf16* A, int lda, int a_t, const bf16* B, int ldb, int b_t, int M, int N, int K,
                  int ep, const float* bias, const float* yprev, float* C32, bf16* C16, int ldc) {
-    GemmArgs g{A, B, lda, ldb, a_t, b_t, M, N, K, ep, bias, yprev, C32, C16, ldc};
-    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-    k_gemm<<<grid, GTHREADS, 0, st>>>(g);
+    GemmArgs g{A, B, lda, ldb, a_t, b_t, M, N, K, ep, bias, yprev, C32, C16, ldc, c->d_err};
+    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
+    k_gemm<<<grid, TTHREADS, GEMM_SMEM, c->stream>>>(g);
     return cudaGetLastError();
+}
+
+// Synchronises the context's stream and reports a product whose bounded wait gave up.
+pic_status sync_checked(mlp_ctx* c, const char* what) {
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, what, e);
+    if (h) return fail(c, PIC_ERR_TIMEOUT, "a tensor-core product's bounded wait timed out");
+    return PIC_OK;
 }
 
 int grid_for(long long n) {
@@ -298,7 +449,7 @@ cudaError_t forward(mlp_ctx* c, int batch, const float* x) {
     for (int l = 0; l < c->L && e == cudaSuccess; ++l) {
         const int in = c->sizes[l], out = c->sizes[l + 1];
         const bf16* A = l == 0 ? c->x16 : c->y16[l - 1];
-        e = gemm(c->stream, A, in, 0, c->w16 + c->w16off[l], in, 0, batch, out, in,
+        e = gemm(c, A, in, 0, c->w16 + c->w16off[l], in, 0, batch, out, in,
                  l + 1 < c->L ? EP_BIAS_TANH : EP_BIAS, c->p + c->boff[l], nullptr, c->y32[l], c->y16[l], out);
     }
     return e;
@@ -314,6 +465,10 @@ pic_status mlp_create(mlp_ctx** out, int32_t n_layers, const int32_t* sizes, int
     *out = nullptr;
     for (int l = 0; l <= n_layers; ++l)
         if (sizes[l] < 1 || sizes[l] > MLP_MAX_WIDTH) return PIC_ERR_ARG;
+    // the product's two operand buffers take 48 KB of dynamic shared memory (above the default limit
+    // together with its barriers)
+    if (cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess)
+        return PIC_ERR_CUDA;
     mlp_ctx* c = new mlp_ctx();
     c->L = n_layers;
     c->max_batch = max_batch;
@@ -342,7 +497,7 @@ pic_status mlp_create(mlp_ctx** out, int32_t n_layers, const int32_t* sizes, int
     const size_t P = (size_t)c->n_params;
     bool ok = dalloc(c, &c->p, P) && dalloc(c, &c->grad, P) && dalloc(c, &c->m, P) && dalloc(c, &c->v, P) &&
               dalloc(c, &c->w16, (size_t)c->n_w) && dalloc(c, &c->x16, (size_t)max_batch * sizes[0]) &&
-              dalloc(c, &c->loss, 1);
+              dalloc(c, &c->loss, 1) && dalloc(c, &c->d_err, 1);
     for (int l = 0; l < n_layers && ok; ++l)
         ok = dalloc(c, &c->y32[l], (size_t)max_batch * sizes[l + 1]) && dalloc(c, &c->y16[l], (size_t)max_batch * sizes[l + 1]);
     for (int b = 0; b < 2 && ok; ++b)
@@ -354,6 +509,7 @@ pic_status mlp_create(mlp_ctx** out, int32_t n_layers, const int32_t* sizes, int
     cudaMemsetAsync(c->m, 0, P * sizeof(float), c->stream);
     cudaMemsetAsync(c->v, 0, P * sizeof(float), c->stream);
     cudaMemsetAsync(c->grad, 0, P * sizeof(float), c->stream);
+    cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
     for (int l = 0; l < n_layers; ++l) {
         const long long nw = (long long)sizes[l] * sizes[l + 1];
         const float a = std::sqrt(6.0f / (float)(sizes[l] + sizes[l + 1]));
@@ -382,8 +538,7 @@ pic_status mlp_set_params(mlp_ctx* c, const float* host) {
 pic_status mlp_get_params(mlp_ctx* c, float* host) {
     if (!c || !host) return PIC_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(host, c->p, sizeof(float) * (size_t)c->n_params, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? PIC_OK : fail(c, PIC_ERR_CUDA, "get params", e);
+    return e == cudaSuccess ? sync_checked(c, "get params") : fail(c, PIC_ERR_CUDA, "get params", e);
 }
 
 pic_status mlp_forward(mlp_ctx* c, int32_t batch, const float* x, float* y) {
@@ -408,14 +563,14 @@ pic_status mlp_loss_grad(mlp_ctx* c, int32_t batch, const float* x, const float*
         const int in = c->sizes[l], out = c->sizes[l + 1];
         const bf16* X = l == 0 ? c->x16 : c->y16[l - 1];
         // dW_l = G^T X: M = out, N = in, K = batch
-        e = gemm(c->stream, c->g16[cur], out, 1, X, in, 1, out, in, batch, EP_STORE, nullptr, nullptr,
+        e = gemm(c, c->g16[cur], out, 1, X, in, 1, out, in, batch, EP_STORE, nullptr, nullptr,
                  c->grad + c->woff[l], nullptr, in);
         if (e != cudaSuccess) break;
         k_colsum<<<(out + 255) / 256, 256, 0, c->stream>>>(c->g32[cur], batch, out, c->grad + c->boff[l]);
         e = cudaGetLastError();
         if (e != cudaSuccess || l == 0) break;
         // G_{l-1} = (G W_l) * (1 - y_{l-1}^2): M = batch, N = in, K = out
-        e = gemm(c->stream, c->g16[cur], out, 0, c->w16 + c->w16off[l], in, 1, batch, in, out, EP_DTANH, nullptr,
+        e = gemm(c, c->g16[cur], out, 0, c->w16 + c->w16off[l], in, 1, batch, in, out, EP_DTANH, nullptr,
                  c->y32[l - 1], c->g32[1 - cur], c->g16[1 - cur], in);
         cur = 1 - cur;
     }
@@ -426,8 +581,7 @@ pic_status mlp_get_grads(mlp_ctx* c, float* host) {
     if (!c || !host) return PIC_ERR_ARG;
     cudaError_t e =
         cudaMemcpyAsync(host, c->grad, sizeof(float) * (size_t)c->n_params, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? PIC_OK : fail(c, PIC_ERR_CUDA, "get grads", e);
+    return e == cudaSuccess ? sync_checked(c, "get grads") : fail(c, PIC_ERR_CUDA, "get grads", e);
 }
 
 pic_status mlp_adam(mlp_ctx* c, float lr, float beta1, float beta2, float eps) {
@@ -450,8 +604,7 @@ pic_status mlp_train_step(mlp_ctx* c, int32_t batch, const float* x, const float
 
 pic_status mlp_sync(mlp_ctx* c) {
     if (!c) return PIC_ERR_ARG;
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? PIC_OK : fail(c, PIC_ERR_CUDA, "synchronize", e);
+    return sync_checked(c, "synchronize");
 }
 
 void mlp_destroy(mlp_ctx* c) {
