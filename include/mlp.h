@@ -8,8 +8,9 @@
  *
  * A multilayer perceptron: layer l computes z_l = y_{l-1} W_l^T + b_l with
  * W_l [out_l x in_l]; hidden layers apply tanh, the last layer is linear.
- * Weights are BF16 copies of FP32 master weights; every product accumulates in
- * FP32 on the tensor cores; activations feed the next product as BF16.
+ * Weights are BF16 copies of FP32 master weights; every product runs on the
+ * tcgen05 tensor cores (BF16 operands from shared memory, FP32 accumulator in
+ * tensor memory); activations feed the next product as BF16.
  * Training minimises the mean squared error over the outputs with Adam.
  *
  * Memory: the context owns all device memory (weights, Adam moments,
@@ -20,7 +21,9 @@
  * Parameter layout (host arrays): for each layer in order, W_l row-major
  * [out_l][in_l], then b_l [out_l].
  * Errors: PIC_ERR_ARG for bad sizes or pointers, PIC_ERR_CUDA for CUDA
- * failures (text in mlp_last_error).                                        */
+ * failures (text in mlp_last_error); PIC_ERR_TIMEOUT from mlp_sync,
+ * mlp_get_params or mlp_get_grads if a product's bounded wait on the tensor
+ * core gave up (its outputs are then not written).                          */
 #ifndef MLP_H
 #define MLP_H
 

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -102,38 +103,94 @@ __device__ __forceinline__ bool tc_wait(uint32_t mb, unsigned parity) {
     return false;
 }
 
-__device__ __forceinline__ bool vec_ok(const bf16* X, int ld, int t) {
-    return !t && (ld % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+// How a thread moves an operand: element gathers (any layout and alignment), 16-byte loads of
+// k-contiguous rows, or (transposed operand, m contiguous) 16- / 8-byte loads of 8 rows of k that
+// the thread transposes in registers.
+enum StageMode { SM_GATHER = 0, SM_VEC = 1, SM_TVEC = 2 };
+
+// Chosen on the host per operand; the product kernel is compiled for each pair of modes.
+inline int stage_mode(const void* X, int ld, int t) {
+    if ((ld % 8) != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return SM_GATHER;
+    return t ? SM_TVEC : SM_VEC;
 }
 
-// Unit u of a tile (8 consecutive k of one row): its row and 8-column group. 16-byte loads
-// (vec): the eight lanes of a quarter warp take the eight rows of one core matrix (its 128 bytes
-// in one conflict-free store), the next eight lanes the next 8 k of the same rows. Element
-// gathers: consecutive lanes take consecutive rows (contiguous in memory when transposed).
-template <int R>
-__device__ __forceinline__ void unit_rk(int u, bool vec, int& r, int& kc) {
-    if (vec) {
+// Unit q of this thread (8 consecutive k of one row of the tile): its row and 8-column group.
+// SM_VEC: the eight lanes of a quarter warp take the eight rows of one core matrix (its 128 bytes
+// in one conflict-free store), the next eight lanes the next 8 k of the same rows. SM_GATHER:
+// consecutive lanes take consecutive rows. SM_TVEC: the thread owns the U rows U (tid % (R / U))
+// .. + U - 1 at the 8 k of group tid / (R / U), unit q being its row q.
+template <int R, int U, int MODE>
+__device__ __forceinline__ void unit_rk(int q, int& r, int& kc) {
+    const int tid = threadIdx.x, u = tid + q * TTHREADS;
+    if constexpr (MODE == SM_VEC) {
         r = (u >> 6) * 8 + (u & 7);
         kc = (u >> 3) & 7;
+    } else if constexpr (MODE == SM_TVEC) {
+        r = U * (tid % (R / U)) + q;
+        kc = tid / (R / U);
     } else {
         r = u % R;
         kc = u / R;
     }
 }
 
+// One k row of a transposed block: U consecutive BF16 (rows m .. m + U - 1) as U / 2 words.
+template <int U>
+__device__ __forceinline__ void load_row(uint32_t (&w)[U / 2], const bf16* src, int avail) {
+#pragma unroll
+    for (int p = 0; p < U / 2; ++p) w[p] = 0u;
+    if (avail >= U) {
+        if constexpr (U == 8) {
+            const uint4 x = *reinterpret_cast<const uint4*>(src);
+            w[0] = x.x;
+            w[1] = x.y;
+            w[2] = x.z;
+            w[3] = x.w;
+        } else {
+            const uint2 x = *reinterpret_cast<const uint2*>(src);
+            w[0] = x.x;
+            w[1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < U; ++e)
+            if (e < avail) w[e >> 1] |= (uint32_t)__bfloat16_as_ushort(src[e]) << (16 * (e & 1));
+    }
+}
+
 // Loads this thread's units of the chunk at k0 of an operand X (rows x K; element (r, k) at
-// X[r ld + k], or X[k ld + r] if t) into registers, 8 BF16 per uint4, zero outside.
-template <int R, int U>
+// X[r ld + k], or X[k ld + r] if t) into registers, 8 BF16 per uint4 (k ascending), zero outside.
+template <int R, int U, int MODE>
 __device__ __forceinline__ void load_units(uint4 (&v)[U], const bf16* __restrict__ X, int ld, int t, int rows, int K,
-                                           int r0, int k0, bool vec) {
+                                           int r0, int k0) {
+    static_assert(U == 4 || U == 8, "a transposed block is 8 k by 4 or 8 rows");
+    if constexpr (MODE == SM_TVEC) {
+        int r, kc;
+        unit_rk<R, U, MODE>(0, r, kc);
+        const int m = r0 + r;  // first of the thread's U rows (a multiple of U)
+        uint32_t w[8][U / 2];  // w[i]: rows m .. m + U - 1 at k = k0 + 8 kc + i
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = k0 + 8 * kc + i;
+            load_row<U>(w[i], X + (size_t)k * ld + m, k < K ? rows - m : 0);
+        }
+        // transpose: unit j (row m + j) word p holds k = 2p (low half) and 2p + 1 (high half)
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const unsigned sel = (j & 1) ? 0x7632u : 0x5410u;
+            v[j] = make_uint4(__byte_perm(w[0][j >> 1], w[1][j >> 1], sel), __byte_perm(w[2][j >> 1], w[3][j >> 1], sel),
+                              __byte_perm(w[4][j >> 1], w[5][j >> 1], sel), __byte_perm(w[6][j >> 1], w[7][j >> 1], sel));
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
         int r, kc;
-        unit_rk<R>((int)threadIdx.x + q * TTHREADS, vec, r, kc);
+        unit_rk<R, U, MODE>(q, r, kc);
         const int m = r0 + r, k = k0 + 8 * kc;
         uint32_t w[4] = {0u, 0u, 0u, 0u};
         if (m < rows) {
-            if (vec && k + 8 <= K) {
+            if (MODE == SM_VEC && k + 8 <= K) {
                 const uint4 x = *reinterpret_cast<const uint4*>(X + (size_t)m * ld + k);
                 w[0] = x.x;
                 w[1] = x.y;
@@ -152,16 +209,17 @@ __device__ __forceinline__ void load_units(uint4 (&v)[U], const bf16* __restrict
     }
 }
 
-template <int R, int U>
-__device__ __forceinline__ void store_units(unsigned char* s, const uint4 (&v)[U], bool vec) {
+template <int R, int U, int MODE>
+__device__ __forceinline__ void store_units(unsigned char* s, const uint4 (&v)[U]) {
 #pragma unroll
     for (int q = 0; q < U; ++q) {
         int r, kc;
-        unit_rk<R>((int)threadIdx.x + q * TTHREADS, vec, r, kc);
+        unit_rk<R, U, MODE>(q, r, kc);
         *reinterpret_cast<uint4*>(s + cm_off(r, 8 * kc)) = v[q];
     }
 }
 
+template <int MA, int MB>  // staging modes of A and B
 __global__ void __launch_bounds__(TTHREADS) k_gemm(GemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];  // two buffers of A (128 x 64) then B (64 x 64)
     __shared__ __align__(8) unsigned long long mbar[2];
@@ -184,11 +242,10 @@ __global__ void __launch_bounds__(TTHREADS) k_gemm(GemmArgs g) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const bool va = vec_ok(g.A, g.lda, g.a_t), vb = vec_ok(g.B, g.ldb, g.b_t);
     const int nk = (g.K + TBK - 1) / TBK;
     uint4 ra[UA], rb[UB];
-    load_units<TBM, UA>(ra, g.A, g.lda, g.a_t, g.M, g.K, m0, 0, va);
-    load_units<TBN, UB>(rb, g.B, g.ldb, g.b_t, g.N, g.K, n0, 0, vb);
+    load_units<TBM, UA, MA>(ra, g.A, g.lda, g.a_t, g.M, g.K, m0, 0);
+    load_units<TBN, UB, MB>(rb, g.B, g.ldb, g.b_t, g.N, g.K, n0, 0);
     bool ok = true;
     int last = -1;  // last chunk whose products were committed
     for (int i = 0; i < nk; ++i) {
@@ -200,8 +257,8 @@ __global__ void __launch_bounds__(TTHREADS) k_gemm(GemmArgs g) {
             break;
         }
         unsigned char* sa = smem + b * STAGE_BYTES;
-        store_units<TBM, UA>(sa, ra, va);
-        store_units<TBN, UB>(sa + A_BYTES, rb, vb);
+        store_units<TBM, UA, MA>(sa, ra);
+        store_units<TBN, UB, MB>(sa + A_BYTES, rb);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, to the tensor core's proxy
         __syncthreads();
         if (tid == 0) {
@@ -222,8 +279,8 @@ __global__ void __launch_bounds__(TTHREADS) k_gemm(GemmArgs g) {
         }
         last = i;
         if (i + 1 < nk) {  // the next chunk's loads overlap the products just issued
-            load_units<TBM, UA>(ra, g.A, g.lda, g.a_t, g.M, g.K, m0, (i + 1) * TBK, va);
-            load_units<TBN, UB>(rb, g.B, g.ldb, g.b_t, g.N, g.K, n0, (i + 1) * TBK, vb);
+            load_units<TBM, UA, MA>(ra, g.A, g.lda, g.a_t, g.M, g.K, m0, (i + 1) * TBK);
+            load_units<TBN, UB, MB>(rb, g.B, g.ldb, g.b_t, g.N, g.K, n0, (i + 1) * TBK);
         }
     }
     if (ok) {  // the last commit covers every product issued before it
@@ -289,13 +346,23 @@ __global__ void __launch_bounds__(TTHREADS) k_gemm(GemmArgs g) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-// Column sums of g[rows x cols] (bias gradients), fixed order per column.
-__global__ void k_colsum(const float* __restrict__ g, int rows, int cols, float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += g[(size_t)r * cols + c];
-    out[c] = s;
+// Column sums of g[rows x cols] (bias gradients): a block of 32 columns x 8 row groups, each
+// thread summing every eighth row, then the eight partial sums in order (a fixed order per column).
+__global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ g, int rows, int cols,
+                                                float* __restrict__ out) {
+    __shared__ float s[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x, gy = threadIdx.y;
+    float acc = 0.0f;
+    if (c < cols)
+        for (int r = gy; r < rows; r += 8) acc += g[(size_t)r * cols + c];
+    s[gy][threadIdx.x] = acc;
+    __syncthreads();
+    if (gy == 0 && c < cols) {
+        float t = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += s[k][threadIdx.x];
+        out[c] = t;
+    }
 }
 
 __global__ void k_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, long long n) {
@@ -303,28 +370,42 @@ __global__ void k_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, lon
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
-// Mean squared error over n = rows x cols values and its gradient 2 (y - t) / n
-// (FP32 and BF16); one block, fixed reduction order.
-__global__ void __launch_bounds__(1024) k_mse(const float* __restrict__ y, const float* __restrict__ t, long long n,
-                                              float* __restrict__ g32, bf16* __restrict__ g16, float* __restrict__ loss) {
-    __shared__ float s_w[32];
+// Sum of a block's values in a fixed tree (warp shuffles, then the warps' sums); thread 0 gets it.
+__device__ __forceinline__ float block_sum256(float v) {
+    __shared__ float s_w[8];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) t += s_w[k];
+    return t;
+}
+
+// Mean squared error over n = rows x cols values and its gradient 2 (y - t) / n (FP32 and BF16):
+// each block strides over the values and leaves its partial sum; k_mse_final adds the partial sums
+// in order (the grid depends on n only, so the reduction order is fixed).
+constexpr int MSE_BLOCKS = 256;
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ y, const float* __restrict__ t, long long n,
+                                             float* __restrict__ g32, bf16* __restrict__ g16,
+                                             float* __restrict__ part) {
     const float sc = 2.0f / (float)n;
     float acc = 0.0f;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
         const float d = y[i] - t[i];
         acc += d * d;
         const float gv = sc * d;
         g32[i] = gv;
         g16[i] = __float2bfloat16_rn(gv);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float v = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0.0f;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-        if (threadIdx.x == 0) *loss = v / (float)n;
-    }
+    const float b = block_sum256(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+__global__ void __launch_bounds__(256) k_mse_final(const float* __restrict__ part, int nb, long long n,
+                                                   float* __restrict__ loss) {
+    const float b = block_sum256(threadIdx.x < nb ? part[threadIdx.x] : 0.0f);
+    if (threadIdx.x == 0) *loss = b / (float)n;
 }
 
 // Adam on the FP32 master parameters; refreshes the BF16 weight copies
@@ -381,6 +462,7 @@ struct mlp_ctx {
     float* g32[2] = {};
     bf16* g16[2] = {};
     float* loss = nullptr;
+    float* mse_part = nullptr;  // per-block partial sums of the loss
     unsigned* d_err = nullptr;  // device word: a product's bounded wait gave up
     long long step = 0;
     cudaStream_t stream = nullptr;
@@ -411,11 +493,20 @@ bool dalloc(mlp_ctx* c, T** p, size_t n) {
     return true;
 }
 
+typedef void (*GemmKernel)(GemmArgs);
+GemmKernel gemm_kernel(int ma, int mb) {
+    static const GemmKernel K[3][3] = {
+        {k_gemm<SM_GATHER, SM_GATHER>, k_gemm<SM_GATHER, SM_VEC>, k_gemm<SM_GATHER, SM_TVEC>},
+        {k_gemm<SM_VEC, SM_GATHER>, k_gemm<SM_VEC, SM_VEC>, k_gemm<SM_VEC, SM_TVEC>},
+        {k_gemm<SM_TVEC, SM_GATHER>, k_gemm<SM_TVEC, SM_VEC>, k_gemm<SM_TVEC, SM_TVEC>}};
+    return K[ma][mb];
+}
+
 cudaError_t gemm(mlp_ctx* c, const bf16* A, int lda, int a_t, const bf16* B, int ldb, int b_t, int M, int N, int K,
                  int ep, const float* bias, const float* yprev, float* C32, bf16* C16, int ldc) {
     GemmArgs g{A, B, lda, ldb, a_t, b_t, M, N, K, ep, bias, yprev, C32, C16, ldc, c->d_err};
     dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
-    k_gemm<<<grid, TTHREADS, GEMM_SMEM, c->stream>>>(g);
+    gemm_kernel(stage_mode(A, lda, a_t), stage_mode(B, ldb, b_t))<<<grid, TTHREADS, GEMM_SMEM, c->stream>>>(g);
     return cudaGetLastError();
 }
 
@@ -467,8 +558,11 @@ pic_status mlp_create(mlp_ctx** out, int32_t n_layers, const int32_t* sizes, int
         if (sizes[l] < 1 || sizes[l] > MLP_MAX_WIDTH) return PIC_ERR_ARG;
     // the product's two operand buffers take 48 KB of dynamic shared memory (above the default limit
     // together with its barriers)
-    if (cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess)
-        return PIC_ERR_CUDA;
+    for (int ma = 0; ma < 3; ++ma)
+        for (int mb = 0; mb < 3; ++mb)
+            if (cudaFuncSetAttribute(gemm_kernel(ma, mb), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) !=
+                cudaSuccess)
+                return PIC_ERR_CUDA;
     mlp_ctx* c = new mlp_ctx();
     c->L = n_layers;
     c->max_batch = max_batch;
@@ -497,7 +591,8 @@ pic_status mlp_create(mlp_ctx** out, int32_t n_layers, const int32_t* sizes, int
     const size_t P = (size_t)c->n_params;
     bool ok = dalloc(c, &c->p, P) && dalloc(c, &c->grad, P) && dalloc(c, &c->m, P) && dalloc(c, &c->v, P) &&
               dalloc(c, &c->w16, (size_t)c->n_w) && dalloc(c, &c->x16, (size_t)max_batch * sizes[0]) &&
-              dalloc(c, &c->loss, 1) && dalloc(c, &c->d_err, 1);
+              dalloc(c, &c->loss, 1) && dalloc(c, &c->d_err, 1) &&
+              dalloc(c, &c->mse_part, (size_t)MSE_BLOCKS);
     for (int l = 0; l < n_layers && ok; ++l)
         ok = dalloc(c, &c->y32[l], (size_t)max_batch * sizes[l + 1]) && dalloc(c, &c->y16[l], (size_t)max_batch * sizes[l + 1]);
     for (int b = 0; b < 2 && ok; ++b)
@@ -557,7 +652,9 @@ pic_status mlp_loss_grad(mlp_ctx* c, int32_t batch, const float* x, const float*
     const int L = c->L;
     const long long ny = (long long)batch * c->sizes[L];
     int cur = 0;
-    k_mse<<<1, 1024, 0, c->stream>>>(c->y32[L - 1], t, ny, c->g32[cur], c->g16[cur], loss ? loss : c->loss);
+    const int nb = (int)std::min<long long>(MSE_BLOCKS, (ny + 255) / 256);
+    k_mse<<<nb, 256, 0, c->stream>>>(c->y32[L - 1], t, ny, c->g32[cur], c->g16[cur], c->mse_part);
+    k_mse_final<<<1, 256, 0, c->stream>>>(c->mse_part, nb, ny, loss ? loss : c->loss);
     e = cudaGetLastError();
     for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
         const int in = c->sizes[l], out = c->sizes[l + 1];
@@ -566,7 +663,7 @@ pic_status mlp_loss_grad(mlp_ctx* c, int32_t batch, const float* x, const float*
         e = gemm(c, c->g16[cur], out, 1, X, in, 1, out, in, batch, EP_STORE, nullptr, nullptr,
                  c->grad + c->woff[l], nullptr, in);
         if (e != cudaSuccess) break;
-        k_colsum<<<(out + 255) / 256, 256, 0, c->stream>>>(c->g32[cur], batch, out, c->grad + c->boff[l]);
+        k_colsum<<<(out + 31) / 32, dim3(32, 8), 0, c->stream>>>(c->g32[cur], batch, out, c->grad + c->boff[l]);
         e = cudaGetLastError();
         if (e != cudaSuccess || l == 0) break;
         // G_{l-1} = (G W_l) * (1 - y_{l-1}^2): M = batch, N = in, K = out

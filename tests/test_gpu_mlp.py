@@ -53,7 +53,7 @@ def test_initial_weights_are_glorot_uniform(N):
     net.close()
 
 
-@pytest.mark.parametrize("sizes,batch", [(WARM, 256), (RAGGED, 37)])
+@pytest.mark.parametrize("sizes,batch", [(WARM, 256), (RAGGED, 37), (WARM, 37), ([16, 64, 40, 24], 200)])
 def test_gradients_match_oracle(N, sizes, batch):
     rng = np.random.default_rng(12)
     net = N.MLP(sizes, max_batch=batch, seed=9)
