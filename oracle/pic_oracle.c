@@ -39,7 +39,10 @@
  *   moments         cycle averages (section "Results"). Pinned by the
  *                   uniform static load.
  * Secondary electron emission is not in the paper (it assumes none); it is
- * an added option, "parity unpinned" beyond its emitted-count statistics.
+ * an added option. Pinned by its emitted count (binomial in the absorbed
+ * ions) and the emitted velocities (the flux of a Maxwellian at 2 eV:
+ * Rayleigh normal speed, normal tangential components, independent, mean
+ * energy 2 T).
  *
  * Every per-particle value is of type real (float or double, see the
  * header); values drawn from the random streams (directions, normals) are

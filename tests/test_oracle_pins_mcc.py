@@ -219,7 +219,8 @@ def test_excitation_and_ionization_directions_are_isotropic():
 def test_secondary_electron_velocity_law():
     """Added option (not in the paper): an emitted electron leaves the wall with the flux-weighted
     half-Maxwellian of kT = 2 eV in its normal component, P(v_n <= v) = 1 - exp(-v^2 / (2 s^2)),
-    s^2 = kT / m_e (a Rayleigh law), and Maxwellian tangential components of the same s."""
+    s^2 = kT / m_e (a Rayleigh law), Maxwellian tangential components of the same s, the three
+    independent, mean energy 2 kT."""
     M = 4.002602 * I.AMU
     d = I.discharge(n_cells=32, gamma_see=0.5, steps_per_period=400)
     n_pts, de = 101, 1.0
@@ -242,3 +243,10 @@ def test_secondary_electron_velocity_law():
     assert stats.kstest(vnorm, "halfnorm", args=(0, s)).pvalue < 1e-6
     for key in ("vx", "vy"):
         assert stats.kstest(born[key] / s, "norm").pvalue > 1e-4
+    # the three components are independent (|r| ~ 1 / sqrt(k) between any two) and a flux member's
+    # energy is Gamma(3, kT) distributed: mean 2 kT, variance 3 (kT)^2
+    for a, b in (("vx", "vy"), ("vx", "vz"), ("vy", "vz")):
+        x, y = born[a], (np.abs(born[b]) if b == "vz" else born[b])
+        assert abs(np.corrcoef(x, y)[0, 1]) < 5 / math.sqrt(k)
+    eps = 0.5 * I.M_E * (born["vx"] ** 2 + born["vy"] ** 2 + born["vz"] ** 2) / I.E_CH
+    assert abs(eps.mean() - 4.0) <= 5 * math.sqrt(3 * 4.0 / k)
