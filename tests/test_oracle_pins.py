@@ -95,18 +95,20 @@ def test_box_muller_and_isotropy_statistics():
 # --------------------------------------------------------------------------- field solve
 
 def test_poisson_uniform_charge_closed_form():
-    """Eq. (poisson) with uniform rho0 and phi(0)=V, phi(d)=0: phi = V(1-z/d) + rho0 z(d-z)/(2 eps0).
-    The 3-point stencil is exact for quadratics, so the nodes agree to round-off; E = -phi' is linear
-    and the central / half-cell wall formulas reproduce it exactly."""
-    for N, d, V, rho0 in [(128, 0.025, 200.0, 3e-5), (2048, 0.05, -500.0, -1e-4), (7, 0.01, 13.0, 2e-6)]:
+    """Eq. (poisson) with uniform rho0 and phi(0) = V0, phi(d) = VN:
+    phi = V0 + (VN - V0) z/d + rho0 z(d-z)/(2 eps0). The 3-point stencil is exact for quadratics, so
+    the nodes agree to round-off; E = -phi' is linear and the central / half-cell wall formulas
+    reproduce it exactly. (The discharge grounds z = d; the solver also takes a nonzero VN.)"""
+    for N, d, V0, VN, rho0 in [(128, 0.025, 200.0, 0.0, 3e-5), (2048, 0.05, -500.0, 0.0, -1e-4),
+                               (7, 0.01, 13.0, 0.0, 2e-6), (64, 0.02, 100.0, -40.0, 5e-6), (9, 0.01, 0.0, 25.0, 0.0)]:
         dx = d / N
         z = np.arange(N + 1) * dx
-        phi, E = O.poisson(np.full(N + 1, rho0), dx, V, 0.0)
-        phi_ref = V * (1 - z / d) + rho0 * z * (d - z) / (2 * I.EPS0)
-        E_ref = V / d - rho0 * (d - 2 * z) / (2 * I.EPS0)
-        scale = abs(V) + abs(rho0) * d * d / I.EPS0
+        phi, E = O.poisson(np.full(N + 1, rho0), dx, V0, VN)
+        phi_ref = V0 + (VN - V0) * z / d + rho0 * z * (d - z) / (2 * I.EPS0)
+        E_ref = (V0 - VN) / d - rho0 * (d - 2 * z) / (2 * I.EPS0)
+        scale = abs(V0) + abs(VN) + abs(rho0) * d * d / I.EPS0
         assert np.max(np.abs(phi - phi_ref)) <= 1e-12 * scale * N
-        assert np.max(np.abs(E - E_ref)) <= 1e-11 * (abs(V) / d + abs(rho0) * d / I.EPS0) * N
+        assert np.max(np.abs(E - E_ref)) <= 1e-11 * ((abs(V0) + abs(VN)) / d + abs(rho0) * d / I.EPS0) * N
 
 
 def test_poisson_random_charge_dense_solve():
@@ -324,6 +326,33 @@ def test_brute_force_collision_probability_electrons():
     se = math.sqrt(p_alg * (1 - p_alg) / n)
     assert abs(k / n - p_alg) <= 5 * se
     assert abs(k / n - p_exact) <= 5 * se + nu * dt * numax * dt / 2
+
+
+def test_collision_rate_above_the_table_is_the_last_row():
+    """Above the table's last energy the last row is used: with sigma_el = 1e-20 m^2 everywhere but
+    1e-19 at the last point (100 eV), an electron at 150 eV has the last row's rate sigma v(100 eV),
+    which is the table's maximum, so it collides with the candidate probability itself,
+    P = 1 - exp(-nu_max dt) (the row before would give a tenth of that)."""
+    n_pts, de = 101, 1.0
+    sig = np.full(n_pts, 1e-20)
+    sig[-1] = 1e-19
+    z = np.zeros(n_pts)
+    g = _gas_custom(4.002602 * I.AMU, n_pts, de, [sig, z, z], [z, z])
+    d = I.discharge(n_cells=64, p_Pa=30.0, steps_per_period=int(1 / (13.56e6 * 7.4e-11)))
+    o = O.Oracle(g, d, "f64", load=False)
+    o.set_field(np.zeros(65))
+    n = 200_000
+    v = math.sqrt(2 * I.E_CH * 150.0 / I.M_E)
+    rng = np.random.default_rng(8)
+    o.set_state(0, I.speed_state(rng, n, 64, v))
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    k = o.counters()["collisions_e"][0]
+    n_gas = d.p_Pa / (I.K_B * d.T_gas_K)
+    numax = n_gas * 1e-19 * math.sqrt(2 * I.E_CH * 100.0 / I.M_E)
+    p = -math.expm1(-numax * d.dt_s)
+    assert 0.05 < p < 0.6
+    assert abs(k / n - p) <= 5 * math.sqrt(p * (1 - p) / n)
 
 
 def test_brute_force_collision_probability_ions_centre_of_mass():
