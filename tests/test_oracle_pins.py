@@ -649,6 +649,15 @@ def test_wall_flux_one_sided_maxwellian():
         assert abs(ab[side] - expect) <= 5 * math.sqrt(expect) + 1e-3 * expect
 
 
+def _half_kick(o, d, sp, st):
+    """(q/m) E(x, 0) dt / 2 at each particle of species sp (He-like mass for ions), with E the
+    oracle's t = 0 node field interpolated linearly: what the load subtracted from v_z."""
+    E = o.get_field()
+    qm = -I.E_CH / I.M_E if sp == 0 else I.E_CH / (4.002602 * I.AMU)
+    Ez = E[st["c"]] + st["f"] * (E[st["c"] + 1] - E[st["c"]])
+    return qm * Ez * d.dt_s / 2
+
+
 def test_load_positions_and_velocities():
     """Homogeneous quasi-neutral start (section 'Boundary conditions and initial values'): uniform
     positions, Maxwellian velocities at T_e0 and T_i0."""
@@ -658,8 +667,17 @@ def test_load_positions_and_velocities():
         st = o.get_state(sp)
         z = (st["c"] + st["f"]) / 128
         assert stats.kstest(z, "uniform").pvalue > 1e-4
+        # every cell, the last one included, holds its binomial share n / N
+        cnt = np.bincount(st["c"], minlength=128)
+        assert cnt.size == 128 and np.all(np.abs(cnt - 30000 / 128) <= 5 * math.sqrt(30000 / 128))
         assert stats.kstest(st["vx"] / sig, "norm").pvalue > 1e-4
         assert stats.kstest(st["vy"] / sig, "norm").pvalue > 1e-4
+        # v_z: the stored value plus the half kick of the t = 0 field is the Maxwellian sample,
+        # independent of the other two components
+        vz0 = st["vz"] + _half_kick(o, d, sp, st)
+        assert stats.kstest(vz0 / sig, "norm").pvalue > 1e-4
+        for a, b in ((st["vx"], st["vy"]), (st["vx"], vz0), (st["vy"], vz0)):
+            assert abs(np.corrcoef(a, b)[0, 1]) < 5 / math.sqrt(a.size)
 
 
 def test_moments_of_uniform_load():
@@ -775,10 +793,12 @@ def test_warm_load_follows_profiles():
     the profile integral over the weight, positions follow the density, electron velocities are
     Maxwellian with kT = 2/3 of the local mean energy, ion velocities Maxwellian at T_gas."""
     P, gap, N = 33, 0.025, 64
-    d = I.discharge(n_cells=N, n_e0=1, n_i0=1, V_rf_V=0.0, n_init_m3=1e14, gap_m=gap)
+    # weights of 1e14 m^-3 x gap / 1000: about 20000 electrons and 15000 ions from these profiles
+    d = I.discharge(n_cells=N, n_e0=1000, n_i0=1000, V_rf_V=0.0, n_init_m3=1e14, gap_m=gap)
     o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=False)
     z, prof = _tent_profiles(P, gap, 4e15, 1.5e15)
     o.load_profiles(*prof)
+    assert o.count(0) > 15000 and o.count(1) > 10000
     ne_int, ni_int = 4e15 * gap / 2, 1.5e15 * gap  # exact integrals of the tent and the flat profile
     assert o.count(0) == math.floor(ne_int / d.w_e + 0.5)
     assert o.count(1) == math.floor(ni_int / d.w_i + 0.5)
@@ -797,6 +817,10 @@ def test_warm_load_follows_profiles():
             sig = np.full(n, math.sqrt(I.K_B * d.T_gas_K / (4.002602 * I.AMU)))
         for k in ("vx", "vy"):
             assert stats.kstest(st[k] / sig, "norm").pvalue > 1e-4
+        vz0 = st["vz"] + _half_kick(o, d, sp, st)
+        assert stats.kstest(vz0 / sig, "norm").pvalue > 1e-4
+        for a, b in ((st["vx"], st["vy"]), (st["vx"], vz0), (st["vy"], vz0)):
+            assert abs(np.corrcoef(a, b)[0, 1]) < 5 / math.sqrt(n)
     # the field is solved at t = 0 from the loaded charge: non-zero, since n_e != n_i
     assert np.max(np.abs(o.get_field())) > 0
 
@@ -814,3 +838,108 @@ def test_warm_load_clips_negative_density_and_loads_empty_species():
     assert o.count(0) == math.floor(A / d.w_e + 0.5)
     st = o.get_state(0)
     assert np.all((st["c"] + st["f"]) / 32 * gap <= z[P // 2 + 1])
+
+
+def test_cold_load_stores_the_half_back_kicked_velocity():
+    """The load stores v* = v_0 - (q/m) E(x_0, 0) dt / 2, so that the first half kick of the first
+    step gives v_0 (the Verlet start). With T_e0 = T_i0 = 0 the loaded velocities are zero, and
+    with twice as many ions as electrons the space charge makes a field at t = 0 (V_rf sin 0 = 0):
+    the stored v_z is exactly minus the half kick of the field at the particle."""
+    d = I.discharge(n_cells=64, n_e0=20000, n_i0=40000, V_rf_V=300.0, T_e0_eV=0.0, T_i0_K=0.0, n_init_m3=1e15)
+    o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=True)
+    E = o.get_field()
+    assert np.max(np.abs(E)) > 1e3
+    M = X.he_like(eps_max_eV=50, de_eV=1e-2).mass_kg
+    for sp, qm in ((0, -I.E_CH / I.M_E), (1, I.E_CH / M)):
+        st = o.get_state(sp)
+        assert np.all(st["vx"] == 0) and np.all(st["vy"] == 0)
+        Ez = E[st["c"]] + st["f"] * (E[st["c"] + 1] - E[st["c"]])
+        kick = qm * Ez * d.dt_s / 2
+        assert np.allclose(st["vz"], -kick, rtol=1e-12, atol=1e-12 * np.max(np.abs(kick)))
+        assert np.max(np.abs(st["vz"])) > 0
+
+
+def test_energy_moment_is_split_by_cic_and_clamped():
+    """The electron energy moment at (x_n, v_n) is deposited like charge: (1 - f) of it at node c, f
+    at node c + 1, in 2^-12 eV units, each electron's energy clamped at 16384 eV (2^26 units)."""
+    o = O.Oracle(_no_collision_gas(4.002602 * I.AMU), I.discharge(n_cells=32), "f64", load=False)
+    o.set_field(np.zeros(33))
+    e1, e2 = 10.0, 20000.0
+    v1, v2 = math.sqrt(2 * I.E_CH * e1 / I.M_E), math.sqrt(2 * I.E_CH * e2 / I.M_E)
+    st = {"c": np.array([3, 20], np.int32), "f": np.array([0.25, 0.5]), "vx": np.array([v1, v2]),
+          "vy": np.zeros(2), "vz": np.zeros(2)}
+    o.set_state(0, st)
+    o.set_state(1, {k: v[:1] for k, v in st.items()})
+    o.sweep()
+    Q = o.get_energy_deposit()
+    u1 = e1 * 4096
+    assert abs(Q[3] - 0.75 * u1) <= 1 and abs(Q[4] - 0.25 * u1) <= 1
+    assert Q[20] == 2 ** 25 and Q[21] == 2 ** 25
+    assert np.sum(Q) == Q[3] + Q[4] + 2 ** 26
+
+
+def test_excitation_levels_lose_their_own_thresholds():
+    """Two excitation levels (Table 'reactions' lists two for each gas) at 10 and 15 eV: an electron
+    of 20 eV that excites level j leaves with exactly 20 eV - eps_j, isotropically."""
+    M = 4.002602 * I.AMU
+    n_pts, de = 40001, 5e-3
+    eps = np.arange(n_pts) * de
+    v = np.sqrt(2 * I.E_CH * np.maximum(eps, 1e-9) / I.M_E)
+    z = np.zeros(n_pts)
+    c1 = np.where(eps > 10.0, 1e-10 / v, 0.0)
+    c2 = np.where(eps > 15.0, 1e-10 / v, 0.0)
+    g = _gas_custom(M, n_pts, de, [z, c1, c2, z], [z, z], eps_exc=(10.0, 15.0))
+    o = O.Oracle(g, I.discharge(n_cells=64), "f64", load=False)
+    o.set_field(np.zeros(65))
+    rng = np.random.default_rng(41)
+    n = 6000
+    st = I.energy_state(rng, n, 64, 20.0, 20.0, I.M_E)
+    st["c"][:] = 32
+    o.set_state(0, st)
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    c = o.counters()["collisions_e"]
+    assert c[1] + c[2] == n and c[1] > n // 3 and c[2] > n // 3
+    out = o.get_state(0)
+    e = 0.5 * I.M_E * (out["vx"] ** 2 + out["vy"] ** 2 + out["vz"] ** 2) / I.E_CH
+    at10, at5 = np.abs(e - 10.0) < 1e-9, np.abs(e - 5.0) < 1e-9
+    assert at10.sum() == c[1] and at5.sum() == c[2]
+
+
+def test_newborns_get_the_half_kick_of_their_birth():
+    """Velocity Verlet with collisions at v_n: the ionizing electron gets its second half kick after
+    the collision, and both newborns (born at t_n) get one half kick from the field at the parent.
+    In a uniform field E0 the scattered and the ejected electron therefore both have
+    |v - (q/m) E0 dt/2 z| = sqrt((eps_n - eps_iz) / 2) in speed units, and the newborn ions' mean v_z
+    is (e / M) E0 dt/2 (their thermal v_z averages out)."""
+    M = 4.002602 * I.AMU
+    eiz = 24.6
+    g = _forced_gas(M, 2, 1e-10, eps_th=eiz)
+    d = I.discharge(n_cells=64)
+    o = O.Oracle(g, d, "f64", load=False)
+    E0 = 1e5
+    o.set_field(np.full(65, E0))
+    rng = np.random.default_rng(43)
+    n = 8000
+    # 80-200 eV: after the first half kick (up to 1.6e6 m/s here) every electron is still above
+    # the threshold, so every one ionizes
+    st = I.energy_state(rng, n, 64, 80.0, 200.0, I.M_E)
+    st["c"][:] = 32
+    o.set_state(0, st)
+    o.set_state(1, I.speed_state(rng, 1, 64, 0.0))
+    o.sweep()
+    assert o.counters()["collisions_e"][3] == n
+    Ke = -I.E_CH / I.M_E * E0 * d.dt_s / 2
+    vzn = st["vz"] + Ke
+    eps_n = 0.5 * I.M_E * (st["vx"] ** 2 + st["vy"] ** 2 + vzn ** 2) / I.E_CH
+    out = o.get_state(0)
+    s2 = (out["vx"] ** 2 + out["vy"] ** 2 + (out["vz"] - Ke) ** 2) * 0.5 * I.M_E / I.E_CH
+    ref = (eps_n - eiz) / 2
+    assert np.max(np.abs(s2[:n] - ref)) < 1e-9 * np.max(ref)
+    assert np.max(np.abs(s2[n:] - ref)) < 1e-9 * np.max(ref)
+    ions = o.get_state(1)
+    vz_i = ions["vz"][1:]
+    Ki = I.E_CH / M * E0 * d.dt_s / 2
+    sig_n = math.sqrt(I.K_B * 300.0 / M)
+    assert abs(np.mean(vz_i) - Ki) <= 5 * sig_n / math.sqrt(n)
+    assert Ki > 10 * sig_n / math.sqrt(n)
