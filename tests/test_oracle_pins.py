@@ -943,3 +943,72 @@ def test_newborns_get_the_half_kick_of_their_birth():
     sig_n = math.sqrt(I.K_B * 300.0 / M)
     assert abs(np.mean(vz_i) - Ki) <= 5 * sig_n / math.sqrt(n)
     assert Ki > 10 * sig_n / math.sqrt(n)
+
+
+def test_sort_schedule():
+    """Periodic sorting: with sort_every = k the store is sorted by cell (stably) after the sweep of
+    step n when (n + 1) % k == 0, and only then; the first load is in random cell order."""
+    d = I.discharge(n_cells=64, n_e0=4000, n_i0=4000, V_rf_V=100.0, steps_per_period=400)
+    o = O.Oracle(X.he_like(eps_max_eV=100, de_eV=1e-2), d, "f64", sort_every=4, load=True)
+    sorted_ = lambda: all(np.all(np.diff(o.get_state(sp)["c"]) >= 0) for sp in (0, 1))
+    assert not sorted_()
+    for n in range(8):
+        o.step(1)
+        assert sorted_() == ((n + 1) % 4 == 0), n
+
+
+def test_mean_energy_divides_by_the_density_at_x_n():
+    """The mean electron energy is the energy moment at (x_n, v_n) over the density moment at x_n
+    (the same particles at the same time), not the density after the push: electrons that sit on
+    node 10 and cross two cells in the step report their energy at node 10 and none at node 12."""
+    N = 32
+    d = I.discharge(n_cells=N, steps_per_period=400)
+    o = O.Oracle(_no_collision_gas(), d, "f64", load=False)
+    o.set_field(np.zeros(N + 1))
+    dx = d.gap_m / N
+    vz = 2.0 * dx / d.dt_s
+    eps = 0.5 * I.M_E * vz * vz / I.E_CH
+    n = 100
+    st = {"c": np.full(n, 10, np.int32), "f": np.zeros(n), "vx": np.zeros(n), "vy": np.zeros(n), "vz": np.full(n, vz)}
+    o.set_state(0, st)
+    o.set_state(1, {k: v[:1] for k, v in st.items()})
+    # the density moment at x_n is the previous sweep's deposit: n electrons on node 10
+    D = np.zeros(N + 1, np.int64)
+    D[10] = n * 2 ** 32
+    o.set_deposit(0, D)
+    o.reset_moments()
+    o.step(1)
+    m = o.moments()
+    assert abs(m["mean_eps"][10] - eps) <= 2.0 ** -12 + 1e-12 * eps
+    assert m["mean_eps"][12] == 0.0
+
+
+def test_warm_load_temperature_is_interpolated_between_profile_points():
+    """Electron temperature of the warm load: kT = 2/3 of the mean energy interpolated linearly at the
+    sampled position. Two profile points, 1 eV at z = 0 and 9 eV at z = d, uniform density."""
+    gap, N = 0.025, 64
+    d = I.discharge(n_cells=N, n_e0=1000, n_i0=1000, V_rf_V=0.0, n_init_m3=1e14, gap_m=gap)
+    o = O.Oracle(X.he_like(eps_max_eV=50, de_eV=1e-2), d, "f64", load=False)
+    o.load_profiles(np.array([1e15, 1e15]), np.array([1e15, 1e15]), np.array([1.0, 9.0]))
+    st = o.get_state(0)
+    assert st["c"].size == 10000  # 1e15 m^-3 x 2.5 cm over the weight 2.5e9
+    x = (st["c"] + st["f"]) / N
+    sig = np.sqrt(I.E_CH * (2.0 / 3.0) * (1.0 + 8.0 * x) / I.M_E)
+    for k in ("vx", "vy"):
+        assert stats.kstest(st[k] / sig, "norm").pvalue > 1e-4
+
+
+def test_moment_reset_counts_absorptions_since_the_reset():
+    """After reset_moments the moments average over the steps since the reset, and the absorbed
+    counts they report are those since the reset."""
+    d = I.discharge(n_cells=64, n_e0=5000, n_i0=5000, V_rf_V=200.0, steps_per_period=200)
+    o = O.Oracle(X.he_like(eps_max_eV=100, de_eV=1e-2), d, "f64", load=True)
+    o.step(40)
+    a0 = np.array(o.counters()["absorbed"], dtype=np.int64)
+    o.reset_moments()
+    o.step(30)
+    a1 = np.array(o.counters()["absorbed"], dtype=np.int64)
+    m = o.moments()
+    assert m["steps"] == 30
+    assert np.all(a0 > 0) or a0.sum() > 0
+    assert np.array_equal(np.array(m["absorbed"], dtype=np.int64), a1 - a0)
