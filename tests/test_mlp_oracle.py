@@ -83,3 +83,17 @@ def test_bf16_rounding_definition():
     # the nearer neighbour: |a - r| <= half the bf16 spacing at a
     sp = 2.0 ** (np.floor(np.log2(np.abs(a))) - 7)
     assert np.all(np.abs(a.astype(np.float64) - ra) <= 0.5 * sp + 1e-30)
+
+
+def test_only_weights_are_rounded_to_bf16():
+    """The network keeps FP32 master parameters; its products see BF16 weights, while the biases
+    enter the epilogue in FP32: weights_bf16 rounds exactly the weight slots of the flat layout."""
+    sizes = [3, 5, 2]
+    lay, n = M.layout(sizes)
+    p = (1.0 + np.arange(n, dtype=np.float32) * np.float32(1e-3)).astype(np.float32)  # none exact in BF16
+    q = M.weights_bf16(p, sizes)
+    for (w, b, i, o) in lay:
+        assert np.array_equal(q[b:b + o], p[b:b + o])
+        W = q[w:w + i * o]
+        assert np.all(W.view(np.uint32) & 0xFFFF == 0) and not np.array_equal(W, p[w:w + i * o])
+        assert np.all(np.abs(W - p[w:w + i * o]) <= np.abs(p[w:w + i * o]) * 2.0 ** -8)
